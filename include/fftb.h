@@ -1,0 +1,193 @@
+/*
+ * fftb.h -- batched, pruned plane-wave 3D FFT between a cutoff sphere of
+ * coefficients and the full real-space cube, on one GPU (sm_103a).
+ *
+ * The operation (Sec. 2.2 of Popovici, Del Ben, Marques, Canning, "Flexible
+ * Multi-Dimensional FFTs for Plane Wave Density Functional Theory Codes"):
+ *
+ *   G -> r   R_b[x,y,z] = sum_{G in sphere} c_b(G) exp(+2 pi j (gx x/N0 + gy y/N1 + gz z/N2))
+ *   r -> G   c_b(G)     = sum_{x,y,z} R_b[x,y,z] exp(-2 pi j (gx x/N0 + gy y/N1 + gz z/N2))
+ *
+ * Neither direction is scaled, so r->G after G->r multiplies by N0*N1*N2.
+ * The sign of G->r follows the plane-wave expansion psi(r) = sum_g c(g)
+ * e^{j g r} (Sec. 2.2); the sign of r->G follows omega_n = e^{-j 2 pi/n}
+ * (Sec. 2.1). The sphere is the set of integer G with |G + k| <= r in grid
+ * units (the cutoff rule 1/2 |g|^2 <= E_cut, Sec. 2.2), components in
+ * [-N/2, N/2). G sits at cube index (gx mod N0, gy mod N1, gz mod N2).
+ *
+ * The padding is staged as in Fig. 3: z-FFTs run only on occupied (x,y)
+ * sticks, y-FFTs only on occupied x-slabs, and x-FFTs on full lines; the
+ * reverse direction prunes its outputs the same way.
+ *
+ * Data layout (all complex data interleaved re,im; float for FP32 and
+ * MIXED_TC plans, double for FP64 plans):
+ *   sphere batch : concatenation over k-points of [B_k][ngw_k]   (band-major)
+ *   cube batch   : concatenation over k-points of [B_k][N2][N1][N0] (x fastest,
+ *                  Sec. 2.1: n0 is the fastest dimension in memory)
+ *   potential V  : real, [N2][N1][N0]
+ * Within one k-point the sphere order is the user's list order, or for a
+ * cutoff sphere the canonical order: sorted by gy, then gx, then gz, each
+ * ascending over signed values (the offset array over the xy projection of
+ * Sec. 3.3 / Fig. 6, one contiguous run per (gx, gy) stick).
+ *
+ * Errors: every call returns a status code; no exception crosses this ABI
+ * (the paper's plan builder throws on an unsupported pattern, Sec. 3.1;
+ * here that is FFTB_ERR_UNSUPPORTED). fftb_last_error() gives a message.
+ * Pointers named *_dev are device pointers owned by the caller; the library
+ * never frees them. Host pointers are read during the call only.
+ */
+#ifndef FFTB_H
+#define FFTB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fftb_plan_s* fftb_plan;
+
+typedef enum {
+  FFTB_OK = 0,
+  FFTB_ERR_INVALID_ARG = 1,    /* bad size, pointer, index or argument combination */
+  FFTB_ERR_UNSUPPORTED = 2,    /* valid request this build has no kernel for       */
+  FFTB_ERR_ALLOC = 3,          /* device or host allocation failed                 */
+  FFTB_ERR_CUDA = 4,           /* a CUDA runtime call failed                       */
+  FFTB_ERR_DEVICE_TIMEOUT = 5  /* a device-side bounded wait gave up               */
+} fftb_status;
+
+typedef enum {
+  FFTB_G_TO_R = 1,        /* sphere -> cube                                      */
+  FFTB_R_TO_G = -1,       /* cube -> sphere                                      */
+  FFTB_ROUNDTRIP = 0,     /* sphere -> cube (kept) -> sphere                     */
+  FFTB_APPLY_LOCAL = 2    /* sphere -> V(r) * psi(r) -> sphere; cube never stored */
+} fftb_direction;
+
+typedef enum {
+  FFTB_FP64 = 0,          /* complex128 storage and arithmetic                   */
+  FFTB_FP32 = 1,          /* complex64 storage and arithmetic                    */
+  FFTB_MIXED_TC = 2       /* complex64 storage; split-precision tensor-core radix stages */
+} fftb_precision;
+
+/* Plan description. Either radius (+ kshift) or g_list describes the spheres. */
+typedef struct {
+  int32_t n[3];            /* N0 (x), N1 (y), N2 (z) grid extents                 */
+  int32_t n_kpoints;       /* number of spheres (k-points), >= 1                   */
+  const int32_t* bands;    /* host, n_kpoints band counts (each >= 0); NULL = 1 each */
+  double radius;           /* cutoff radius r in grid units (used when g_list == NULL) */
+  const double* kshift;    /* host, n_kpoints * 3 shifts (kx,ky,kz) in grid units; NULL = 0 */
+  const int32_t* g_list;   /* host, optional explicit spheres: concatenated (gx,gy,gz)
+                              triples of every k-point, in the order the data uses;
+                              copied at plan creation                                */
+  const int64_t* g_count;  /* host, n_kpoints sizes of g_list's parts (with g_list)  */
+  int32_t layout;          /* 0 = band-major sphere and cube (the only layout now)   */
+  int32_t max_chunk_bands; /* bands per launch chunk; 0 = chosen by the plan         */
+} fftb_desc;
+
+/* Plan facts, for allocation and reporting. */
+typedef struct {
+  int64_t sphere_elems;    /* complex elements of the whole sphere batch            */
+  int64_t cube_elems;      /* complex elements of the whole cube batch              */
+  int64_t scratch_bytes;   /* device scratch the plan owns                          */
+  int32_t total_bands;     /* sum of bands over k-points                            */
+  int32_t max_sticks;      /* largest number of occupied (x,y) sticks over k-points */
+  int32_t max_slabs;       /* largest number of occupied x values over k-points     */
+  int32_t chunk_bands;     /* bands per launch chunk                                */
+  int32_t kernels_per_execute; /* kernel launches one fftb_execute issues           */
+  int32_t complex_bytes;   /* 8 (FP32, MIXED_TC) or 16 (FP64)                       */
+} fftb_plan_info_t;
+
+/* Builds the spheres, stick/slab tables and twiddles on the host, uploads
+ * them to the current CUDA device and allocates the plan's scratch. The only
+ * call that allocates device memory or synchronises the device.
+ * Errors: INVALID_ARG for a bad description (grid extent outside the
+ * supported list, sphere that does not fit the grid and would alias, G
+ * outside [-N/2, N/2), duplicate G, negative bands); UNSUPPORTED for a valid
+ * request without a kernel; ALLOC; CUDA. *out is NULL on error. */
+fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* desc,
+                             fftb_direction direction, fftb_precision precision);
+
+/* Number of G vectors of one k-point's sphere. */
+fftb_status fftb_plan_ngw(fftb_plan plan, int32_t kpoint, int64_t* ngw);
+
+/* Copies one k-point's sphere, ngw*3 int32 (gx,gy,gz), into host memory, in
+ * the order the sphere data uses. */
+fftb_status fftb_plan_sphere(fftb_plan plan, int32_t kpoint, int32_t* g_out);
+
+/* Fills *info. */
+fftb_status fftb_plan_get_info(fftb_plan plan, fftb_plan_info_t* info);
+
+/* Sets the real potential V (device, [N2][N1][N0], float for FP32/MIXED_TC,
+ * double for FP64) used by FFTB_APPLY_LOCAL plans. Borrowed: it must stay
+ * valid while executes that use it are in flight. */
+fftb_status fftb_set_potential(fftb_plan plan, const void* v_dev);
+
+/* Enqueues the transform on `stream` (a cudaStream_t; NULL = legacy default
+ * stream). Asynchronous: no synchronisation and no allocation.
+ *   G_TO_R      : in_dev = sphere batch, out_dev = cube batch, cube_dev NULL
+ *   R_TO_G      : in_dev = cube batch,   out_dev = sphere batch, cube_dev NULL
+ *   ROUNDTRIP   : in_dev = sphere batch, out_dev = sphere batch,
+ *                 cube_dev = cube batch that receives the real-space cube
+ *   APPLY_LOCAL : in_dev = sphere batch, out_dev = sphere batch, cube_dev NULL,
+ *                 out = P_sphere DFT_fwd(V * DFT_inv(pad(in)))
+ * in_dev and out_dev must not overlap; buffers are aligned to the complex
+ * element size (8 bytes FP32/MIXED_TC, 16 bytes FP64). */
+fftb_status fftb_execute(fftb_plan plan, const void* in_dev, void* out_dev,
+                         void* cube_dev, void* stream);
+
+/* As fftb_execute, but in_host / out_host are host buffers (pinned for
+ * full-speed copies). Copies the input to plan-owned device staging, runs
+ * the transform, copies the result back and synchronises `stream`. The
+ * staging buffers are allocated on the first call and kept with the plan.
+ * For ROUNDTRIP cube_dev is a device cube batch (may be NULL: plan-owned). */
+fftb_status fftb_execute_host(fftb_plan plan, const void* in_host, void* out_host,
+                              void* cube_dev, void* stream);
+
+/* Per-kernel timing, for profiling. While enabled, fftb_execute records a
+ * CUDA event pair around every kernel it launches, on the execute's stream
+ * (the events are created by the first timed execute). Disabled by default.
+ * Kinds: 0 z-stage G->r, 1 plane G->r, 2 plane r->G, 3 z-stage r->G,
+ * 4 plane apply (FFTB_STAGE_KINDS entries). */
+#define FFTB_STAGE_KINDS 5
+fftb_status fftb_plan_set_timing(fftb_plan plan, int32_t enable);
+
+/* Waits for the recorded events, writes for each kind the summed kernel
+ * milliseconds and launch count since the previous query (arrays of
+ * FFTB_STAGE_KINDS entries), then starts a new accumulation. */
+fftb_status fftb_plan_stage_times(fftb_plan plan, double* ms, int64_t* launches);
+
+/* Kernel launches this plan has issued so far (all executes). */
+int64_t fftb_plan_launches(fftb_plan plan);
+
+/* Releases the plan's device memory and tables. NULL is accepted. */
+fftb_status fftb_destroy(fftb_plan plan);
+
+/* Static description of a status code. */
+const char* fftb_error_string(fftb_status status);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char* fftb_last_error(void);
+
+/* Host-only helpers (no GPU needed). */
+
+/* Enumerates the cutoff sphere |G + k| <= r of an N0 x N1 x N2 grid (Sec.
+ * 2.2) in canonical order (gy, then gx, then gz ascending). kshift may be
+ * NULL (k = 0). Sets *ngw; when g_out is non-NULL writes min(ngw, capacity)
+ * (gx,gy,gz) triples. INVALID_ARG if the sphere does not fit the grid. */
+fftb_status fftb_sphere_enumerate(const int32_t n[3], double radius, const double* kshift,
+                                  int32_t* g_out, int64_t capacity, int64_t* ngw);
+
+/* Validates an explicit sphere (components in [-N/2, N/2), no duplicates)
+ * and reports its occupied (x,y) sticks and occupied x values: the offset
+ * array over the xy projection (Sec. 3.3, Fig. 6) has n_sticks runs. */
+fftb_status fftb_sphere_sticks(const int32_t n[3], const int32_t* g, int64_t ngw,
+                               int32_t* n_sticks, int32_t* n_slabs);
+
+/* Library version string. */
+const char* fftb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFTB_H */

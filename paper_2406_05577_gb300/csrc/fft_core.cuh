@@ -1,0 +1,233 @@
+// fft_core.cuh -- register codelets and shared-memory Stockham passes for the
+// batched 1D DFTs of the staged sphere <-> cube transform.
+//
+// A 1D DFT of length N (Sec. 2.1: y = DFT_n x, omega_n = e^{-j 2 pi/n}; the
+// G -> r direction uses the conjugate root, Sec. 2.2) is factored
+// Cooley-Tukey style (N = R_0 R_1 ... R_{P-1}, Sec. 2.1) into Stockham
+// autosort passes. Pass p with radix R reads R inputs spaced N/R apart,
+// twiddles them by w^{j k} (k = butterfly index mod L, L = R_0...R_{p-1},
+// w = e^{s 2 pi j/(L R)}), runs a radix-R DFT in registers and writes the R
+// outputs spaced L apart at (i - k) R + k. After the last pass the data are
+// in natural order.
+//
+// Many independent lines run together. Every thread of the CTA takes
+// (line, butterfly) work items; a pass first loads all of its items into
+// registers, synchronises, then computes and stores, so a pass may work in
+// place on a shared-memory buffer.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fftb {
+
+// ------------------------------------------------------------ complex math
+template <typename T> struct cplx;
+template <> struct cplx<float> { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+
+__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+  return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// a * (S j), S = +1 or -1
+template <int S, typename C> __device__ __forceinline__ C mulj(C a) {
+  return S > 0 ? mk(-a.y, a.x) : mk(a.y, -a.x);
+}
+template <typename C, typename T> __device__ __forceinline__ C scale(C a, T s) {
+  return mk(a.x * s, a.y * s);
+}
+template <typename C> __device__ __forceinline__ C czero() { return mk(decltype(C::x)(0), decltype(C::x)(0)); }
+
+// ------------------------------------------------------------- codelets
+// In-place radix-R DFT y_k = sum_j x_j e^{S 2 pi j jk / R}, natural order.
+// The constants are cos/sin of 2 pi m / R written out from their closed forms.
+template <int S, typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
+  C t = a - b;
+  a = a + b;
+  b = t;
+}
+
+template <int S, typename C> __device__ __forceinline__ void dft4(C& x0, C& x1, C& x2, C& x3) {
+  C t0 = x0 + x2, t1 = x0 - x2, t2 = x1 + x3, t3 = mulj<S>(x1 - x3);
+  x0 = t0 + t2;
+  x2 = t0 - t2;
+  x1 = t1 + t3;
+  x3 = t1 - t3;
+}
+
+template <int S, typename C> __device__ __forceinline__ void dft3(C& x0, C& x1, C& x2) {
+  using T = decltype(C::x);
+  const T c1 = T(-0.5);                                   // cos(2 pi/3)
+  const T s1 = T(S) * T(0.86602540378443864676372317);   // S sin(2 pi/3) = S sqrt(3)/2
+  C t1 = x1 + x2, t2 = x1 - x2;
+  C a = x0 + scale(t1, c1);
+  C b = mulj<1>(scale(t2, s1));
+  x0 = x0 + t1;
+  x1 = a + b;
+  x2 = a - b;
+}
+
+template <int S, typename C> __device__ __forceinline__ void dft5(C& x0, C& x1, C& x2, C& x3, C& x4) {
+  using T = decltype(C::x);
+  const T c1 = T(0.30901699437494742410229342);          // cos(2 pi/5) = (sqrt5 - 1)/4
+  const T c2 = T(-0.80901699437494742410229342);         // cos(4 pi/5) = -(sqrt5 + 1)/4
+  const T s1 = T(S) * T(0.95105651629515357211643933);   // sin(2 pi/5)
+  const T s2 = T(S) * T(0.58778525229247312916870595);   // sin(4 pi/5)
+  C t1 = x1 + x4, t2 = x2 + x3, t3 = x1 - x4, t4 = x2 - x3;
+  C a1 = x0 + scale(t1, c1) + scale(t2, c2);
+  C a2 = x0 + scale(t1, c2) + scale(t2, c1);
+  C b1 = mulj<1>(scale(t3, s1) + scale(t4, s2));
+  C b2 = mulj<1>(scale(t3, s2) - scale(t4, s1));
+  x0 = x0 + t1 + t2;
+  x1 = a1 + b1;
+  x4 = a1 - b1;
+  x2 = a2 + b2;
+  x3 = a2 - b2;
+}
+
+template <int S, typename C> __device__ __forceinline__ void dft8(C* v) {
+  using T = decltype(C::x);
+  const T h = T(0.70710678118654752440084436);           // 1/sqrt(2)
+  C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<S>(e0, e1, e2, e3);
+  dft4<S>(o0, o1, o2, o3);
+  // o1 *= (1 + S j)/sqrt2, o2 *= S j, o3 *= (-1 + S j)/sqrt2
+  o1 = scale(o1 + mulj<S>(o1), h);
+  o2 = mulj<S>(o2);
+  o3 = scale(mulj<S>(o3) - o3, h);
+  v[0] = e0 + o0; v[4] = e0 - o0;
+  v[1] = e1 + o1; v[5] = e1 - o1;
+  v[2] = e2 + o2; v[6] = e2 - o2;
+  v[3] = e3 + o3; v[7] = e3 - o3;
+}
+
+template <int R, int S, typename C> __device__ __forceinline__ void dft(C* v) {
+  if constexpr (R == 2) dft2<S>(v[0], v[1]);
+  else if constexpr (R == 3) dft3<S>(v[0], v[1], v[2]);
+  else if constexpr (R == 4) dft4<S>(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 5) dft5<S>(v[0], v[1], v[2], v[3], v[4]);
+  else if constexpr (R == 8) dft8<S>(v);
+  else static_assert(R == 2, "unsupported radix");
+}
+
+// ------------------------------------------------------------ radix plan
+// Radices taken in this order: 8 while 8 | N, then 4, 2, 3, 5.
+template <int N> struct first_radix {
+  static constexpr int value = (N % 8 == 0) ? 8 : (N % 4 == 0) ? 4 : (N % 2 == 0) ? 2
+                               : (N % 3 == 0) ? 3 : (N % 5 == 0) ? 5 : 0;
+};
+template <int N> struct min_radix {
+  static constexpr int R = first_radix<N>::value;
+  static constexpr int rest = (R == 0 || R == N) ? 0 : min_radix<N / R>::value;
+  static constexpr int value = (rest == 0 || R < rest) ? R : rest;
+};
+template <> struct min_radix<1> { static constexpr int value = 0; };
+
+// ------------------------------------------------------------ fast division
+// q = n / d for n, d < 2^16 via one multiply-high (m = ceil(2^32 / d)).
+struct FastDiv {
+  uint32_t d, m;
+  __device__ __forceinline__ FastDiv(uint32_t dd) : d(dd), m(dd ? (uint32_t)((0x100000000ull + dd - 1) / dd) : 0u) {}
+  __device__ __forceinline__ uint32_t div(uint32_t n) const { return d == 1 ? n : __umulhi(n, m); }
+};
+
+// --------------------------------------------------------------- one pass
+// MAP_ELEM: consecutive threads take consecutive butterflies of one line
+// (coalesced along the transformed dimension); otherwise consecutive
+// threads take consecutive lines.
+template <int N, int R, int P, int S, int NT, int MAXIT, bool MAP_ELEM, typename C,
+          typename Src, typename Dst>
+__device__ __forceinline__ void stockham_pass(int nl, const C* __restrict__ tw, Src&& src, Dst&& dst) {
+  constexpr int NB = N / R;
+  const int total = nl * NB;
+  const FastDiv fd(nl > 0 ? nl : 1);
+  C v[MAXIT][R];
+#pragma unroll
+  for (int it = 0; it < MAXIT; ++it) {
+    const int w = threadIdx.x + it * NT;
+    if (w < total) {
+      int line, i;
+      if constexpr (MAP_ELEM) { line = w / NB; i = w - line * NB; }
+      else { i = (int)fd.div((uint32_t)w); line = w - i * nl; }
+#pragma unroll
+      for (int j = 0; j < R; ++j) v[it][j] = src(line, i + j * NB);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < MAXIT; ++it) {
+    const int w = threadIdx.x + it * NT;
+    if (w < total) {
+      int line, i;
+      if constexpr (MAP_ELEM) { line = w / NB; i = w - line * NB; }
+      else { i = (int)fd.div((uint32_t)w); line = w - i * nl; }
+      const int k = i % P;
+      if constexpr (P > 1) {
+        constexpr int STEP = N / (P * R);
+#pragma unroll
+        for (int j = 1; j < R; ++j) {
+          const C w_ = tw[j * k * STEP];
+          v[it][j] = (S > 0) ? cmul(v[it][j], w_) : cmulc(v[it][j], w_);
+        }
+      }
+      dft<R, S>(v[it]);
+      const int base = (i - k) * R + k;
+#pragma unroll
+      for (int j = 0; j < R; ++j) dst(line, base + j * P, v[it][j]);
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------- whole line FFT
+// Runs every pass of a length-N DFT on nl lines (nl * N <= NT * EPT).
+// first(line, e) reads the input, mid_ld / mid_st address the in-place
+// shared buffer used between passes, last(line, e, v) receives the output.
+template <int N, int REM, int P, int S, int NT, int EPT, bool MAP_ELEM, bool FIRST, typename C,
+          typename First, typename MidLd, typename MidSt, typename Last>
+__device__ __forceinline__ void fft_passes(int nl, const C* __restrict__ tw, First&& first,
+                                           MidLd&& mid_ld, MidSt&& mid_st, Last&& last) {
+  constexpr int R = first_radix<REM>::value;
+  static_assert(R != 0, "length must be 2^a 3^b 5^c");
+  constexpr int MAXIT = (EPT * NT / N * (N / R) + NT - 1) / NT;  // ceil(lines_max * N/R / NT)
+  constexpr bool LAST = (REM == R);
+  if constexpr (FIRST && LAST) {
+    stockham_pass<N, R, P, S, NT, MAXIT, MAP_ELEM, C>(nl, tw, first, last);
+  } else if constexpr (FIRST) {
+    stockham_pass<N, R, P, S, NT, MAXIT, MAP_ELEM, C>(nl, tw, first, mid_st);
+  } else if constexpr (LAST) {
+    stockham_pass<N, R, P, S, NT, MAXIT, MAP_ELEM, C>(nl, tw, mid_ld, last);
+  } else {
+    stockham_pass<N, R, P, S, NT, MAXIT, MAP_ELEM, C>(nl, tw, mid_ld, mid_st);
+  }
+  if constexpr (!LAST)
+    fft_passes<N, REM / R, P * R, S, NT, EPT, MAP_ELEM, false, C>(nl, tw, first, mid_ld, mid_st, last);
+}
+
+template <int N, int S, int NT, int EPT, bool MAP_ELEM, typename C, typename First, typename MidLd,
+          typename MidSt, typename Last>
+__device__ __forceinline__ void fft_lines(int nl, const C* __restrict__ tw, First&& first, MidLd&& mid_ld,
+                                          MidSt&& mid_st, Last&& last) {
+  fft_passes<N, N, 1, S, NT, EPT, MAP_ELEM, true, C>(nl, tw, first, mid_ld, mid_st, last);
+}
+
+// Lines of length N one pass-set can hold with NT threads and EPT elements each.
+template <int N, int NT, int EPT> struct lines_per_chunk {
+  static constexpr int value = (NT * EPT) / N;
+};
+
+__host__ __device__ constexpr int odd_pitch(int n) { return (n & 1) ? n : n + 1; }
+
+}  // namespace fftb

@@ -1,0 +1,555 @@
+// fftb_api.cpp -- the C ABI: plans (geometry, twiddles, device tables,
+// scratch) and the launch schedule of each direction.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fftb.h"
+#include "fftb_internal.h"
+#include "geometry.h"
+
+#define FFTB_EXPORT extern "C" __attribute__((visibility("default")))
+
+namespace fftb {
+
+template <typename T> size_t stick_smem_t(int);
+template <typename T> size_t plane_smem_t(int, int, int);
+template <typename T> int stick_tile_t(int);
+template <typename T> cudaError_t launch_stick_t(int, const Launch&, int);
+template <typename T> cudaError_t launch_plane_t(int, const Launch&);
+template <typename T> cudaError_t prepare_t(int, int, int, int);
+
+static const int kSizes[] = {12, 16, 20, 24, 32, 40, 48, 64, 96, 128, 160};
+
+bool grid_size_supported(int n) {
+  for (int s : kSizes)
+    if (s == n) return true;
+  return false;
+}
+bool plane_size_supported(int n0, int n1) { return n0 == n1 && grid_size_supported(n0); }
+size_t stick_smem(int prec, int n2) { return prec == P_F64 ? stick_smem_t<double>(n2) : stick_smem_t<float>(n2); }
+size_t plane_smem(int prec, int n0, int n1, int xmax) {
+  return prec == P_F64 ? plane_smem_t<double>(n0, n1, xmax) : plane_smem_t<float>(n0, n1, xmax);
+}
+int stick_tile(int prec, int n2) { return prec == P_F64 ? stick_tile_t<double>(n2) : stick_tile_t<float>(n2); }
+cudaError_t prepare_kernels(int prec, int n0, int n1, int n2, int xmax) {
+  return prec == P_F64 ? prepare_t<double>(n0, n1, n2, xmax) : prepare_t<float>(n0, n1, n2, xmax);
+}
+cudaError_t launch_stick(int prec, int mode, const Launch& L, int tiles) {
+  return prec == P_F64 ? launch_stick_t<double>(mode, L, tiles) : launch_stick_t<float>(mode, L, tiles);
+}
+cudaError_t launch_plane(int prec, int mode, const Launch& L) {
+  return prec == P_F64 ? launch_plane_t<double>(mode, L) : launch_plane_t<float>(mode, L);
+}
+
+static thread_local std::string g_last_error;
+
+static fftb_status fail(fftb_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+static fftb_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(FFTB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace fftb
+
+using namespace fftb;
+
+struct fftb_plan_s {
+  int32_t n[3];
+  int32_t nk;
+  fftb_direction dir;
+  fftb_precision prec;
+  int prec_kernel;  // P_F32 or P_F64
+  int32_t csize;    // bytes per complex element
+  std::vector<KGeom> geo;
+  std::vector<int32_t> bands;
+  int32_t total_bands = 0;
+  int64_t sphere_elems = 0, cube_elems = 0;
+  int32_t smax = 0, xmax = 0, tiles = 0, chunk = 1;
+  int device = 0;
+  // device memory
+  void* d_tables = nullptr;
+  size_t tables_bytes = 0;
+  void* d_T = nullptr;
+  size_t T_bytes = 0;
+  Geo g{};
+  const void* d_V = nullptr;
+  // host-buffer path staging (allocated on first use)
+  void* d_stage_in = nullptr;
+  void* d_stage_out = nullptr;
+  void* d_stage_cube = nullptr;
+  size_t stage_in_bytes = 0, stage_out_bytes = 0, stage_cube_bytes = 0;
+  int64_t launches = 0;
+  // per-kernel timing (fftb_plan_set_timing)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Rec { int kind; int a, b; };
+  std::vector<Rec> recs;
+  int ev_used = 0;
+};
+
+namespace {
+
+bool valid_direction(int d) { return d == FFTB_G_TO_R || d == FFTB_R_TO_G || d == FFTB_ROUNDTRIP || d == FFTB_APPLY_LOCAL; }
+
+template <typename T> void make_twiddles(int n, std::vector<unsigned char>& out) {
+  // e^{+2 pi j m / n}, m = 0..n-1, evaluated in double and rounded once.
+  out.resize(sizeof(T) * 2 * n);
+  T* p = reinterpret_cast<T*>(out.data());
+  for (int m = 0; m < n; ++m) {
+    const double a = 2.0 * M_PI * (double)m / (double)n;
+    p[2 * m] = (T)std::cos(a);
+    p[2 * m + 1] = (T)std::sin(a);
+  }
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+void release(fftb_plan_s* p) {
+  if (!p) return;
+  if (p->d_tables) cudaFree(p->d_tables);
+  if (p->d_T) cudaFree(p->d_T);
+  if (p->d_stage_in) cudaFree(p->d_stage_in);
+  if (p->d_stage_out) cudaFree(p->d_stage_out);
+  if (p->d_stage_cube) cudaFree(p->d_stage_cube);
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  delete p;
+}
+
+}  // namespace
+
+FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fftb_direction dir,
+                                         fftb_precision prec) {
+  if (!out) return fail(FFTB_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(FFTB_ERR_INVALID_ARG, "desc is NULL");
+  if (!valid_direction(dir)) return fail(FFTB_ERR_INVALID_ARG, "unknown direction");
+  if (prec != FFTB_FP64 && prec != FFTB_FP32 && prec != FFTB_MIXED_TC)
+    return fail(FFTB_ERR_INVALID_ARG, "unknown precision");
+  for (int i = 0; i < 3; ++i)
+    if (d->n[i] < 1) return fail(FFTB_ERR_INVALID_ARG, "grid extents must be >= 1");
+  if (d->n_kpoints < 1) return fail(FFTB_ERR_INVALID_ARG, "n_kpoints must be >= 1");
+  if (d->layout != 0) return fail(FFTB_ERR_UNSUPPORTED, "only the band-major layout (0) is implemented");
+  if (d->max_chunk_bands < 0) return fail(FFTB_ERR_INVALID_ARG, "max_chunk_bands must be >= 0");
+  if (d->g_list && !d->g_count) return fail(FFTB_ERR_INVALID_ARG, "g_list given without g_count");
+  if (prec == FFTB_MIXED_TC) return fail(FFTB_ERR_UNSUPPORTED, "MIXED_TC precision is not built yet");
+  if (!grid_size_supported(d->n[0]) || !grid_size_supported(d->n[1]) || !grid_size_supported(d->n[2]) ||
+      !plane_size_supported(d->n[0], d->n[1]))
+    return fail(FFTB_ERR_UNSUPPORTED,
+                "grid extents must be one of 12,16,20,24,32,40,48,64,96,128,160 with N0 == N1");
+
+  fftb_plan_s* p = new (std::nothrow) fftb_plan_s();
+  if (!p) return fail(FFTB_ERR_ALLOC, "host allocation failed");
+  std::memcpy(p->n, d->n, sizeof(p->n));
+  p->nk = d->n_kpoints;
+  p->dir = dir;
+  p->prec = prec;
+  p->prec_kernel = (prec == FFTB_FP64) ? P_F64 : P_F32;
+  p->csize = (prec == FFTB_FP64) ? 16 : 8;
+  p->geo.resize(p->nk);
+  p->bands.resize(p->nk);
+  const int64_t vol = (int64_t)d->n[0] * d->n[1] * d->n[2];
+  int64_t goff = 0;
+  for (int k = 0; k < p->nk; ++k) {
+    const int32_t b = d->bands ? d->bands[k] : 1;
+    if (b < 0) { release(p); return fail(FFTB_ERR_INVALID_ARG, "band counts must be >= 0"); }
+    p->bands[k] = b;
+    std::vector<int32_t> g;
+    std::string err;
+    const int32_t* gp;
+    int64_t ngw;
+    if (d->g_list) {
+      ngw = d->g_count[k];
+      if (ngw < 0) { release(p); return fail(FFTB_ERR_INVALID_ARG, "g_count must be >= 0"); }
+      gp = d->g_list + 3 * goff;
+      goff += ngw;
+    } else {
+      const double zero[3] = {0, 0, 0};
+      err = sphere_by_cutoff(d->n, d->radius, d->kshift ? d->kshift + 3 * k : zero, g);
+      if (!err.empty()) { release(p); return fail(FFTB_ERR_INVALID_ARG, "k-point " + std::to_string(k) + ": " + err); }
+      gp = g.data();
+      ngw = (int64_t)g.size() / 3;
+    }
+    err = build_geometry(d->n, gp, ngw, p->geo[k]);
+    if (!err.empty()) { release(p); return fail(FFTB_ERR_INVALID_ARG, "k-point " + std::to_string(k) + ": " + err); }
+    p->total_bands += b;
+    p->sphere_elems += (int64_t)b * ngw;
+    p->cube_elems += (int64_t)b * vol;
+    p->smax = std::max(p->smax, p->geo[k].S);
+    p->xmax = std::max(p->xmax, p->geo[k].X);
+  }
+  if (p->total_bands > 65535) { release(p); return fail(FFTB_ERR_UNSUPPORTED, "more than 65535 bands in one plan"); }
+
+  const size_t smem_limit = 227 * 1024;
+  if (stick_smem(p->prec_kernel, p->n[2]) > smem_limit ||
+      plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax) > smem_limit) {
+    release(p);
+    return fail(FFTB_ERR_UNSUPPORTED, "plane of this size and precision does not fit in shared memory");
+  }
+  const int ts = stick_tile(p->prec_kernel, p->n[2]);
+  p->tiles = p->smax > 0 ? (p->smax + ts - 1) / ts : 1;
+  const int32_t smax_pitch = std::max<int32_t>(p->smax, 1);
+
+  // band chunk: keep the stick buffer near 48 MB, or as requested
+  const size_t t_band = (size_t)p->n[2] * smax_pitch * p->csize;
+  int chunk = d->max_chunk_bands > 0 ? d->max_chunk_bands : (int)std::max<size_t>(1, (48u << 20) / t_band);
+  chunk = std::max(1, std::min(chunk, std::max(1, p->total_bands)));
+  p->chunk = chunk;
+
+  // ---- host tables
+  std::vector<int32_t> band_k, stick_ent, ent_pos, ent_zs, stick_xy;
+  std::vector<int64_t> band_sph;
+  std::vector<int16_t> xmap;
+  std::vector<KInfo> kinfo(p->nk);
+  int64_t sph = 0, ent_base = 0;
+  for (int k = 0; k < p->nk; ++k) {
+    const KGeom& G = p->geo[k];
+    for (int b = 0; b < p->bands[k]; ++b) {
+      band_k.push_back(k);
+      band_sph.push_back(sph + (int64_t)b * G.ngw);
+    }
+    sph += (int64_t)p->bands[k] * G.ngw;
+    kinfo[k].S = G.S;
+    kinfo[k].X = G.X;
+    kinfo[k].stick_base = (int32_t)stick_xy.size();
+    kinfo[k].xmap_base = (int32_t)xmap.size();
+    for (int32_t v : G.stick_ent) stick_ent.push_back((int32_t)(v + ent_base));
+    for (int32_t v : G.ent_pos) ent_pos.push_back(v);
+    for (int32_t v : G.ent_zs) ent_zs.push_back(v);
+    for (int32_t v : G.stick_xy) stick_xy.push_back(v);
+    for (int16_t v : G.xmap) xmap.push_back(v);
+    ent_base += G.ngw;
+  }
+  if (ent_base >= (int64_t(1) << 31)) { release(p); return fail(FFTB_ERR_UNSUPPORTED, "total sphere entries above 2^31"); }
+  if (band_k.empty()) { band_k.push_back(0); band_sph.push_back(0); }
+  if (ent_pos.empty()) { ent_pos.push_back(0); ent_zs.push_back(0); }
+  if (stick_xy.empty()) stick_xy.push_back(0);
+  std::vector<unsigned char> tw[3];
+  for (int dd = 0; dd < 3; ++dd) {
+    if (p->prec_kernel == P_F64) make_twiddles<double>(p->n[dd], tw[dd]);
+    else make_twiddles<float>(p->n[dd], tw[dd]);
+  }
+
+  struct Part { const void* src; size_t bytes; size_t off; };
+  std::vector<Part> parts = {
+      {band_k.data(), band_k.size() * 4, 0},       {band_sph.data(), band_sph.size() * 8, 0},
+      {kinfo.data(), kinfo.size() * sizeof(KInfo), 0}, {stick_ent.data(), stick_ent.size() * 4, 0},
+      {ent_pos.data(), ent_pos.size() * 4, 0},     {ent_zs.data(), ent_zs.size() * 4, 0},
+      {stick_xy.data(), stick_xy.size() * 4, 0},   {xmap.data(), xmap.size() * 2, 0},
+      {tw[0].data(), tw[0].size(), 0},             {tw[1].data(), tw[1].size(), 0},
+      {tw[2].data(), tw[2].size(), 0}};
+  size_t total = 0;
+  for (auto& pt : parts) {
+    pt.off = total;
+    total = align_up(total + pt.bytes, 256);
+  }
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) { release(p); return cuda_fail(e, "cudaGetDevice"); }
+  e = cudaMalloc(&p->d_tables, total);
+  if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaMalloc tables failed"); }
+  p->tables_bytes = total;
+  std::vector<unsigned char> blob(total, 0);
+  for (auto& pt : parts) std::memcpy(blob.data() + pt.off, pt.src, pt.bytes);
+  e = cudaMemcpy(p->d_tables, blob.data(), total, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { release(p); return cuda_fail(e, "cudaMemcpy tables"); }
+  unsigned char* base = static_cast<unsigned char*>(p->d_tables);
+  Geo& g = p->g;
+  g.band_k = reinterpret_cast<const int32_t*>(base + parts[0].off);
+  g.band_sph = reinterpret_cast<const int64_t*>(base + parts[1].off);
+  g.kinfo = reinterpret_cast<const KInfo*>(base + parts[2].off);
+  g.stick_ent = reinterpret_cast<const int32_t*>(base + parts[3].off);
+  g.ent_pos = reinterpret_cast<const int32_t*>(base + parts[4].off);
+  g.ent_zs = reinterpret_cast<const int32_t*>(base + parts[5].off);
+  g.stick_xy = reinterpret_cast<const int32_t*>(base + parts[6].off);
+  g.xmap = reinterpret_cast<const int16_t*>(base + parts[7].off);
+  g.tw0 = base + parts[8].off;
+  g.tw1 = base + parts[9].off;
+  g.tw2 = base + parts[10].off;
+  g.n0 = p->n[0];
+  g.n1 = p->n[1];
+  g.n2 = p->n[2];
+  g.smax = smax_pitch;
+  g.xmax = p->xmax;
+
+  p->T_bytes = (size_t)chunk * p->n[2] * smax_pitch * p->csize;
+  e = cudaMalloc(&p->d_T, p->T_bytes);
+  if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaMalloc stick scratch failed"); }
+  e = prepare_kernels(p->prec_kernel, p->n[0], p->n[1], p->n[2], p->xmax);
+  if (e != cudaSuccess) { release(p); return cuda_fail(e, "kernel attributes"); }
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) { release(p); return cuda_fail(e, "plan synchronise"); }
+  *out = p;
+  return FFTB_OK;
+}
+
+FFTB_EXPORT fftb_status fftb_plan_ngw(fftb_plan p, int32_t k, int64_t* ngw) {
+  if (!p || !ngw) return fail(FFTB_ERR_INVALID_ARG, "NULL argument");
+  if (k < 0 || k >= p->nk) return fail(FFTB_ERR_INVALID_ARG, "k-point out of range");
+  *ngw = p->geo[k].ngw;
+  return FFTB_OK;
+}
+
+FFTB_EXPORT fftb_status fftb_plan_sphere(fftb_plan p, int32_t k, int32_t* g_out) {
+  if (!p || !g_out) return fail(FFTB_ERR_INVALID_ARG, "NULL argument");
+  if (k < 0 || k >= p->nk) return fail(FFTB_ERR_INVALID_ARG, "k-point out of range");
+  if (!p->geo[k].g.empty()) std::memcpy(g_out, p->geo[k].g.data(), p->geo[k].g.size() * 4);
+  return FFTB_OK;
+}
+
+static int kernels_per_chunk(fftb_direction d) {
+  switch (d) {
+    case FFTB_G_TO_R: return 2;
+    case FFTB_R_TO_G: return 2;
+    case FFTB_ROUNDTRIP: return 4;
+    case FFTB_APPLY_LOCAL: return 3;
+  }
+  return 0;
+}
+
+FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) {
+  if (!p || !info) return fail(FFTB_ERR_INVALID_ARG, "NULL argument");
+  info->sphere_elems = p->sphere_elems;
+  info->cube_elems = p->cube_elems;
+  info->scratch_bytes = (int64_t)(p->T_bytes + p->tables_bytes);
+  info->total_bands = p->total_bands;
+  info->max_sticks = p->smax;
+  info->max_slabs = p->xmax;
+  info->chunk_bands = p->chunk;
+  const int nchunks = p->total_bands > 0 ? (p->total_bands + p->chunk - 1) / p->chunk : 0;
+  info->kernels_per_execute = nchunks * kernels_per_chunk(p->dir);
+  info->complex_bytes = p->csize;
+  return FFTB_OK;
+}
+
+FFTB_EXPORT fftb_status fftb_set_potential(fftb_plan p, const void* v) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (v && (reinterpret_cast<uintptr_t>(v) % (p->csize / 2)) != 0)
+    return fail(FFTB_ERR_INVALID_ARG, "potential pointer misaligned");
+  p->d_V = v;
+  return FFTB_OK;
+}
+
+enum StageKind { K_STICK_G2R = 0, K_PLANE_G2R = 1, K_PLANE_R2G = 2, K_STICK_R2G = 3, K_PLANE_APPLY = 4 };
+
+static cudaEvent_t next_event(fftb_plan_s* p, int* idx) {
+  if (p->ev_used == (int)p->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    p->ev_pool.push_back(e);
+  }
+  *idx = p->ev_used;
+  return p->ev_pool[p->ev_used++];
+}
+
+// Launches one stage kernel, bracketed by events when timing is enabled.
+static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
+  int a = -1, b = -1;
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (p->timing) {
+    ea = next_event(p, &a);
+    eb = next_event(p, &b);
+    if (!ea || !eb) return cudaErrorMemoryAllocation;
+    cudaEventRecord(ea, L.stream);
+  }
+  cudaError_t e;
+  const int pk = p->prec_kernel;
+  switch (kind) {
+    case K_STICK_G2R: e = launch_stick(pk, M_G2R, L, p->tiles); break;
+    case K_PLANE_G2R: e = launch_plane(pk, M_G2R, L); break;
+    case K_PLANE_R2G: e = launch_plane(pk, M_R2G, L); break;
+    case K_STICK_R2G: e = launch_stick(pk, M_R2G, L, p->tiles); break;
+    default: e = launch_plane(pk, M_APPLY, L); break;
+  }
+  if (e == cudaSuccess) ++p->launches;
+  if (p->timing) {
+    cudaEventRecord(eb, L.stream);
+    p->recs.push_back({kind, a, b});
+  }
+  return e;
+}
+
+static bool aligned(const void* q, int a) { return (reinterpret_cast<uintptr_t>(q) % (uintptr_t)a) == 0; }
+
+FFTB_EXPORT fftb_status fftb_execute(fftb_plan p, const void* in, void* out, void* cube, void* stream) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (p->total_bands == 0) return FFTB_OK;
+  if (!in || !out) return fail(FFTB_ERR_INVALID_ARG, "in and out must be device pointers");
+  if (!aligned(in, p->csize) || !aligned(out, p->csize) || (cube && !aligned(cube, p->csize)))
+    return fail(FFTB_ERR_INVALID_ARG, "buffers must be aligned to the complex element size");
+  if (in == out) return fail(FFTB_ERR_INVALID_ARG, "in and out must not overlap");
+  if (p->dir == FFTB_ROUNDTRIP && !cube) return fail(FFTB_ERR_INVALID_ARG, "ROUNDTRIP needs a cube buffer");
+  if (p->dir != FFTB_ROUNDTRIP && cube) return fail(FFTB_ERR_INVALID_ARG, "cube buffer only for ROUNDTRIP");
+  if (p->dir == FFTB_APPLY_LOCAL && !p->d_V) return fail(FFTB_ERR_INVALID_ARG, "APPLY_LOCAL needs fftb_set_potential");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != p->device) return fail(FFTB_ERR_INVALID_ARG, "current device differs from the plan's device");
+
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Launch L{};
+  L.g = p->g;
+  L.T = p->d_T;
+  L.V = p->d_V;
+  L.stream = s;
+  for (int b0 = 0; b0 < p->total_bands; b0 += p->chunk) {
+    L.band0 = b0;
+    L.nb = std::min(p->chunk, p->total_bands - b0);
+    cudaError_t e = cudaSuccess;
+    switch (p->dir) {
+      case FFTB_G_TO_R:
+        L.sph_in = in;
+        L.cube_out = out;
+        e = stage(p, K_STICK_G2R, L);
+        if (e == cudaSuccess) e = stage(p, K_PLANE_G2R, L);
+        break;
+      case FFTB_R_TO_G:
+        L.cube_in = in;
+        L.sph_out = out;
+        e = stage(p, K_PLANE_R2G, L);
+        if (e == cudaSuccess) e = stage(p, K_STICK_R2G, L);
+        break;
+      case FFTB_ROUNDTRIP:
+        L.sph_in = in;
+        L.cube_out = cube;
+        L.cube_in = cube;
+        L.sph_out = out;
+        e = stage(p, K_STICK_G2R, L);
+        if (e == cudaSuccess) e = stage(p, K_PLANE_G2R, L);
+        if (e == cudaSuccess) e = stage(p, K_PLANE_R2G, L);
+        if (e == cudaSuccess) e = stage(p, K_STICK_R2G, L);
+        break;
+      case FFTB_APPLY_LOCAL:
+        L.sph_in = in;
+        L.sph_out = out;
+        e = stage(p, K_STICK_G2R, L);
+        if (e == cudaSuccess) e = stage(p, K_PLANE_APPLY, L);
+        if (e == cudaSuccess) e = stage(p, K_STICK_R2G, L);
+        break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  }
+  return FFTB_OK;
+}
+
+static fftb_status ensure(void** ptr, size_t* have, size_t need) {
+  if (*have >= need && *ptr) return FFTB_OK;
+  if (*ptr) cudaFree(*ptr);
+  *ptr = nullptr;
+  *have = 0;
+  if (cudaMalloc(ptr, need ? need : 16) != cudaSuccess) return fail(FFTB_ERR_ALLOC, "cudaMalloc staging failed");
+  *have = need;
+  return FFTB_OK;
+}
+
+FFTB_EXPORT fftb_status fftb_execute_host(fftb_plan p, const void* in_host, void* out_host, void* cube_dev,
+                                          void* stream) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (!in_host || !out_host) return fail(FFTB_ERR_INVALID_ARG, "in_host and out_host must be given");
+  const size_t sph_b = (size_t)p->sphere_elems * p->csize, cube_b = (size_t)p->cube_elems * p->csize;
+  size_t in_b = sph_b, out_b = sph_b;
+  if (p->dir == FFTB_G_TO_R) out_b = cube_b;
+  if (p->dir == FFTB_R_TO_G) in_b = cube_b;
+  fftb_status st = ensure(&p->d_stage_in, &p->stage_in_bytes, in_b);
+  if (st == FFTB_OK) st = ensure(&p->d_stage_out, &p->stage_out_bytes, out_b);
+  if (st == FFTB_OK && p->dir == FFTB_ROUNDTRIP && !cube_dev) {
+    st = ensure(&p->d_stage_cube, &p->stage_cube_bytes, cube_b);
+    cube_dev = p->d_stage_cube;
+  }
+  if (st != FFTB_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(p->d_stage_in, in_host, in_b, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "copy in");
+  st = fftb_execute(p, p->d_stage_in, p->d_stage_out, p->dir == FFTB_ROUNDTRIP ? cube_dev : nullptr, stream);
+  if (st != FFTB_OK) return st;
+  e = cudaMemcpyAsync(out_host, p->d_stage_out, out_b, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "copy out");
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
+  return FFTB_OK;
+}
+
+FFTB_EXPORT int64_t fftb_plan_launches(fftb_plan p) { return p ? p->launches : -1; }
+
+FFTB_EXPORT fftb_status fftb_destroy(fftb_plan p) {
+  release(p);
+  return FFTB_OK;
+}
+
+FFTB_EXPORT const char* fftb_error_string(fftb_status s) {
+  switch (s) {
+    case FFTB_OK: return "success";
+    case FFTB_ERR_INVALID_ARG: return "invalid argument";
+    case FFTB_ERR_UNSUPPORTED: return "unsupported request";
+    case FFTB_ERR_ALLOC: return "allocation failed";
+    case FFTB_ERR_CUDA: return "CUDA error";
+    case FFTB_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+  }
+  return "unknown status";
+}
+
+FFTB_EXPORT const char* fftb_last_error(void) { return g_last_error.c_str(); }
+
+FFTB_EXPORT const char* fftb_version(void) { return "fftb-gb300 0.1 (sm_103a)"; }
+
+FFTB_EXPORT fftb_status fftb_sphere_enumerate(const int32_t n[3], double radius, const double* kshift,
+                                              int32_t* g_out, int64_t capacity, int64_t* ngw) {
+  if (!n || !ngw) return fail(FFTB_ERR_INVALID_ARG, "NULL argument");
+  for (int i = 0; i < 3; ++i)
+    if (n[i] < 1) return fail(FFTB_ERR_INVALID_ARG, "grid extents must be >= 1");
+  const double zero[3] = {0, 0, 0};
+  std::vector<int32_t> g;
+  const std::string err = sphere_by_cutoff(n, radius, kshift ? kshift : zero, g);
+  if (!err.empty()) return fail(FFTB_ERR_INVALID_ARG, err);
+  *ngw = (int64_t)g.size() / 3;
+  if (g_out && capacity > 0) {
+    const int64_t m = std::min<int64_t>(capacity, *ngw);
+    std::memcpy(g_out, g.data(), (size_t)m * 3 * sizeof(int32_t));
+  }
+  return FFTB_OK;
+}
+
+FFTB_EXPORT fftb_status fftb_sphere_sticks(const int32_t n[3], const int32_t* g, int64_t ngw,
+                                           int32_t* n_sticks, int32_t* n_slabs) {
+  if (!n || (!g && ngw > 0) || !n_sticks || !n_slabs) return fail(FFTB_ERR_INVALID_ARG, "NULL argument");
+  for (int i = 0; i < 3; ++i)
+    if (n[i] < 1) return fail(FFTB_ERR_INVALID_ARG, "grid extents must be >= 1");
+  KGeom geo;
+  const std::string err = build_geometry(n, g, ngw, geo);
+  if (!err.empty()) return fail(FFTB_ERR_INVALID_ARG, err);
+  *n_sticks = geo.S;
+  *n_slabs = geo.X;
+  return FFTB_OK;
+}
+
+FFTB_EXPORT fftb_status fftb_plan_set_timing(fftb_plan p, int32_t enable) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  p->timing = enable != 0;
+  return FFTB_OK;
+}
+
+FFTB_EXPORT fftb_status fftb_plan_stage_times(fftb_plan p, double* ms, int64_t* launches) {
+  if (!p || !ms || !launches) return fail(FFTB_ERR_INVALID_ARG, "NULL argument");
+  for (int i = 0; i < FFTB_STAGE_KINDS; ++i) {
+    ms[i] = 0.0;
+    launches[i] = 0;
+  }
+  for (const auto& r : p->recs) {
+    cudaError_t e = cudaEventSynchronize(p->ev_pool[r.b]);
+    if (e != cudaSuccess) return cuda_fail(e, "event synchronise");
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, p->ev_pool[r.a], p->ev_pool[r.b]);
+    if (e != cudaSuccess) return cuda_fail(e, "event elapsed time");
+    ms[r.kind] += t;
+    launches[r.kind] += 1;
+  }
+  p->recs.clear();
+  p->ev_used = 0;
+  return FFTB_OK;
+}

@@ -1,0 +1,66 @@
+// fftb_internal.h -- host-side types shared by the plan code and the kernel
+// launchers. No CUDA templates here; the .cu files own the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace fftb {
+
+// Per-k-point geometry as the kernels see it.
+struct KInfo {
+  int32_t S;           // occupied (x,y) sticks
+  int32_t X;           // occupied x values (y-z slabs)
+  int32_t stick_base;  // first entry of this k in stick_xy; stick_ent uses stick_base + k
+  int32_t xmap_base;   // first entry of this k in xmap (k * N0)
+};
+
+// Device tables for all k-points (concatenated) plus twiddles.
+struct Geo {
+  const int32_t* band_k;     // [total_bands] k-point of each band
+  const int64_t* band_sph;   // [total_bands] offset of each band's sphere (complex elements)
+  const KInfo* kinfo;        // [n_k]
+  const int32_t* stick_ent;  // [sum(S_k + 1)] global entry offset of each stick (CSR)
+  const int32_t* ent_pos;    // [sum ngw] position of the entry within its k's sphere list
+  const int32_t* ent_zs;     // [sum ngw] (z index << 24) | local stick index
+  const int32_t* stick_xy;   // [sum S_k] (xi << 16) | y index
+  const int16_t* xmap;       // [n_k * N0] slab index of x, or -1
+  const void* tw0;           // [N0] e^{+2 pi j m / N0} in the plan's real type
+  const void* tw1;           // [N1]
+  const void* tw2;           // [N2]
+  int32_t n0, n1, n2;
+  int32_t smax;              // T pitch (max sticks over k)
+  int32_t xmax;              // max slabs over k
+};
+
+// One launch over the bands [band0, band0 + nb).
+struct Launch {
+  Geo g;
+  int32_t band0, nb;
+  const void* sph_in;   // sphere batch read by the z-stage (G -> r)
+  void* sph_out;        // sphere batch written by the z-stage (r -> G)
+  const void* cube_in;  // cube batch read by the plane stage (r -> G)
+  void* cube_out;       // cube batch written by the plane stage (G -> r)
+  void* T;              // stick scratch [nb][N2][smax]
+  const void* V;        // potential (apply)
+  cudaStream_t stream;
+};
+
+enum Prec { P_F64 = 0, P_F32 = 1 };
+enum Mode { M_G2R = 1, M_R2G = -1, M_APPLY = 2 };
+
+bool grid_size_supported(int n);
+bool plane_size_supported(int n0, int n1);
+// Dynamic shared memory (bytes) of each kernel for one k geometry.
+size_t stick_smem(int prec, int n2);
+size_t plane_smem(int prec, int n0, int n1, int xmax);
+int stick_tile(int prec, int n2);
+// Raise the dynamic shared-memory limit of the kernels a plan uses.
+cudaError_t prepare_kernels(int prec, int n0, int n1, int n2, int xmax);
+cudaError_t launch_stick(int prec, int mode, const Launch& L, int tiles);
+cudaError_t launch_plane(int prec, int mode, const Launch& L);
+
+}  // namespace fftb

@@ -1,0 +1,37 @@
+// geometry.h -- host-side sphere enumeration and stick / slab tables.
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace fftb {
+
+// One k-point's sphere and the tables the kernels index it with.
+//   entries are the sphere's G sorted by stick (gy, then gx) and then gz
+//   (the CSR-over-xy offset array of Sec. 3.3 / Fig. 6);
+//   stick_ent[s] .. stick_ent[s+1] are the entries of stick s (S + 1 values);
+//   ent_pos[j] is entry j's position in the caller's sphere list;
+//   ent_zs[j]  = (gz mod N2) << 24 | s;
+//   stick_xy[s] = xi << 16 | (gy mod N1), xi = rank of gx among occupied x;
+//   xmap[x] = xi of x = gx mod N0, or -1 for an empty x-slab.
+struct KGeom {
+  int64_t ngw = 0;
+  std::vector<int32_t> g;  // ngw * 3, the caller's order
+  int32_t S = 0, X = 0;
+  std::vector<int32_t> stick_ent, ent_pos, ent_zs, stick_xy;
+  std::vector<int16_t> xmap;
+};
+
+// Cutoff sphere |G + k| <= r (Sec. 2.2), components in [-N/2, N/2), in
+// canonical order (gy, gx, gz ascending). Returns "" or an error message
+// (the sphere does not fit the grid and would alias).
+std::string sphere_by_cutoff(const int32_t n[3], double radius, const double k[3],
+                             std::vector<int32_t>& g);
+
+// Builds the tables for a sphere given as ngw (gx,gy,gz) triples. Returns ""
+// or an error message (component out of range, duplicate G, size limit).
+std::string build_geometry(const int32_t n[3], const int32_t* g, int64_t ngw, KGeom& out);
+
+}  // namespace fftb

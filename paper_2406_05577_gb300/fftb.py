@@ -1,0 +1,315 @@
+"""ctypes binding of libfftb.so (the C ABI in include/fftb.h).
+
+Argument marshalling only: every step of the transform runs in the library's
+CUDA kernels. The functions keep the C names; ``Plan`` wraps a plan handle
+and accepts torch tensors (device memory and streams come from PyTorch).
+The library must be built (``paper_2406_05577_gb300.build.build()``); if it
+is missing, loading raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfftb.so")
+
+FFTB_OK, FFTB_ERR_INVALID_ARG, FFTB_ERR_UNSUPPORTED, FFTB_ERR_ALLOC, FFTB_ERR_CUDA, \
+    FFTB_ERR_DEVICE_TIMEOUT = range(6)
+FFTB_G_TO_R, FFTB_R_TO_G, FFTB_ROUNDTRIP, FFTB_APPLY_LOCAL = 1, -1, 0, 2
+FFTB_FP64, FFTB_FP32, FFTB_MIXED_TC = 0, 1, 2
+
+DIRECTIONS = {"g2r": FFTB_G_TO_R, "r2g": FFTB_R_TO_G, "roundtrip": FFTB_ROUNDTRIP,
+              "apply": FFTB_APPLY_LOCAL}
+PRECISIONS = {"fp64": FFTB_FP64, "fp32": FFTB_FP32, "mixed": FFTB_MIXED_TC}
+
+
+class fftb_desc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32 * 3),
+        ("n_kpoints", ctypes.c_int32),
+        ("bands", ctypes.POINTER(ctypes.c_int32)),
+        ("radius", ctypes.c_double),
+        ("kshift", ctypes.POINTER(ctypes.c_double)),
+        ("g_list", ctypes.POINTER(ctypes.c_int32)),
+        ("g_count", ctypes.POINTER(ctypes.c_int64)),
+        ("layout", ctypes.c_int32),
+        ("max_chunk_bands", ctypes.c_int32),
+    ]
+
+
+class fftb_plan_info_t(ctypes.Structure):
+    _fields_ = [
+        ("sphere_elems", ctypes.c_int64),
+        ("cube_elems", ctypes.c_int64),
+        ("scratch_bytes", ctypes.c_int64),
+        ("total_bands", ctypes.c_int32),
+        ("max_sticks", ctypes.c_int32),
+        ("max_slabs", ctypes.c_int32),
+        ("chunk_bands", ctypes.c_int32),
+        ("kernels_per_execute", ctypes.c_int32),
+        ("complex_bytes", ctypes.c_int32),
+    ]
+
+
+EXPORTS = {
+    "fftb_plan_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(fftb_desc),
+                                        ctypes.c_int, ctypes.c_int]),
+    "fftb_plan_ngw": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
+    "fftb_plan_sphere": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "fftb_plan_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fftb_plan_info_t)]),
+    "fftb_set_potential": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "fftb_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "fftb_execute_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "fftb_plan_launches": (ctypes.c_int64, [ctypes.c_void_p]),
+    "fftb_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "fftb_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "fftb_last_error": (ctypes.c_char_p, []),
+    "fftb_version": (ctypes.c_char_p, []),
+    "fftb_plan_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "fftb_plan_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "fftb_sphere_enumerate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_double,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                             ctypes.POINTER(ctypes.c_int64)]),
+    "fftb_sphere_sticks": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32)]),
+}
+
+_lib = None
+
+
+def lib():
+    """Loads libfftb.so once; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2406_05577_gb300.build.build()")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+class FFTBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def _check(status):
+    if status != FFTB_OK:
+        L = lib()
+        detail = L.fftb_last_error().decode()
+        raise FFTBError(status, f"{L.fftb_error_string(status).decode()}: {detail}")
+
+
+# ------------------------------------------------------------ C-named calls
+
+def fftb_plan_create(n, direction, precision, radius=0.0, kshift=None, bands=None,
+                     g_lists=None, max_chunk_bands=0, layout=0):
+    """Returns a plan handle (int). n = (N0, N1, N2); kshift (nk, 3);
+    bands (nk,); g_lists: list of (ngw_k, 3) int arrays (explicit spheres)."""
+    L = lib()
+    if isinstance(direction, str):
+        direction = DIRECTIONS[direction]
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    nk = 1
+    if g_lists is not None:
+        nk = len(g_lists)
+    elif kshift is not None:
+        nk = int(np.asarray(kshift).reshape(-1, 3).shape[0])
+    elif bands is not None:
+        nk = len(bands)
+    d = fftb_desc()
+    d.n[0], d.n[1], d.n[2] = (int(v) for v in n)
+    d.n_kpoints = nk
+    d.radius = float(radius)
+    d.layout = int(layout)
+    d.max_chunk_bands = int(max_chunk_bands)
+    keep = []
+    if bands is not None:
+        b = np.ascontiguousarray(np.asarray(bands, dtype=np.int32).reshape(-1))
+        keep.append(b)
+        d.bands = b.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    if kshift is not None:
+        k = np.ascontiguousarray(np.asarray(kshift, dtype=np.float64).reshape(-1))
+        keep.append(k)
+        d.kshift = k.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if g_lists is not None:
+        parts = [np.asarray(g, dtype=np.int32).reshape(-1, 3) for g in g_lists]
+        gl = np.ascontiguousarray(np.concatenate(parts, axis=0) if parts else np.zeros((0, 3), np.int32))
+        gc = np.ascontiguousarray(np.array([len(p) for p in parts], dtype=np.int64))
+        if gl.size == 0:
+            gl = np.zeros(3, np.int32)  # non-NULL pointer for empty spheres
+        keep += [gl, gc]
+        d.g_list = gl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.g_count = gc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    h = ctypes.c_void_p()
+    _check(L.fftb_plan_create(ctypes.byref(h), ctypes.byref(d), int(direction), int(precision)))
+    return h.value
+
+
+def fftb_plan_ngw(plan, kpoint):
+    v = ctypes.c_int64()
+    _check(lib().fftb_plan_ngw(plan, int(kpoint), ctypes.byref(v)))
+    return v.value
+
+
+def fftb_plan_sphere(plan, kpoint):
+    ngw = fftb_plan_ngw(plan, kpoint)
+    out = np.zeros((max(ngw, 1), 3), dtype=np.int32)
+    _check(lib().fftb_plan_sphere(plan, int(kpoint), out.ctypes.data))
+    return out[:ngw]
+
+
+def fftb_plan_get_info(plan):
+    info = fftb_plan_info_t()
+    _check(lib().fftb_plan_get_info(plan, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in fftb_plan_info_t._fields_}
+
+
+def fftb_set_potential(plan, v_ptr):
+    _check(lib().fftb_set_potential(plan, v_ptr))
+
+
+def fftb_execute(plan, in_ptr, out_ptr, cube_ptr=None, stream=None):
+    _check(lib().fftb_execute(plan, in_ptr, out_ptr, cube_ptr, stream))
+
+
+def fftb_execute_host(plan, in_host_ptr, out_host_ptr, cube_ptr=None, stream=None):
+    _check(lib().fftb_execute_host(plan, in_host_ptr, out_host_ptr, cube_ptr, stream))
+
+
+STAGE_KINDS = ("stick_g2r", "plane_g2r", "plane_r2g", "stick_r2g", "plane_apply")
+
+
+def fftb_plan_set_timing(plan, enable):
+    _check(lib().fftb_plan_set_timing(plan, 1 if enable else 0))
+
+
+def fftb_plan_stage_times(plan):
+    """{kind: (ms, launches)} since the previous query (waits for the events)."""
+    ms = np.zeros(len(STAGE_KINDS), np.float64)
+    cnt = np.zeros(len(STAGE_KINDS), np.int64)
+    _check(lib().fftb_plan_stage_times(plan, ms.ctypes.data, cnt.ctypes.data))
+    return {k: (float(m), int(c)) for k, m, c in zip(STAGE_KINDS, ms, cnt)}
+
+
+def fftb_plan_launches(plan):
+    return int(lib().fftb_plan_launches(plan))
+
+
+def fftb_destroy(plan):
+    if plan:
+        _check(lib().fftb_destroy(plan))
+
+
+def fftb_sphere_enumerate(n, radius, kshift=None):
+    """Cutoff sphere in canonical order, (ngw, 3) int32 (host only)."""
+    L = lib()
+    nn = (ctypes.c_int32 * 3)(*[int(v) for v in n])
+    k = None if kshift is None else np.ascontiguousarray(np.asarray(kshift, np.float64).reshape(3))
+    kp = None if k is None else k.ctypes.data
+    cnt = ctypes.c_int64()
+    _check(L.fftb_sphere_enumerate(nn, float(radius), kp, None, 0, ctypes.byref(cnt)))
+    out = np.zeros((max(cnt.value, 1), 3), np.int32)
+    _check(L.fftb_sphere_enumerate(nn, float(radius), kp, out.ctypes.data, cnt.value, ctypes.byref(cnt)))
+    return out[:cnt.value]
+
+
+def fftb_sphere_sticks(n, g):
+    """(n_sticks, n_slabs) of an explicit sphere (host only)."""
+    L = lib()
+    nn = (ctypes.c_int32 * 3)(*[int(v) for v in n])
+    gg = np.ascontiguousarray(np.asarray(g, np.int32).reshape(-1, 3))
+    s, x = ctypes.c_int32(), ctypes.c_int32()
+    _check(L.fftb_sphere_sticks(nn, gg.ctypes.data if gg.size else None, len(gg),
+                                ctypes.byref(s), ctypes.byref(x)))
+    return s.value, x.value
+
+
+def fftb_version():
+    return lib().fftb_version().decode()
+
+
+# -------------------------------------------------------- torch convenience
+
+class Plan:
+    """Owns one plan handle; execute() takes torch tensors on the plan's GPU."""
+
+    def __init__(self, n, direction, precision, **kw):
+        self.n = tuple(int(v) for v in n)
+        self.direction = DIRECTIONS[direction] if isinstance(direction, str) else direction
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
+        self.handle = fftb_plan_create(self.n, self.direction, self.precision, **kw)
+        self.info = fftb_plan_get_info(self.handle)
+        self.nk = kw.get("g_lists") and len(kw["g_lists"]) or (
+            np.asarray(kw["kshift"]).reshape(-1, 3).shape[0] if kw.get("kshift") is not None
+            else (len(kw["bands"]) if kw.get("bands") is not None else 1))
+        self._v = None
+
+    @property
+    def complex_dtype(self):
+        import torch
+        return torch.complex128 if self.precision == FFTB_FP64 else torch.complex64
+
+    @property
+    def real_dtype(self):
+        import torch
+        return torch.float64 if self.precision == FFTB_FP64 else torch.float32
+
+    def ngw(self, k=0):
+        return fftb_plan_ngw(self.handle, k)
+
+    def sphere(self, k=0):
+        return fftb_plan_sphere(self.handle, k)
+
+    def _ptr(self, t, dtype, numel, what):
+        if t is None:
+            return None
+        if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+            raise ValueError(f"{what}: need a contiguous CUDA tensor of {dtype}")
+        if t.numel() < numel:
+            raise ValueError(f"{what}: need at least {numel} elements, got {t.numel()}")
+        return t.data_ptr()
+
+    def set_potential(self, v):
+        n0, n1, n2 = self.n
+        fftb_set_potential(self.handle, self._ptr(v, self.real_dtype, n0 * n1 * n2, "potential"))
+        self._v = v  # keep it alive while the plan may use it
+
+    def execute(self, x, out, cube=None, stream=None):
+        import torch
+        sph, cub = self.info["sphere_elems"], self.info["cube_elems"]
+        nin, nout = sph, sph
+        if self.direction == FFTB_G_TO_R:
+            nout = cub
+        elif self.direction == FFTB_R_TO_G:
+            nin = cub
+        cd = self.complex_dtype
+        s = stream if stream is not None else torch.cuda.current_stream()
+        fftb_execute(self.handle, self._ptr(x, cd, nin, "in"), self._ptr(out, cd, nout, "out"),
+                     self._ptr(cube, cd, cub, "cube"), s.cuda_stream)
+
+    def launches(self):
+        return fftb_plan_launches(self.handle)
+
+    def close(self):
+        if self.handle:
+            fftb_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

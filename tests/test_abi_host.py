@@ -1,0 +1,111 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+symbol include/fftb.h declares, enumerates spheres bit-exactly like the
+oracle's independent enumerator, and rejects bad plans with status codes."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import fftb_inputs as fi
+from oracle import sphere_gvectors
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fftb():
+    from paper_2406_05577_gb300 import build
+    build.build()
+    from paper_2406_05577_gb300 import fftb as mod
+    return mod
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "fftb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fftb_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(fftb):
+    names = declared_functions()
+    assert "fftb_plan_create" in names and "fftb_execute" in names
+    lib = fftb.lib()
+    for name in names:
+        assert hasattr(lib, name), name
+    # and the binding covers them with the same names
+    assert set(names) <= set(fftb.EXPORTS)
+
+
+@pytest.mark.parametrize("n,r", [((24, 24, 24), 6.0), ((64, 64, 64), 16.0), ((32, 32, 48), 10.0),
+                                 ((20, 20, 40), 6.5), ((12, 12, 16), 3.0), ((160, 160, 160), 40.0)])
+def test_sphere_matches_oracle_bit_exact(fftb, n, r):
+    got = fftb.fftb_sphere_enumerate(n, r)
+    want = sphere_gvectors(n, r)
+    assert got.dtype == np.int32 and np.array_equal(got, want)
+
+
+def test_kshift_spheres_match_oracle(fftb):
+    ks = fi.kshifts(8, seed=3)
+    counts = []
+    for k in ks:
+        got = fftb.fftb_sphere_enumerate((96, 96, 96), 24.0, k)
+        want = sphere_gvectors((96, 96, 96), 24.0, k)
+        assert np.array_equal(got, want)
+        counts.append(len(got))
+    assert len(set(counts)) > 1  # uneven sphere sizes across k-points
+
+
+@pytest.mark.parametrize("n,r,sticks,slabs", [((24, 24, 24), 6.0, 113, 13), ((64, 64, 64), 16.0, 797, 33),
+                                              ((128, 128, 128), 32.0, 3209, 65),
+                                              ((160, 160, 160), 40.0, 5025, 81)])
+def test_stick_and_slab_counts(fftb, n, r, sticks, slabs):
+    g = sphere_gvectors(n, r)
+    # independent count from the oracle's list
+    assert len({(a, b) for a, b, _ in g.tolist()}) == sticks
+    assert len({a for a, _, _ in g.tolist()}) == slabs
+    assert fftb.fftb_sphere_sticks(n, g) == (sticks, slabs)
+
+
+def test_explicit_list_errors(fftb):
+    g = sphere_gvectors((24, 24, 24), 6.0)
+    dup = np.concatenate([g, g[:1]])
+    with pytest.raises(fftb.FFTBError) as e:
+        fftb.fftb_sphere_sticks((24, 24, 24), dup)
+    assert e.value.status == fftb.FFTB_ERR_INVALID_ARG and "duplicate" in str(e.value)
+    bad = g.copy()
+    bad[0] = [12, 0, 0]  # outside [-12, 12)
+    with pytest.raises(fftb.FFTBError):
+        fftb.fftb_sphere_sticks((24, 24, 24), bad)
+    assert fftb.fftb_sphere_sticks((24, 24, 24), np.zeros((0, 3), np.int32)) == (0, 0)
+
+
+def test_plan_errors_before_device(fftb):
+    E = fftb.FFTBError
+    with pytest.raises(E) as e:
+        fftb.fftb_plan_create((64, 64, 50), "roundtrip", "fp32", radius=16.0)
+    assert e.value.status == fftb.FFTB_ERR_UNSUPPORTED
+    with pytest.raises(E) as e:
+        fftb.fftb_plan_create((24, 24, 24), "roundtrip", "fp32", radius=12.0)  # aliases
+    assert e.value.status == fftb.FFTB_ERR_INVALID_ARG
+    with pytest.raises(E) as e:
+        fftb.fftb_plan_create((24, 24, 24), "roundtrip", "fp32", radius=6.0, bands=[-1])
+    assert e.value.status == fftb.FFTB_ERR_INVALID_ARG
+    with pytest.raises(E) as e:
+        fftb.fftb_plan_create((24, 24, 24), "roundtrip", "fp32", radius=6.0, layout=1)
+    assert e.value.status == fftb.FFTB_ERR_UNSUPPORTED
+    with pytest.raises(E) as e:
+        fftb.fftb_plan_create((24, 24, 24), 7, "fp32", radius=6.0)
+    assert e.value.status == fftb.FFTB_ERR_INVALID_ARG
+    g = sphere_gvectors((24, 24, 24), 6.0)
+    with pytest.raises(E) as e:
+        fftb.fftb_plan_create((24, 24, 24), "g2r", "fp64", g_lists=[np.concatenate([g, g[:2]])])
+    assert "duplicate" in str(e.value)
+
+
+def test_sphere_enumerate_rejects_alias(fftb):
+    with pytest.raises(fftb.FFTBError):
+        fftb.fftb_sphere_enumerate((24, 24, 24), 12.0)
+    with pytest.raises(fftb.FFTBError):
+        fftb.fftb_sphere_enumerate((24, 24, 16), 8.5)
+    assert len(fftb.fftb_sphere_enumerate((25, 25, 25), 12.0)) == len(sphere_gvectors((25, 25, 25), 12.0))

@@ -1,0 +1,196 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative L2 over the whole output batch): FP64 <= 1e-12,
+FP32 <= 2e-6. Inputs are rounded to the plan's precision first and the
+oracle sees the rounded values widened to float64, so input rounding is not
+charged to the transform.
+"""
+import numpy as np
+import pytest
+
+import fftb_inputs as fi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 2e-6}
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    from paper_2406_05577_gb300 import build
+    build.build()
+    from paper_2406_05577_gb300 import fftb
+    assert torch.cuda.is_available()
+    return fftb
+
+
+def relerr(a, b):
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def to_dev(x, prec):
+    import torch
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dt).cuda()
+
+
+def rounded(x, prec):
+    return x.astype(np.complex128 if prec == "fp64" else np.complex64).astype(np.complex128)
+
+
+def sphere_batch(ngws, bands, seed, prec):
+    parts = [rounded(fi.complex_gaussian((b, n), seed + 17 * k), prec)
+             for k, (n, b) in enumerate(zip(ngws, bands))]
+    return parts
+
+
+def run_plan(F, n, direction, prec, x_host, **kw):
+    import torch
+    plan = F.Plan(n, direction, prec, **kw)
+    info = plan.info
+    cd = plan.complex_dtype
+    x = to_dev(x_host, prec)
+    if direction == "g2r":
+        out = torch.empty(info["cube_elems"], dtype=cd, device="cuda")
+    else:
+        out = torch.empty(info["sphere_elems"], dtype=cd, device="cuda")
+    cube = None
+    if direction == "roundtrip":
+        cube = torch.empty(info["cube_elems"], dtype=cd, device="cuda")
+    plan.execute(x, out, cube)
+    torch.cuda.synchronize()
+    res = out.cpu().numpy().astype(np.complex128)
+    cube_np = cube.cpu().numpy().astype(np.complex128) if cube is not None else None
+    return plan, res, cube_np
+
+
+CASES = [
+    # (grid, radius, kshift)
+    ((24, 24, 24), 6.0, None),
+    ((32, 32, 48), 10.0, (0.25, -0.4, 0.1)),
+    ((20, 20, 40), 6.5, (-0.5, 0.3, 0.45)),
+    ((12, 12, 16), 3.0, (0.1, 0.2, -0.3)),
+    ((48, 48, 24), 9.0, None),
+    ((16, 16, 96), 4.5, (0.0, 0.5, -0.25)),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,r,k", CASES)
+def test_g2r_r2g_roundtrip_vs_oracle(F, n, r, k, prec):
+    bands = 5
+    g = oracle.sphere_gvectors(n, r, k if k else (0, 0, 0))
+    c = sphere_batch([len(g)], [bands], seed=31, prec=prec)[0]
+    kw = dict(radius=r, bands=[bands])
+    if k:
+        kw["kshift"] = [k]
+    # G -> r
+    plan, cube, _ = run_plan(F, n, "g2r", prec, c, **kw)
+    assert np.array_equal(plan.sphere(0), g)
+    want = oracle.g2r(g, c, n).reshape(-1)
+    assert relerr(cube, want) <= TOL[prec]
+    # r -> G on an independent random cube
+    R = rounded(fi.complex_gaussian((bands, n[2], n[1], n[0]), 32), prec)
+    _, sph, _ = run_plan(F, n, "r2g", prec, R, **kw)
+    assert relerr(sph, oracle.r2g(g, R, n).reshape(-1)) <= TOL[prec]
+    # round trip keeps the cube and returns N0 N1 N2 * c
+    _, back, cub = run_plan(F, n, "roundtrip", prec, c, **kw)
+    assert relerr(cub, want) <= TOL[prec]
+    assert relerr(back, np.prod(n) * c.reshape(-1)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_uneven_kpoints_and_chunks(F, prec):
+    n, r = (24, 24, 24), 6.0
+    ks = fi.kshifts(4, seed=7)
+    bands = [3, 0, 5, 2]  # a k-point without bands
+    gs = [oracle.sphere_gvectors(n, r, k) for k in ks]
+    cs = sphere_batch([len(g) for g in gs], bands, seed=41, prec=prec)
+    x = np.concatenate([c.reshape(-1) for c in cs])
+    # chunk of 3 bands: chunks straddle k-points and end ragged (10 bands)
+    plan, cube, _ = run_plan(F, n, "g2r", prec, x, radius=r, kshift=ks, bands=bands, max_chunk_bands=3)
+    assert plan.info["chunk_bands"] == 3 and plan.info["total_bands"] == 10
+    want = np.concatenate([oracle.g2r(g, c, n).reshape(-1) for g, c in zip(gs, cs) if len(c)])
+    assert relerr(cube, want) <= TOL[prec]
+    _, back, _ = run_plan(F, n, "roundtrip", prec, x, radius=r, kshift=ks, bands=bands, max_chunk_bands=3)
+    assert relerr(back, np.prod(n) * x) <= TOL[prec]
+
+
+def test_explicit_user_order_and_empty_sphere(F):
+    n = (32, 32, 48)
+    g = oracle.sphere_gvectors(n, 9.0)
+    perm = np.random.default_rng(5).permutation(len(g))
+    gu = g[perm]
+    c = fi.complex_gaussian((2, len(gu)), 51)
+    empty = np.zeros((0, 3), np.int32)
+    x = c.reshape(-1)
+    plan, cube, _ = run_plan(F, n, "g2r", "fp64", x, g_lists=[gu, empty], bands=[2, 1])
+    assert np.array_equal(plan.sphere(0), gu) and plan.ngw(1) == 0
+    want = oracle.g2r(gu, c, n).reshape(-1)
+    vol = np.prod(n)
+    assert relerr(cube[: 2 * vol], want) <= 1e-12
+    assert np.abs(cube[2 * vol:]).max() == 0.0  # empty sphere -> zero cube
+    R = fi.complex_gaussian((3, n[2], n[1], n[0]), 52)
+    _, sph, _ = run_plan(F, n, "r2g", "fp64", R, g_lists=[gu, empty], bands=[2, 1])
+    assert relerr(sph, oracle.r2g(gu, R[:2], n).reshape(-1)) <= 1e-12
+
+
+def test_single_g_vector_sphere(F):
+    # r = 0: only G = 0; the cube is the constant c(0)
+    n = (16, 16, 16)
+    c = np.array([[1.5 - 0.5j], [2.0 + 1.0j]])
+    _, cube, _ = run_plan(F, n, "g2r", "fp64", c, radius=0.0, bands=[2])
+    cube = cube.reshape(2, -1)
+    assert np.abs(cube - c).max() < 1e-15
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,r", [((24, 24, 24), 6.0), ((32, 32, 48), 10.0)])
+def test_apply_potential_vs_oracle(F, n, r, prec):
+    import torch
+    bands = 3
+    g = oracle.sphere_gvectors(n, r)
+    c = sphere_batch([len(g)], [bands], seed=61, prec=prec)[0]
+    v = fi.gaussian_potential(n, 8, 2.0, seed=62)
+    vr = v.astype(np.float64 if prec == "fp64" else np.float32)
+    plan = F.Plan(n, "apply", prec, radius=r, bands=[bands])
+    vd = torch.from_numpy(np.ascontiguousarray(vr)).cuda()
+    plan.set_potential(vd)
+    x = to_dev(c, prec)
+    out = torch.empty_like(x)
+    plan.execute(x, out)
+    torch.cuda.synchronize()
+    want = oracle.apply_potential(g, c, vr.astype(np.float64), n)
+    assert relerr(out.cpu().numpy(), want) <= TOL[prec]
+
+
+def test_execute_argument_errors(F):
+    import torch
+    plan = F.Plan((24, 24, 24), "roundtrip", "fp32", radius=6.0, bands=[2])
+    x = torch.zeros(plan.info["sphere_elems"], dtype=torch.complex64, device="cuda")
+    y = torch.zeros_like(x)
+    with pytest.raises(F.FFTBError):  # ROUNDTRIP needs a cube
+        F.fftb_execute(plan.handle, x.data_ptr(), y.data_ptr(), None, None)
+    with pytest.raises(F.FFTBError):  # in == out
+        F.fftb_execute(plan.handle, x.data_ptr(), x.data_ptr(), y.data_ptr(), None)
+    with pytest.raises(F.FFTBError):  # misaligned
+        F.fftb_execute(plan.handle, x.data_ptr() + 4, y.data_ptr(), y.data_ptr(), None)
+    ap = F.Plan((24, 24, 24), "apply", "fp32", radius=6.0, bands=[2])
+    with pytest.raises(F.FFTBError):  # apply without a potential
+        F.fftb_execute(ap.handle, x.data_ptr(), y.data_ptr(), None, None)
+
+
+def test_host_buffer_entry_point(F):
+    n, r = (24, 24, 24), 6.0
+    g = oracle.sphere_gvectors(n, r)
+    c = fi.complex_gaussian((3, len(g)), 71)
+    plan = F.Plan(n, "roundtrip", "fp64", radius=r, bands=[3])
+    xin = np.ascontiguousarray(c.reshape(-1))
+    xout = np.zeros_like(xin)
+    F.fftb_execute_host(plan.handle, xin.ctypes.data, xout.ctypes.data, None, None)
+    assert relerr(xout, np.prod(n) * xin) <= 1e-12
+    assert plan.launches() == plan.info["kernels_per_execute"]
