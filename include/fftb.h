@@ -168,6 +168,38 @@ const char* fftb_error_string(fftb_status status);
 /* Message of the last error raised on the calling thread ("" if none). */
 const char* fftb_last_error(void);
 
+/* Allocation-free G -> r. The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc -- real-time or embedded
+ * hosts that forbid device allocation after start-up, programs whose device
+ * memory is handed out entirely by their own allocator or pool, and libraries
+ * that must not change the memory footprint of their caller. Creating a plan
+ * allocates; this call does not, and needs no plan.
+ *
+ * Computes what a G_TO_R FP32 plan for one cutoff sphere computes (same
+ * kernels): in_dev = [bands][ngw] complex64 sphere coefficients in canonical
+ * order (fftb_sphere_enumerate gives the G list), out_dev = [bands][N2][N1][N0]
+ * complex64 cube. Both are caller-owned device buffers, 8-byte aligned.
+ * Enqueued on `stream`; no synchronisation.
+ *
+ * Scratch: the stick buffer and the geometry tables live in two file-scope
+ * device arrays of FFTB_NOALLOC_SCRATCH_BYTES and FFTB_NOALLOC_TABLE_BYTES,
+ * which every GPU that loads the library holds until the process exits.
+ * Bands are processed in chunks that fit the scratch. A sphere whose single
+ * band's stick buffer (N2 * sticks * 8 bytes) or whose tables exceed these
+ * sizes is rejected with FFTB_ERR_UNSUPPORTED and a message saying which.
+ * Every call shares the arrays and leaves its contents there; nothing in them
+ * needs to start at zero. Calls that overlap on the GPU (different streams or
+ * host threads) race on the arrays and must be serialised by the caller.
+ * The first call on a device looks up the arrays' device addresses once for
+ * that device (cudaGetSymbolAddress, with the device current); make that
+ * first call before any stream capture.
+ * Errors: INVALID_ARG (bad pointer, alignment, sphere that does not fit the
+ * grid), UNSUPPORTED (grid extent, size limits above), CUDA. */
+#define FFTB_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define FFTB_NOALLOC_TABLE_BYTES (4u << 20)
+fftb_status fftb_g2r_noalloc(const int32_t n[3], double radius, const double* kshift,
+                             int32_t bands, const void* in_dev, void* out_dev, void* stream);
+
 /* Host-only helpers (no GPU needed). */
 
 /* Enumerates the cutoff sphere |G + k| <= r of an N0 x N1 x N2 grid (Sec.

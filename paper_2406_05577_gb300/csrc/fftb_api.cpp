@@ -54,6 +54,8 @@ static fftb_status fail(fftb_status s, const std::string& msg) {
   g_last_error = msg;
   return s;
 }
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
 static fftb_status cuda_fail(cudaError_t e, const char* where) {
   return fail(FFTB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }

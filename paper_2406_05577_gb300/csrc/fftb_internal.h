@@ -62,5 +62,7 @@ int stick_tile(int prec, int n2);
 cudaError_t prepare_kernels(int prec, int n0, int n1, int n2, int xmax);
 cudaError_t launch_stick(int prec, int mode, const Launch& L, int tiles);
 cudaError_t launch_plane(int prec, int mode, const Launch& L);
+// Sets the calling thread's message for fftb_last_error().
+void set_last_error(const std::string& msg);
 
 }  // namespace fftb

@@ -1,0 +1,198 @@
+// noalloc.cu -- fftb_g2r_noalloc: the G -> r transform for callers that
+// cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc: real-time or embedded hosts that
+// forbid device allocation after start-up, programs whose device memory is
+// handed out entirely by their own allocator or pool (a cudaMalloc behind its
+// back would break its accounting or fail), and libraries that must not
+// change the memory footprint of the process that calls them. Creating a plan
+// allocates, so those callers cannot use fftb_plan_create. This entry point
+// needs no plan and allocates nothing: the stick scratch and the geometry
+// tables live in the two file-scope arrays below, which every GPU that loads
+// the library holds until the process exits.
+//
+// The first call on a device looks up the arrays' device addresses
+// (cudaGetSymbolAddress, once per device, with that device current); make
+// that first call before any stream capture.
+//
+// The scratch is the stick buffer T between the z-stage and the plane stage
+// (the same kernels as a G_TO_R plan). Every call shares both arrays and
+// leaves the last call's contents in them; nothing in them needs to start at
+// zero, because each call writes every table word and every T entry it later
+// reads. Calls that overlap on the GPU (two streams, or two host threads)
+// race on the arrays: serialise them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fftb.h"
+#include "fftb_internal.h"
+#include "geometry.h"
+
+namespace fftb {
+template <typename T> size_t plane_smem_t(int, int, int);
+template <typename T> int stick_tile_t(int);
+template <typename T> cudaError_t launch_stick_t(int, const Launch&, int);
+template <typename T> cudaError_t launch_plane_t(int, const Launch&);
+template <typename T> cudaError_t prepare_t(int, int, int, int);
+}  // namespace fftb
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FFTB_NOALLOC_SCRATCH_BYTES];
+static __device__ __align__(256) unsigned char g_noalloc_tables[FFTB_NOALLOC_TABLE_BYTES];
+
+namespace {
+
+fftb_status err(fftb_status s, const std::string& m) {
+  fftb::set_last_error(m);  // read back with fftb_last_error()
+  return s;
+}
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+void* g_scratch_ptr[kMaxDevices];
+void* g_tables_ptr[kMaxDevices];
+
+// Once per device, with that device current: device addresses of the arrays.
+fftb_status device_arrays(int dev, void** scratch, void** tables) {
+  if (dev < 0 || dev >= kMaxDevices) return err(FFTB_ERR_UNSUPPORTED, "device index above 63");
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (!g_scratch_ptr[dev]) {
+    void* s = nullptr;
+    void* t = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&s, g_noalloc_scratch);
+    if (e != cudaSuccess) return err(FFTB_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    e = cudaGetSymbolAddress(&t, g_noalloc_tables);
+    if (e != cudaSuccess) return err(FFTB_ERR_CUDA, std::string("cudaGetSymbolAddress(tables): ") + cudaGetErrorString(e));
+    g_tables_ptr[dev] = t;
+    g_scratch_ptr[dev] = s;
+  }
+  *scratch = g_scratch_ptr[dev];
+  *tables = g_tables_ptr[dev];
+  return FFTB_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
+    const int32_t n[3], double radius, const double* kshift, int32_t bands, const void* in_dev,
+    void* out_dev, void* stream) {
+  using namespace fftb;
+  if (!n) return err(FFTB_ERR_INVALID_ARG, "n is NULL");
+  if (bands < 0) return err(FFTB_ERR_INVALID_ARG, "bands must be >= 0");
+  if (!grid_size_supported(n[0]) || !grid_size_supported(n[1]) || !grid_size_supported(n[2]) ||
+      !plane_size_supported(n[0], n[1]))
+    return err(FFTB_ERR_UNSUPPORTED, "grid extents must be one of 12,16,20,24,32,40,48,64,96,128,160 with N0 == N1");
+  if (bands == 0) return FFTB_OK;
+  if (!in_dev || !out_dev) return err(FFTB_ERR_INVALID_ARG, "in_dev and out_dev must be device pointers");
+  if ((reinterpret_cast<uintptr_t>(in_dev) | reinterpret_cast<uintptr_t>(out_dev)) % 8 != 0)
+    return err(FFTB_ERR_INVALID_ARG, "buffers must be 8-byte aligned (complex64)");
+
+  const double zero[3] = {0, 0, 0};
+  std::vector<int32_t> g;
+  std::string e = sphere_by_cutoff(n, radius, kshift ? kshift : zero, g);
+  if (!e.empty()) return err(FFTB_ERR_INVALID_ARG, e);
+  KGeom G;
+  e = build_geometry(n, g.data(), (int64_t)g.size() / 3, G);
+  if (!e.empty()) return err(FFTB_ERR_INVALID_ARG, e);
+
+  // stick scratch: as many bands per launch as the static array holds
+  const int32_t smax = std::max<int32_t>(G.S, 1);
+  const size_t t_band = (size_t)n[2] * smax * 8;
+  if (t_band > FFTB_NOALLOC_SCRATCH_BYTES)
+    return err(FFTB_ERR_UNSUPPORTED, "one band's stick buffer (" + std::to_string(t_band) +
+                                         " bytes) exceeds FFTB_NOALLOC_SCRATCH_BYTES");
+  const int chunk = (int)std::min<size_t>((size_t)bands, FFTB_NOALLOC_SCRATCH_BYTES / t_band);
+  if (plane_smem_t<float>(n[0], n[1], G.X) > 227 * 1024)
+    return err(FFTB_ERR_UNSUPPORTED, "plane does not fit in shared memory");
+
+  // tables, packed like a one-k-point plan
+  KInfo ki{G.S, G.X, 0, 0};
+  std::vector<int32_t> band_k((size_t)bands, 0);
+  std::vector<int64_t> band_sph((size_t)bands);
+  for (int b = 0; b < bands; ++b) band_sph[b] = (int64_t)b * G.ngw;
+  std::vector<float> tw[3];
+  for (int d = 0; d < 3; ++d) {
+    tw[d].resize(2 * (size_t)n[d]);
+    for (int m = 0; m < n[d]; ++m) {
+      const double a = 2.0 * M_PI * (double)m / (double)n[d];
+      tw[d][2 * m] = (float)std::cos(a);
+      tw[d][2 * m + 1] = (float)std::sin(a);
+    }
+  }
+  std::vector<int32_t> one_zero(1, 0);
+  const std::vector<int32_t>& pos = G.ent_pos.empty() ? one_zero : G.ent_pos;
+  const std::vector<int32_t>& zs = G.ent_zs.empty() ? one_zero : G.ent_zs;
+  const std::vector<int32_t>& sxy = G.stick_xy.empty() ? one_zero : G.stick_xy;
+  struct Part { const void* p; size_t bytes; size_t off; };
+  Part parts[] = {{band_k.data(), band_k.size() * 4, 0},  {band_sph.data(), band_sph.size() * 8, 0},
+                  {&ki, sizeof(KInfo), 0},                {G.stick_ent.data(), G.stick_ent.size() * 4, 0},
+                  {pos.data(), pos.size() * 4, 0},         {zs.data(), zs.size() * 4, 0},
+                  {sxy.data(), sxy.size() * 4, 0},         {G.xmap.data(), G.xmap.size() * 2, 0},
+                  {tw[0].data(), tw[0].size() * 4, 0},     {tw[1].data(), tw[1].size() * 4, 0},
+                  {tw[2].data(), tw[2].size() * 4, 0}};
+  size_t total = 0;
+  for (Part& p : parts) {
+    p.off = total;
+    total = align256(total + p.bytes);
+  }
+  if (total > FFTB_NOALLOC_TABLE_BYTES)
+    return err(FFTB_ERR_UNSUPPORTED, "geometry tables (" + std::to_string(total) +
+                                         " bytes) exceed FFTB_NOALLOC_TABLE_BYTES");
+
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return err(FFTB_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
+  void* scratch = nullptr;
+  void* tables = nullptr;
+  fftb_status st = device_arrays(dev, &scratch, &tables);
+  if (st != FFTB_OK) return st;
+  ce = prepare_t<float>(n[0], n[1], n[2], G.X);
+  if (ce != cudaSuccess) return err(FFTB_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(ce));
+
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<unsigned char> blob(total, 0);
+  for (const Part& p : parts) std::memcpy(blob.data() + p.off, p.p, p.bytes);
+  // pageable source: the call returns once the bytes are staged, so blob may go
+  ce = cudaMemcpyAsync(tables, blob.data(), total, cudaMemcpyHostToDevice, s);
+  if (ce != cudaSuccess) return err(FFTB_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(ce));
+
+  unsigned char* base = static_cast<unsigned char*>(tables);
+  Launch L{};
+  L.g.band_k = reinterpret_cast<const int32_t*>(base + parts[0].off);
+  L.g.band_sph = reinterpret_cast<const int64_t*>(base + parts[1].off);
+  L.g.kinfo = reinterpret_cast<const KInfo*>(base + parts[2].off);
+  L.g.stick_ent = reinterpret_cast<const int32_t*>(base + parts[3].off);
+  L.g.ent_pos = reinterpret_cast<const int32_t*>(base + parts[4].off);
+  L.g.ent_zs = reinterpret_cast<const int32_t*>(base + parts[5].off);
+  L.g.stick_xy = reinterpret_cast<const int32_t*>(base + parts[6].off);
+  L.g.xmap = reinterpret_cast<const int16_t*>(base + parts[7].off);
+  L.g.tw0 = base + parts[8].off;
+  L.g.tw1 = base + parts[9].off;
+  L.g.tw2 = base + parts[10].off;
+  L.g.n0 = n[0];
+  L.g.n1 = n[1];
+  L.g.n2 = n[2];
+  L.g.smax = smax;
+  L.g.xmax = G.X;
+  L.sph_in = in_dev;
+  L.cube_out = out_dev;
+  L.T = scratch;
+  L.stream = s;
+  const int ts = stick_tile_t<float>(n[2]);
+  const int tiles = (smax + ts - 1) / ts;
+  for (int b0 = 0; b0 < bands; b0 += chunk) {
+    L.band0 = b0;
+    L.nb = std::min(chunk, bands - b0);
+    ce = launch_stick_t<float>(M_G2R, L, tiles);
+    if (ce == cudaSuccess) ce = launch_plane_t<float>(M_G2R, L);
+    if (ce != cudaSuccess) return err(FFTB_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(ce));
+  }
+  return FFTB_OK;
+}

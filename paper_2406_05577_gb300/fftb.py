@@ -72,6 +72,8 @@ EXPORTS = {
     "fftb_version": (ctypes.c_char_p, []),
     "fftb_plan_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fftb_plan_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "fftb_g2r_noalloc": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_double, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fftb_sphere_enumerate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_double,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                              ctypes.POINTER(ctypes.c_int64)]),
@@ -235,6 +237,14 @@ def fftb_sphere_sticks(n, g):
     _check(L.fftb_sphere_sticks(nn, gg.ctypes.data if gg.size else None, len(gg),
                                 ctypes.byref(s), ctypes.byref(x)))
     return s.value, x.value
+
+
+def fftb_g2r_noalloc(n, radius, kshift, bands, in_ptr, out_ptr, stream=None):
+    """Allocation-free G -> r (FP32, one cutoff sphere); see include/fftb.h."""
+    nn = (ctypes.c_int32 * 3)(*[int(v) for v in n])
+    k = None if kshift is None else np.ascontiguousarray(np.asarray(kshift, np.float64).reshape(3))
+    _check(lib().fftb_g2r_noalloc(nn, float(radius), None if k is None else k.ctypes.data, int(bands),
+                                  in_ptr, out_ptr, stream))
 
 
 def fftb_version():
