@@ -2,7 +2,9 @@
 
 Compiles the CUDA translation units and the host C++ in parallel into
 ``_build/`` and links ``libfftb.so`` next to this file. Objects are rebuilt
-when their source or any header is newer.
+when their source or any header is newer. ``FFTB_NVCC_FLAGS`` (environment)
+adds nvcc flags, e.g. ``-DFFTB_PLANE_EPT_F32=16`` to try a kernel tuning
+knob; it forces a rebuild.
 """
 from __future__ import annotations
 
@@ -40,7 +42,7 @@ def _headers():
 
 
 def _stale(obj: str, src: str, deps) -> bool:
-    if not os.path.exists(obj):
+    if not os.path.exists(obj) or os.environ.get("FFTB_NVCC_FLAGS"):
         return True
     t = os.path.getmtime(obj)
     return any(os.path.getmtime(p) > t for p in [src, *deps])
@@ -71,6 +73,7 @@ def build(verbose: bool = False, ptxas_verbose: bool = False) -> str:
                    "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I", CSRC, "-I", INCLUDE]
             if ptxas_verbose:
                 cmd += ["-Xptxas", "-v"]
+            cmd += os.environ.get("FFTB_NVCC_FLAGS", "").split()
             jobs.append(cmd)
     for s in CPP_SOURCES:
         src = os.path.join(CSRC, s)

@@ -113,12 +113,56 @@ template <int S, typename C> __device__ __forceinline__ void dft8(C* v) {
   v[3] = e3 + o3; v[7] = e3 - o3;
 }
 
+// radix 6 = 3 x 2 (Cooley-Tukey): DFT3 of the even and odd inputs, twiddle
+// the odd outputs by W6^k1, then radix-2 butterflies.
+template <int S, typename C> __device__ __forceinline__ void dft6(C* v) {
+  using T = decltype(C::x);
+  const T h = T(0.5), r = T(S) * T(0.86602540378443864676372317);  // W6 = 1/2 + S j sqrt3/2
+  C a0 = v[0], a1 = v[2], a2 = v[4], b0 = v[1], b1 = v[3], b2 = v[5];
+  dft3<S>(a0, a1, a2);
+  dft3<S>(b0, b1, b2);
+  b1 = mk(b1.x * h - b1.y * r, b1.x * r + b1.y * h);   // * W6^1
+  b2 = mk(-b2.x * h - b2.y * r, b2.x * r - b2.y * h);  // * W6^2 = -1/2 + S j sqrt3/2
+  v[0] = a0 + b0; v[3] = a0 - b0;
+  v[1] = a1 + b1; v[4] = a1 - b1;
+  v[2] = a2 + b2; v[5] = a2 - b2;
+}
+
+// radix 16 = 4 x 4: DFT4 over n1 for each n2 (inputs 4 n1 + n2), twiddle by
+// W16^(n2 k1), DFT4 over n2, outputs k1 + 4 k2.
+template <int S, typename C> __device__ __forceinline__ void dft16(C* v) {
+  using T = decltype(C::x);
+  const T c1 = T(0.92387953251128675612818319);  // cos(pi/8)
+  const T s1 = T(0.38268343236508977172845998);  // sin(pi/8)
+  const T h = T(0.70710678118654752440084436);   // cos(pi/4)
+  C y[4][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    C a = v[n2], b = v[4 + n2], c = v[8 + n2], d = v[12 + n2];
+    dft4<S>(a, b, c, d);
+    y[n2][0] = a; y[n2][1] = b; y[n2][2] = c; y[n2][3] = d;
+  }
+  // W16^m = cos(2 pi m/16) + S j sin(2 pi m/16)
+  auto w = [&](C a, T cr, T si) { return mk(a.x * cr - a.y * (T(S) * si), a.x * (T(S) * si) + a.y * cr); };
+  y[1][1] = w(y[1][1], c1, s1);  y[1][2] = w(y[1][2], h, h);   y[1][3] = w(y[1][3], s1, c1);
+  y[2][1] = w(y[2][1], h, h);    y[2][2] = mulj<S>(y[2][2]);   y[2][3] = w(y[2][3], -h, h);
+  y[3][1] = w(y[3][1], s1, c1);  y[3][2] = w(y[3][2], -h, h);  y[3][3] = w(y[3][3], -c1, -s1);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C a = y[0][k1], b = y[1][k1], c = y[2][k1], d = y[3][k1];
+    dft4<S>(a, b, c, d);
+    v[k1] = a; v[k1 + 4] = b; v[k1 + 8] = c; v[k1 + 12] = d;
+  }
+}
+
 template <int R, int S, typename C> __device__ __forceinline__ void dft(C* v) {
   if constexpr (R == 2) dft2<S>(v[0], v[1]);
   else if constexpr (R == 3) dft3<S>(v[0], v[1], v[2]);
   else if constexpr (R == 4) dft4<S>(v[0], v[1], v[2], v[3]);
   else if constexpr (R == 5) dft5<S>(v[0], v[1], v[2], v[3], v[4]);
+  else if constexpr (R == 6) dft6<S>(v);
   else if constexpr (R == 8) dft8<S>(v);
+  else if constexpr (R == 16) dft16<S>(v);
   else static_assert(R == 2, "unsupported radix");
 }
 
@@ -229,5 +273,84 @@ template <int N, int NT, int EPT> struct lines_per_chunk {
 };
 
 __host__ __device__ constexpr int odd_pitch(int n) { return (n & 1) ? n : n + 1; }
+
+// ------------------------------------------------------- warp-level passes
+// A warp owns a few whole lines and runs all passes of their DFTs alone,
+// synchronising with __syncwarp only. Between passes the lines sit in the
+// warp's private shared-memory scratch, row-major with one pad element after
+// every 8 (wpad): stride-R butterfly stores then fall on distinct banks.
+// The row pitch is = 8 (mod 16) complex elements, so the two lines a
+// half-warp touches use opposite bank halves.
+__host__ __device__ constexpr int wpitch(int n) {
+  return (n + n / 8) + ((8 - (n + n / 8) % 16) + 16) % 16;
+}
+__device__ __forceinline__ int wpad(int e) { return e + (e >> 3); }
+
+template <int N, int R, int P, int S, int MAXIT, typename C, typename Src, typename Dst>
+__device__ __forceinline__ void wpass(int nl, const C* __restrict__ tw, Src&& src, Dst&& dst) {
+  constexpr int NB = N / R;
+  const int lane = threadIdx.x & 31;
+  const int total = nl * NB;
+  C v[MAXIT][R];
+#pragma unroll
+  for (int it = 0; it < MAXIT; ++it) {
+    const int w = lane + 32 * it;
+    if (w < total) {
+      const int line = w / NB, i = w - line * NB;
+#pragma unroll
+      for (int j = 0; j < R; ++j) v[it][j] = src(line, i + j * NB);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int it = 0; it < MAXIT; ++it) {
+    const int w = lane + 32 * it;
+    if (w < total) {
+      const int line = w / NB, i = w - line * NB;
+      const int k = i % P;
+      if constexpr (P > 1) {
+        constexpr int STEP = N / (P * R);
+#pragma unroll
+        for (int j = 1; j < R; ++j) {
+          const C w_ = tw[j * k * STEP];
+          v[it][j] = (S > 0) ? cmul(v[it][j], w_) : cmulc(v[it][j], w_);
+        }
+      }
+      dft<R, S>(v[it]);
+      const int base = (i - k) * R + k;
+#pragma unroll
+      for (int j = 0; j < R; ++j) dst(line, base + j * P, v[it][j]);
+    }
+  }
+  __syncwarp();
+}
+
+// All passes of a length-N DFT on nl <= LMAX lines owned by one warp.
+template <int N, int REM, int P, int S, int LMAX, bool FIRST, typename C, typename First,
+          typename MidLd, typename MidSt, typename Last>
+__device__ __forceinline__ void wfft_passes(int nl, const C* __restrict__ tw, First&& first,
+                                            MidLd&& mid_ld, MidSt&& mid_st, Last&& last) {
+  constexpr int R = first_radix<REM>::value;
+  static_assert(R != 0, "length must be 2^a 3^b 5^c");
+  constexpr int MAXIT = (LMAX * (N / R) + 31) / 32;
+  constexpr bool LAST = (REM == R);
+  if constexpr (FIRST && LAST) {
+    wpass<N, R, P, S, MAXIT, C>(nl, tw, first, last);
+  } else if constexpr (FIRST) {
+    wpass<N, R, P, S, MAXIT, C>(nl, tw, first, mid_st);
+  } else if constexpr (LAST) {
+    wpass<N, R, P, S, MAXIT, C>(nl, tw, mid_ld, last);
+  } else {
+    wpass<N, R, P, S, MAXIT, C>(nl, tw, mid_ld, mid_st);
+  }
+  if constexpr (!LAST)
+    wfft_passes<N, REM / R, P * R, S, LMAX, false, C>(nl, tw, first, mid_ld, mid_st, last);
+}
+
+template <int N, int S, int LMAX, typename C, typename First, typename MidLd, typename MidSt, typename Last>
+__device__ __forceinline__ void wfft(int nl, const C* __restrict__ tw, First&& first, MidLd&& mid_ld,
+                                     MidSt&& mid_st, Last&& last) {
+  wfft_passes<N, N, 1, S, LMAX, true, C>(nl, tw, first, mid_ld, mid_st, last);
+}
 
 }  // namespace fftb

@@ -19,11 +19,12 @@
 namespace fftb {
 
 template <typename T> size_t stick_smem_t(int);
-template <typename T> size_t plane_smem_t(int, int, int);
+template <typename T> size_t plane_smem_t(int, int, int, int);
 template <typename T> int stick_tile_t(int);
 template <typename T> cudaError_t launch_stick_t(int, const Launch&, int);
 template <typename T> cudaError_t launch_plane_t(int, const Launch&);
-template <typename T> cudaError_t prepare_t(int, int, int, int);
+template <typename T> cudaError_t prepare_t(int, int, int, int, int);
+template <typename T> int plane_occupancy_t(int, int, int, int, int);
 
 static const int kSizes[] = {12, 16, 20, 24, 32, 40, 48, 64, 96, 128, 160};
 
@@ -34,12 +35,16 @@ bool grid_size_supported(int n) {
 }
 bool plane_size_supported(int n0, int n1) { return n0 == n1 && grid_size_supported(n0); }
 size_t stick_smem(int prec, int n2) { return prec == P_F64 ? stick_smem_t<double>(n2) : stick_smem_t<float>(n2); }
-size_t plane_smem(int prec, int n0, int n1, int xmax) {
-  return prec == P_F64 ? plane_smem_t<double>(n0, n1, xmax) : plane_smem_t<float>(n0, n1, xmax);
+size_t plane_smem(int prec, int n0, int n1, int xmax, int a_bufs) {
+  return prec == P_F64 ? plane_smem_t<double>(n0, n1, xmax, a_bufs) : plane_smem_t<float>(n0, n1, xmax, a_bufs);
 }
 int stick_tile(int prec, int n2) { return prec == P_F64 ? stick_tile_t<double>(n2) : stick_tile_t<float>(n2); }
-cudaError_t prepare_kernels(int prec, int n0, int n1, int n2, int xmax) {
-  return prec == P_F64 ? prepare_t<double>(n0, n1, n2, xmax) : prepare_t<float>(n0, n1, n2, xmax);
+cudaError_t prepare_kernels(int prec, int n0, int n1, int n2, int xmax, int a_bufs) {
+  return prec == P_F64 ? prepare_t<double>(n0, n1, n2, xmax, a_bufs) : prepare_t<float>(n0, n1, n2, xmax, a_bufs);
+}
+int plane_occupancy(int prec, int mode, int n0, int n1, int xmax, int a_bufs) {
+  return prec == P_F64 ? plane_occupancy_t<double>(mode, n0, n1, xmax, a_bufs)
+                       : plane_occupancy_t<float>(mode, n0, n1, xmax, a_bufs);
 }
 cudaError_t launch_stick(int prec, int mode, const Launch& L, int tiles) {
   return prec == P_F64 ? launch_stick_t<double>(mode, L, tiles) : launch_stick_t<float>(mode, L, tiles);
@@ -77,6 +82,8 @@ struct fftb_plan_s {
   int64_t sphere_elems = 0, cube_elems = 0;
   int32_t smax = 0, xmax = 0, tiles = 0, chunk = 1;
   int device = 0;
+  int32_t plane_ctas[3] = {0, 0, 0};  // persistent CTAs: G->r, r->G, apply
+  int32_t a_bufs = 2;                 // slab-plane buffers of the plane stage
   // device memory
   void* d_tables = nullptr;
   size_t tables_bytes = 0;
@@ -191,8 +198,9 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   if (p->total_bands > 65535) { release(p); return fail(FFTB_ERR_UNSUPPORTED, "more than 65535 bands in one plan"); }
 
   const size_t smem_limit = 227 * 1024;
+  if (plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, 2) > smem_limit) p->a_bufs = 1;
   if (stick_smem(p->prec_kernel, p->n[2]) > smem_limit ||
-      plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax) > smem_limit) {
+      plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, p->a_bufs) > smem_limit) {
     release(p);
     return fail(FFTB_ERR_UNSUPPORTED, "plane of this size and precision does not fit in shared memory");
   }
@@ -207,9 +215,10 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   p->chunk = chunk;
 
   // ---- host tables
-  std::vector<int32_t> band_k, stick_ent, ent_pos, ent_zs, stick_xy;
+  std::vector<int32_t> band_k, stick_ent, ent_pos, ent_zs, col_start, stick_xy;
   std::vector<int64_t> band_sph;
   std::vector<int16_t> xmap;
+  int32_t sticks_so_far = 0;
   std::vector<KInfo> kinfo(p->nk);
   int64_t sph = 0, ent_base = 0;
   for (int k = 0; k < p->nk; ++k) {
@@ -221,13 +230,17 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
     sph += (int64_t)p->bands[k] * G.ngw;
     kinfo[k].S = G.S;
     kinfo[k].X = G.X;
-    kinfo[k].stick_base = (int32_t)stick_xy.size();
+    kinfo[k].stick_base = sticks_so_far;
     kinfo[k].xmap_base = (int32_t)xmap.size();
+    kinfo[k].col_base = (int32_t)col_start.size();
+    kinfo[k].flags = G.contiguous_columns ? KF_CONTIGUOUS_COLUMNS : 0;
+    sticks_so_far += G.S;
     for (int32_t v : G.stick_ent) stick_ent.push_back((int32_t)(v + ent_base));
     for (int32_t v : G.ent_pos) ent_pos.push_back(v);
     for (int32_t v : G.ent_zs) ent_zs.push_back(v);
-    for (int32_t v : G.stick_xy) stick_xy.push_back(v);
     for (int16_t v : G.xmap) xmap.push_back(v);
+    for (int32_t v : G.col_start) col_start.push_back(v);
+    for (int32_t v : G.stick_xy) stick_xy.push_back(v);
     ent_base += G.ngw;
   }
   if (ent_base >= (int64_t(1) << 31)) { release(p); return fail(FFTB_ERR_UNSUPPORTED, "total sphere entries above 2^31"); }
@@ -247,7 +260,7 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
       {ent_pos.data(), ent_pos.size() * 4, 0},     {ent_zs.data(), ent_zs.size() * 4, 0},
       {stick_xy.data(), stick_xy.size() * 4, 0},   {xmap.data(), xmap.size() * 2, 0},
       {tw[0].data(), tw[0].size(), 0},             {tw[1].data(), tw[1].size(), 0},
-      {tw[2].data(), tw[2].size(), 0}};
+      {tw[2].data(), tw[2].size(), 0},             {col_start.data(), col_start.size() * 4, 0}};
   size_t total = 0;
   for (auto& pt : parts) {
     pt.off = total;
@@ -271,6 +284,7 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   g.ent_pos = reinterpret_cast<const int32_t*>(base + parts[4].off);
   g.ent_zs = reinterpret_cast<const int32_t*>(base + parts[5].off);
   g.stick_xy = reinterpret_cast<const int32_t*>(base + parts[6].off);
+  g.col_start = reinterpret_cast<const int32_t*>(base + parts[11].off);
   g.xmap = reinterpret_cast<const int16_t*>(base + parts[7].off);
   g.tw0 = base + parts[8].off;
   g.tw1 = base + parts[9].off;
@@ -284,8 +298,17 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   p->T_bytes = (size_t)chunk * p->n[2] * smax_pitch * p->csize;
   e = cudaMalloc(&p->d_T, p->T_bytes);
   if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaMalloc stick scratch failed"); }
-  e = prepare_kernels(p->prec_kernel, p->n[0], p->n[1], p->n[2], p->xmax);
+  e = prepare_kernels(p->prec_kernel, p->n[0], p->n[1], p->n[2], p->xmax, p->a_bufs);
   if (e != cudaSuccess) { release(p); return cuda_fail(e, "kernel attributes"); }
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) { release(p); return cuda_fail(e, "device attribute"); }
+  const int modes[3] = {M_G2R, M_R2G, M_APPLY};
+  for (int i = 0; i < 3; ++i) {
+    const int occ = plane_occupancy(p->prec_kernel, modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs);
+    if (occ < 1) { release(p); return fail(FFTB_ERR_UNSUPPORTED, "plane kernel cannot be resident on this device"); }
+    p->plane_ctas[i] = sms * occ;
+  }
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) { release(p); return cuda_fail(e, "plan synchronise"); }
   *out = p;
@@ -365,10 +388,25 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
   const int pk = p->prec_kernel;
   switch (kind) {
     case K_STICK_G2R: e = launch_stick(pk, M_G2R, L, p->tiles); break;
-    case K_PLANE_G2R: e = launch_plane(pk, M_G2R, L); break;
-    case K_PLANE_R2G: e = launch_plane(pk, M_R2G, L); break;
+    case K_PLANE_G2R: {
+      Launch Lp = L;
+      Lp.plane_ctas = p->plane_ctas[0];
+      e = launch_plane(pk, M_G2R, Lp);
+      break;
+    }
+    case K_PLANE_R2G: {
+      Launch Lp = L;
+      Lp.plane_ctas = p->plane_ctas[1];
+      e = launch_plane(pk, M_R2G, Lp);
+      break;
+    }
     case K_STICK_R2G: e = launch_stick(pk, M_R2G, L, p->tiles); break;
-    default: e = launch_plane(pk, M_APPLY, L); break;
+    default: {
+      Launch Lp = L;
+      Lp.plane_ctas = p->plane_ctas[2];
+      e = launch_plane(pk, M_APPLY, Lp);
+      break;
+    }
   }
   if (e == cudaSuccess) ++p->launches;
   if (p->timing) {
@@ -399,6 +437,7 @@ FFTB_EXPORT fftb_status fftb_execute(fftb_plan p, const void* in, void* out, voi
   L.g = p->g;
   L.T = p->d_T;
   L.V = p->d_V;
+  L.a_bufs = p->a_bufs;
   L.stream = s;
   for (int b0 = 0; b0 < p->total_bands; b0 += p->chunk) {
     L.band0 = b0;

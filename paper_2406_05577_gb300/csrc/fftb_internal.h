@@ -14,9 +14,14 @@ namespace fftb {
 struct KInfo {
   int32_t S;           // occupied (x,y) sticks
   int32_t X;           // occupied x values (y-z slabs)
-  int32_t stick_base;  // first entry of this k in stick_xy; stick_ent uses stick_base + k
+  int32_t stick_base;  // sticks of earlier k-points; stick_ent uses stick_base + k
   int32_t xmap_base;   // first entry of this k in xmap (k * N0)
+  int32_t col_base;    // first entry of this k in col_start (sum of X + 1 over earlier k)
+  int32_t flags;       // KF_* bits
 };
+// Every slab column's sticks have consecutive gy (always true for a cutoff
+// sphere); the plane stage then indexes stick rows directly.
+constexpr int32_t KF_CONTIGUOUS_COLUMNS = 1;
 
 // Device tables for all k-points (concatenated) plus twiddles.
 struct Geo {
@@ -26,8 +31,9 @@ struct Geo {
   const int32_t* stick_ent;  // [sum(S_k + 1)] global entry offset of each stick (CSR)
   const int32_t* ent_pos;    // [sum ngw] position of the entry within its k's sphere list
   const int32_t* ent_zs;     // [sum ngw] (z index << 24) | local stick index
-  const int32_t* stick_xy;   // [sum S_k] (xi << 16) | y index
   const int16_t* xmap;       // [n_k * N0] slab index of x, or -1
+  const int32_t* col_start;  // [sum (X_k + 1)] first stick of each slab (local stick index)
+  const int32_t* stick_xy;   // [sum S_k] (xi << 16) | y index
   const void* tw0;           // [N0] e^{+2 pi j m / N0} in the plan's real type
   const void* tw1;           // [N1]
   const void* tw2;           // [N2]
@@ -46,6 +52,8 @@ struct Launch {
   void* cube_out;       // cube batch written by the plane stage (G -> r)
   void* T;              // stick scratch [nb][N2][smax]
   const void* V;        // potential (apply)
+  int32_t plane_ctas;   // persistent plane-stage CTAs (0: one per plane)
+  int32_t a_bufs;       // slab-plane buffers of the plane stage (1 or 2)
   cudaStream_t stream;
 };
 
@@ -56,10 +64,12 @@ bool grid_size_supported(int n);
 bool plane_size_supported(int n0, int n1);
 // Dynamic shared memory (bytes) of each kernel for one k geometry.
 size_t stick_smem(int prec, int n2);
-size_t plane_smem(int prec, int n0, int n1, int xmax);
+size_t plane_smem(int prec, int n0, int n1, int xmax, int a_bufs);
 int stick_tile(int prec, int n2);
 // Raise the dynamic shared-memory limit of the kernels a plan uses.
-cudaError_t prepare_kernels(int prec, int n0, int n1, int n2, int xmax);
+cudaError_t prepare_kernels(int prec, int n0, int n1, int n2, int xmax, int a_bufs);
+// Resident plane-stage CTAs per SM for this geometry (after prepare_kernels).
+int plane_occupancy(int prec, int mode, int n0, int n1, int xmax, int a_bufs);
 cudaError_t launch_stick(int prec, int mode, const Launch& L, int tiles);
 cudaError_t launch_plane(int prec, int mode, const Launch& L);
 // Sets the calling thread's message for fftb_last_error().

@@ -87,8 +87,8 @@ std::string build_geometry(const int32_t n[3], const int32_t* g, int64_t ngw, KG
   std::vector<int32_t> order((size_t)ngw);
   std::iota(order.begin(), order.end(), 0);
   std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-    if (g[3 * a + 1] != g[3 * b + 1]) return g[3 * a + 1] < g[3 * b + 1];
     if (g[3 * a] != g[3 * b]) return g[3 * a] < g[3 * b];
+    if (g[3 * a + 1] != g[3 * b + 1]) return g[3 * a + 1] < g[3 * b + 1];
     return g[3 * a + 2] < g[3 * b + 2];
   });
   // occupied x values, ascending signed
@@ -100,6 +100,7 @@ std::string build_geometry(const int32_t n[3], const int32_t* g, int64_t ngw, KG
   out.xmap.assign(n[0], (int16_t)-1);
   for (size_t i = 0; i < xs.size(); ++i) out.xmap[wrap(xs[i], n[0])] = (int16_t)i;
 
+  out.col_start.assign((size_t)out.X + 1, 0);
   out.ent_pos.resize(ngw);
   out.ent_zs.resize(ngw);
   int32_t s = -1;
@@ -108,19 +109,22 @@ std::string build_geometry(const int32_t n[3], const int32_t* g, int64_t ngw, KG
     const int32_t i = order[j];
     const int32_t gx = g[3 * i], gy = g[3 * i + 1], gz = g[3 * i + 2];
     if (s < 0 || gx != px || gy != py) {
+      if (s >= 0 && gx == px && gy != py + 1) out.contiguous_columns = false;
       ++s;
       px = gx;
       py = gy;
       out.stick_ent.push_back((int32_t)j);
       const int32_t xi = out.xmap[wrap(gx, n[0])];
       out.stick_xy.push_back((xi << 16) | wrap(gy, n[1]));
+      out.col_start[xi + 1] = s + 1;
     }
     out.ent_pos[j] = i;
     out.ent_zs[j] = (wrap(gz, n[2]) << 24) | s;
   }
   out.S = s + 1;
   out.stick_ent.push_back((int32_t)ngw);
-  if (out.S >= (1 << 24)) return "too many sticks";
+  for (int32_t xi = 1; xi <= out.X; ++xi) out.col_start[xi] = std::max(out.col_start[xi], out.col_start[xi - 1]);
+  if (out.S >= (1 << 15)) return "too many sticks (limit 32767)";
   return "";
 }
 

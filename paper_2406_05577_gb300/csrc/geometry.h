@@ -9,18 +9,22 @@
 namespace fftb {
 
 // One k-point's sphere and the tables the kernels index it with.
-//   entries are the sphere's G sorted by stick (gy, then gx) and then gz
-//   (the CSR-over-xy offset array of Sec. 3.3 / Fig. 6);
+//   sticks (occupied (x,y) columns) are numbered x-major: by gx, then gy,
+//   so the sticks of one x-slab are consecutive (the offset array over the
+//   xy projection of Sec. 3.3 / Fig. 6, regrouped slab by slab);
+//   entries are the sphere's G sorted by stick and then gz;
 //   stick_ent[s] .. stick_ent[s+1] are the entries of stick s (S + 1 values);
 //   ent_pos[j] is entry j's position in the caller's sphere list;
 //   ent_zs[j]  = (gz mod N2) << 24 | s;
-//   stick_xy[s] = xi << 16 | (gy mod N1), xi = rank of gx among occupied x;
-//   xmap[x] = xi of x = gx mod N0, or -1 for an empty x-slab.
+//   xmap[x] = xi of x = gx mod N0 (rank of gx among occupied x), or -1;
+//   col_start[xi] .. col_start[xi+1] are the sticks of slab xi (X + 1 values);
+//   stick_xy[s] = xi << 16 | (gy mod N1).
 struct KGeom {
   int64_t ngw = 0;
   std::vector<int32_t> g;  // ngw * 3, the caller's order
   int32_t S = 0, X = 0;
-  std::vector<int32_t> stick_ent, ent_pos, ent_zs, stick_xy;
+  bool contiguous_columns = true;  // each slab's sticks have consecutive gy
+  std::vector<int32_t> stick_ent, ent_pos, ent_zs, col_start, stick_xy;
   std::vector<int16_t> xmap;
 };
 

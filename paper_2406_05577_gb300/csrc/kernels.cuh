@@ -23,6 +23,7 @@
 
 #include "fft_core.cuh"
 #include "fftb_internal.h"
+#include "line_fft.cuh"
 
 namespace fftb {
 
@@ -36,19 +37,10 @@ template <typename T, int N> __host__ __device__ constexpr int line_cap() {
 template <typename T, int N2> __host__ __device__ constexpr int stick_tile_c() {
   return line_cap<T, N2>() > 128 ? 128 : line_cap<T, N2>();
 }
-template <typename T, int N0, int N1> __host__ __device__ constexpr int row_chunk_c() {
-  return line_cap<T, N0>() > N1 ? N1 : line_cap<T, N0>();
-}
 
 template <typename T, int N2> constexpr size_t stick_smem_c() {
   using C = typename cplx<T>::type;
   return sizeof(C) * ((size_t)N2 * odd_pitch(stick_tile_c<T, N2>()) + N2);
-}
-template <typename T, int N0, int N1> size_t plane_smem_c(int xmax) {
-  using C = typename cplx<T>::type;
-  const int xp = odd_pitch(xmax > 0 ? xmax : 1);
-  return sizeof(C) * ((size_t)N1 * xp + (size_t)N0 * odd_pitch(row_chunk_c<T, N0, N1>()) + N0 + N1) +
-         sizeof(int) * N0;
 }
 
 // ------------------------------------------------------------------ z stage
@@ -105,108 +97,276 @@ __global__ void __launch_bounds__(Cfg<T>::NT) k_stick(const Launch L) {
 }
 
 // ------------------------------------------------------------- y, x stages
-template <typename T, int N0, int N1, int MODE>
-__global__ void __launch_bounds__(Cfg<T>::NT) k_plane(const Launch L) {
+// Persistent CTAs walk the (band, z) planes with a grid stride. Every y- or
+// x-line is transformed by a group of Line<N>::G lanes holding it in
+// registers (line_fft.cuh); a warp carries 32 / G lines at a time and needs
+// no block barrier inside a phase. The slab plane A[y][xi] (the plane
+// restricted to the X occupied x-slabs) is double buffered when shared memory
+// allows, so one block barrier per plane separates its y and x phases, and a
+// warp that finishes plane p's x phase goes straight on to plane p+1's y
+// phase (with one buffer a second barrier ends each plane). A's pitch is X
+// rounded up to 2 (mod 16): conflict-free for the column writes of the y
+// phase and the row reads of the x phase. x-phase tasks are dealt out after
+// the y-phase tasks, so the warps with fewer y lines get more x rows.
+#ifndef FFTB_PLANE_NW
+#define FFTB_PLANE_NW 8
+#endif
+template <typename T> struct PlaneCfg { static constexpr int NW = FFTB_PLANE_NW; };
+// resident CTAs per SM the register allocation must allow (measured best)
+template <typename T, int N0> __host__ __device__ constexpr int plane_minb() {
+  return sizeof(T) == 8 ? 1 : (N0 <= 64 ? 3 : 2);
+}
+
+__host__ __device__ constexpr int a_pitch(int x) { return x + ((2 - x % 16) + 16) % 16; }
+template <int N0, int N1> __host__ __device__ constexpr int plane_scratch() {
+  return (32 / Line<N1>::G) * Line<N1>::PITCH > (32 / Line<N0>::G) * Line<N0>::PITCH
+             ? (32 / Line<N1>::G) * Line<N1>::PITCH
+             : (32 / Line<N0>::G) * Line<N0>::PITCH;
+}
+
+template <typename T, int N0, int N1> size_t plane_smem_c(int xmax, int a_bufs) {
   using C = typename cplx<T>::type;
-  constexpr int NT = Cfg<T>::NT, EPT = Cfg<T>::EPT;
-  constexpr int LCY = line_cap<T, N1>();          // y-DFT columns per pass set
-  constexpr int YC = row_chunk_c<T, N0, N1>();    // x-DFT rows per pass set
-  constexpr int YCP = odd_pitch(YC);
+  return sizeof(C) * ((size_t)a_bufs * N1 * a_pitch(xmax) + (size_t)PlaneCfg<T>::NW * plane_scratch<N0, N1>() + N0 + N1);
+}
+
+// packed per-lane slab indices: byte q of w[q / 4] = xi of position q, 255 = empty
+template <int E> struct XiPack {
+  uint32_t w[(E + 3) / 4];
+  __device__ __forceinline__ int get(int q) const { return (int)((w[q >> 2] >> (8 * (q & 3))) & 0xFFu); }
+};
+
+template <typename T, int N0, int N1, int MODE>
+__global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k_plane(const Launch L) {
+  using C = typename cplx<T>::type;
+  using LY = Line<N1>;
+  using LX = Line<N0>;
+  constexpr int NW = PlaneCfg<T>::NW, NT = NW * 32;
+  constexpr int WY = 32 / LY::G, WX = 32 / LX::G;   // lines per warp
+  constexpr int EY = LY::E, EX = LX::E;
+  constexpr int SCR = plane_scratch<N0, N1>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
 
-  const int z = blockIdx.x;
-  const int bl = blockIdx.y;
-  const int gb = L.band0 + bl;
   const int n2 = L.g.n2;
-  const int k = L.g.band_k[gb];
-  const KInfo ki = L.g.kinfo[k];
-  const int X = ki.X, S = ki.S;
-  const int XP = odd_pitch(X > 0 ? X : 1);
-
-  C* A = reinterpret_cast<C*>(smem_raw);
-  C* B = A + N1 * XP;
-  C* tw0 = B + N0 * YCP;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gy = lane % LY::G, ly = lane / LY::G;
+  const int gx = lane % LX::G, lx = lane / LX::G;
+  const int abuf = N1 * a_pitch(L.g.xmax);
+  C* A0 = reinterpret_cast<C*>(smem_raw);
+  const int nbuf = L.a_bufs;
+  C* scr = A0 + nbuf * abuf + warp * SCR;
+  C* tw0 = A0 + nbuf * abuf + NW * SCR;
   C* tw1 = tw0 + N0;
-  int* xm = reinterpret_cast<int*>(tw1 + N1);
   {
     const C* t0 = static_cast<const C*>(L.g.tw0);
     const C* t1 = static_cast<const C*>(L.g.tw1);
-    for (int m = threadIdx.x; m < N0; m += NT) {
-      tw0[m] = t0[m];
-      xm[m] = L.g.xmap[ki.xmap_base + m];
-    }
+    for (int m = threadIdx.x; m < N0; m += NT) tw0[m] = t0[m];
     for (int m = threadIdx.x; m < N1; m += NT) tw1[m] = t1[m];
   }
-  C* Tz = static_cast<C*>(L.T) + ((size_t)bl * n2 + z) * L.g.smax;
-  const int32_t* sxy = L.g.stick_xy + ki.stick_base;
-  const size_t plane = ((size_t)gb * n2 + z) * (size_t)(N1 * N0);
+  __syncthreads();
+  C* rowy = scr + ly * LY::PITCH;
+  C* rowx = scr + lx * LX::PITCH;
+  typename LY::template TwCache<C> tcy;
+  typename LX::template TwCache<C> tcx;
+  tcy.load(gy, tw1);
+  tcx.load(gx, tw0);
+  // signed y of this lane's first-pass / last-pass y positions (direct stick I/O)
+  auto ysigned = [](int y) { return y < N1 - N1 / 2 ? y : y - N1; };
 
-  auto b_ld = [&](int line, int e) -> C { return B[e * YCP + line]; };
-  auto b_st = [&](int line, int e, C v) { B[e * YCP + line] = v; };
+  const int nplanes = L.nb * n2;
+  int cur_k = -1;
+  XiPack<EX> xin, xout;  // slab index of this lane's first-pass / last-pass x positions
+  int parity = 0;
+#pragma unroll 1
+  for (int p = blockIdx.x; p < nplanes; p += gridDim.x, parity ^= (nbuf - 1)) {
+    const int bl = p / n2;
+    const int z = p - bl * n2;
+    const int gb = L.band0 + bl;
+    const int k = L.g.band_k[gb];
+    const KInfo ki = L.g.kinfo[k];
+    const int X = ki.X;
+    const int XP = a_pitch(X);
+    if (k != cur_k) {  // uniform across the CTA
+      cur_k = k;
+      const int16_t* xm = L.g.xmap + ki.xmap_base;
+#pragma unroll
+      for (int q = 0; q < (EX + 3) / 4; ++q) { xin.w[q] = 0; xout.w[q] = 0; }
+#pragma unroll
+      for (int m = 0; m < EX / LX::R0; ++m)
+#pragma unroll
+        for (int j = 0; j < LX::R0; ++j) {
+          const int q = m * LX::R0 + j, xi = xm[LX::first_pos(gx, m, j)];
+          xin.w[q >> 2] |= (uint32_t)(xi < 0 ? 255 : xi) << (8 * (q & 3));
+        }
+#pragma unroll
+      for (int m = 0; m < EX / LX::RL; ++m)
+#pragma unroll
+        for (int j = 0; j < LX::RL; ++j) {
+          const int q = m * LX::RL + j, xi = xm[LX::last_pos(gx, m, j)];
+          xout.w[q >> 2] |= (uint32_t)(xi < 0 ? 255 : xi) << (8 * (q & 3));
+        }
+    }
+    C* A = A0 + parity * abuf;
+    const int32_t* cs = L.g.col_start + ki.col_base;
+    const int32_t* sxy = L.g.stick_xy + ki.stick_base;
+    C* Tz = static_cast<C*>(L.T) + ((size_t)bl * n2 + z) * L.g.smax;
+    const size_t plane = ((size_t)gb * n2 + z) * (size_t)(N1 * N0);
+    const int ty = (X + WY - 1) / WY;       // y tasks of this plane
+    const int tx = (N1 + WX - 1) / WX;      // x tasks
+    const int x_first = ty % NW;            // x tasks start after the y tasks
 
-  if constexpr (MODE == M_G2R || MODE == M_APPLY) {
-    for (int m = threadIdx.x; m < N1 * XP; m += NT) A[m] = czero<C>();
-    __syncthreads();
-    for (int s = threadIdx.x; s < S; s += NT) {
-      const int xy = sxy[s];
-      A[(xy & 0xFFFF) * XP + (xy >> 16)] = Tz[s];
-    }
-    __syncthreads();
-    // y-DFT (+) of each occupied x-slab column
-    for (int c0 = 0; c0 < X; c0 += LCY) {
-      const int nl = min(LCY, X - c0);
-      auto a_ld = [&](int line, int e) -> C { return A[e * XP + c0 + line]; };
-      auto a_st = [&](int line, int e, C v) { A[e * XP + c0 + line] = v; };
-      fft_lines<N1, +1, NT, EPT, false, C>(nl, tw1, a_ld, a_ld, a_st, a_st);
-    }
-    // x-DFT (+) of every row, zero-extended from the X occupied columns
-    for (int y0 = 0; y0 < N1; y0 += YC) {
-      const int nl = min(YC, N1 - y0);
-      auto first = [&](int line, int x) -> C {
-        const int xi = xm[x];
-        return xi >= 0 ? A[(y0 + line) * XP + xi] : czero<C>();
-      };
-      if constexpr (MODE == M_G2R) {
-        C* out = static_cast<C*>(L.cube_out) + plane + (size_t)y0 * N0;
-        auto last = [&](int line, int x, C v) { out[line * N0 + x] = v; };
-        fft_lines<N0, +1, NT, EPT, true, C>(nl, tw0, first, b_ld, b_st, last);
-      } else {
-        const T* V = static_cast<const T*>(L.V) + (size_t)z * (N1 * N0) + (size_t)y0 * N0;
-        auto last = [&](int line, int x, C v) { B[x * YCP + line] = scale(v, V[line * N0 + x]); };
-        fft_lines<N0, +1, NT, EPT, true, C>(nl, tw0, first, b_ld, b_st, last);
-        auto back = [&](int line, int x, C v) {
-          const int xi = xm[x];
-          if (xi >= 0) A[(y0 + line) * XP + xi] = v;
-        };
-        fft_lines<N0, -1, NT, EPT, true, C>(nl, tw0, b_ld, b_ld, b_st, back);
+    if constexpr (MODE == M_G2R || MODE == M_APPLY) {
+      // y-DFT (+) of the occupied x-slab columns: scatter the sticks of this
+      // warp's columns into zeroed scratch rows, transform, write A columns
+#pragma unroll 1
+      for (int t = warp; t < ty; t += NW) {
+        const int c0 = t * WY, nl = min(WY, X - c0);
+        C v[EY];
+        if (ki.flags & KF_CONTIGUOUS_COLUMNS) {
+          // each column's sticks are consecutive in gy: index them directly
+          const int col = c0 + (ly < nl ? ly : 0);
+          const int sa = cs[col], len = cs[col + 1] - sa;
+          const int ylo = ysigned(sxy[sa] & 0xFFFF);
+#pragma unroll
+          for (int m = 0; m < EY / LY::R0; ++m)
+#pragma unroll
+            for (int j = 0; j < LY::R0; ++j) {
+              const int d = ysigned(LY::first_pos(gy, m, j)) - ylo;
+              v[m * LY::R0 + j] = (unsigned)d < (unsigned)len ? Tz[sa + d] : czero<C>();
+            }
+        } else {
+          for (int q = lane; q < WY * LY::PITCH; q += 32) scr[q] = czero<C>();
+          __syncwarp();
+          const int s1 = cs[c0 + nl];
+          for (int s = cs[c0] + lane; s < s1; s += 32) {
+            const int xy = sxy[s];
+            scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)] = Tz[s];
+          }
+          __syncwarp();
+#pragma unroll
+          for (int m = 0; m < EY / LY::R0; ++m)
+#pragma unroll
+            for (int j = 0; j < LY::R0; ++j) v[m * LY::R0 + j] = rowy[wpad(LY::first_pos(gy, m, j))];
+          __syncwarp();
+        }
+        LY::template run<+1>(v, gy, rowy, tw1, tcy);
+        if (ly < nl) {
+#pragma unroll
+          for (int m = 0; m < EY / LY::RL; ++m)
+#pragma unroll
+            for (int j = 0; j < LY::RL; ++j) A[LY::last_pos(gy, m, j) * XP + c0 + ly] = v[m * LY::RL + j];
+        }
+      }
+      __syncthreads();
+      // x-DFT (+) of every row, zero-extended from the X occupied columns
+#pragma unroll 1
+      for (int t = (warp - x_first + NW) % NW; t < tx; t += NW) {
+        const int y0 = t * WX, row = y0 + lx;
+        const bool live = row < N1;
+        C v[EX];
+#pragma unroll
+        for (int q = 0; q < EX; ++q) {
+          const int xi = xin.get(q);
+          v[q] = (live && xi != 255) ? A[row * XP + xi] : czero<C>();
+        }
+        LX::template run<+1>(v, gx, rowx, tw0, tcx);
+        if constexpr (MODE == M_G2R) {
+          if (live) {
+            C* out = static_cast<C*>(L.cube_out) + plane + (size_t)row * N0;
+#pragma unroll
+            for (int m = 0; m < EX / LX::RL; ++m)
+#pragma unroll
+              for (int j = 0; j < LX::RL; ++j) out[LX::last_pos(gx, m, j)] = v[m * LX::RL + j];
+          }
+        } else {
+          // V(r) * psi(r), then back to first-pass order and x-DFT (-)
+          const T* V = static_cast<const T*>(L.V) + (size_t)z * (N1 * N0) + (size_t)(live ? row : 0) * N0;
+#pragma unroll
+          for (int m = 0; m < EX / LX::RL; ++m)
+#pragma unroll
+            for (int j = 0; j < LX::RL; ++j) {
+              const int x = LX::last_pos(gx, m, j);
+              rowx[wpad(x)] = scale(v[m * LX::RL + j], __ldg(V + x));
+            }
+          __syncwarp();
+#pragma unroll
+          for (int m = 0; m < EX / LX::R0; ++m)
+#pragma unroll
+            for (int j = 0; j < LX::R0; ++j) v[m * LX::R0 + j] = rowx[wpad(LX::first_pos(gx, m, j))];
+          __syncwarp();
+          LX::template run<-1>(v, gx, rowx, tw0, tcx);
+          if (live) {
+#pragma unroll
+            for (int q = 0; q < EX; ++q) {
+              const int xi = xout.get(q);
+              if (xi != 255) A[row * XP + xi] = v[q];
+            }
+          }
+        }
       }
     }
-  }
-  if constexpr (MODE == M_R2G) {
-    __syncthreads();
-    for (int y0 = 0; y0 < N1; y0 += YC) {
-      const int nl = min(YC, N1 - y0);
-      const C* in = static_cast<const C*>(L.cube_in) + plane + (size_t)y0 * N0;
-      auto first = [&](int line, int x) -> C { return in[line * N0 + x]; };
-      auto last = [&](int line, int x, C v) {
-        const int xi = xm[x];
-        if (xi >= 0) A[(y0 + line) * XP + xi] = v;
-      };
-      fft_lines<N0, -1, NT, EPT, true, C>(nl, tw0, first, b_ld, b_st, last);
+    if constexpr (MODE == M_R2G) {
+#pragma unroll 1
+      for (int t = (warp - x_first + NW) % NW; t < tx; t += NW) {
+        const int y0 = t * WX, row = y0 + lx;
+        const bool live = row < N1;
+        const C* in = static_cast<const C*>(L.cube_in) + plane + (size_t)(live ? row : 0) * N0;
+        C v[EX];
+#pragma unroll
+        for (int m = 0; m < EX / LX::R0; ++m)
+#pragma unroll
+          for (int j = 0; j < LX::R0; ++j)
+            v[m * LX::R0 + j] = live ? in[LX::first_pos(gx, m, j)] : czero<C>();
+        LX::template run<-1>(v, gx, rowx, tw0, tcx);
+        if (live) {
+#pragma unroll
+          for (int q = 0; q < EX; ++q) {
+            const int xi = xout.get(q);
+            if (xi != 255) A[row * XP + xi] = v[q];
+          }
+        }
+      }
     }
-  }
-  if constexpr (MODE == M_R2G || MODE == M_APPLY) {
-    // y-DFT (-) of each occupied column, then keep the occupied sticks
-    for (int c0 = 0; c0 < X; c0 += LCY) {
-      const int nl = min(LCY, X - c0);
-      auto a_ld = [&](int line, int e) -> C { return A[e * XP + c0 + line]; };
-      auto a_st = [&](int line, int e, C v) { A[e * XP + c0 + line] = v; };
-      fft_lines<N1, -1, NT, EPT, false, C>(nl, tw1, a_ld, a_ld, a_st, a_st);
+    if constexpr (MODE == M_R2G || MODE == M_APPLY) {
+      __syncthreads();
+      // y-DFT (-) of each occupied column; keep the occupied sticks
+#pragma unroll 1
+      for (int t = warp; t < ty; t += NW) {
+        const int c0 = t * WY, nl = min(WY, X - c0);
+        const int col = c0 + (ly < nl ? ly : 0);
+        C v[EY];
+#pragma unroll
+        for (int m = 0; m < EY / LY::R0; ++m)
+#pragma unroll
+          for (int j = 0; j < LY::R0; ++j) v[m * LY::R0 + j] = A[LY::first_pos(gy, m, j) * XP + col];
+        LY::template run<-1>(v, gy, rowy, tw1, tcy);
+        if (ki.flags & KF_CONTIGUOUS_COLUMNS) {
+          if (ly < nl) {
+            const int sa = cs[col], len = cs[col + 1] - sa;
+            const int ylo = ysigned(sxy[sa] & 0xFFFF);
+#pragma unroll
+            for (int m = 0; m < EY / LY::RL; ++m)
+#pragma unroll
+              for (int j = 0; j < LY::RL; ++j) {
+                const int d = ysigned(LY::last_pos(gy, m, j)) - ylo;
+                if ((unsigned)d < (unsigned)len) Tz[sa + d] = v[m * LY::RL + j];
+              }
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < EY / LY::RL; ++m)
+#pragma unroll
+            for (int j = 0; j < LY::RL; ++j) rowy[wpad(LY::last_pos(gy, m, j))] = v[m * LY::RL + j];
+          __syncwarp();
+          const int s1 = cs[c0 + nl];
+          for (int s = cs[c0] + lane; s < s1; s += 32) {
+            const int xy = sxy[s];
+            Tz[s] = scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)];
+          }
+          __syncwarp();
+        }
+      }
     }
-    for (int s = threadIdx.x; s < S; s += NT) {
-      const int xy = sxy[s];
-      Tz[s] = A[(xy & 0xFFFF) * XP + (xy >> 16)];
-    }
+    if (nbuf == 1) __syncthreads();
   }
 }
 
@@ -221,10 +381,10 @@ template <typename T> size_t stick_smem_t(int n2) {
   }
   return 0;
 }
-template <typename T> size_t plane_smem_t(int n0, int n1, int xmax) {
+template <typename T> size_t plane_smem_t(int n0, int n1, int xmax, int a_bufs) {
   if (n0 != n1) return 0;
   switch (n0) {
-#define C_(N) case N: return plane_smem_c<T, N, N>(xmax);
+#define C_(N) case N: return plane_smem_c<T, N, N>(xmax, a_bufs);
     FFTB_SIZES(C_)
 #undef C_
   }
@@ -247,11 +407,13 @@ template <typename T, int N2> cudaError_t go_stick(int mode, const Launch& L, in
   return cudaGetLastError();
 }
 template <typename T, int N> cudaError_t go_plane(int mode, const Launch& L) {
-  const size_t smem = plane_smem_c<T, N, N>(L.g.xmax);
-  const dim3 grid(L.g.n2, L.nb);
-  if (mode == M_G2R) k_plane<T, N, N, M_G2R><<<grid, Cfg<T>::NT, smem, L.stream>>>(L);
-  else if (mode == M_R2G) k_plane<T, N, N, M_R2G><<<grid, Cfg<T>::NT, smem, L.stream>>>(L);
-  else k_plane<T, N, N, M_APPLY><<<grid, Cfg<T>::NT, smem, L.stream>>>(L);
+  const size_t smem = plane_smem_c<T, N, N>(L.g.xmax, L.a_bufs);
+  const int nplanes = L.nb * L.g.n2;
+  const dim3 grid(L.plane_ctas > 0 ? min(L.plane_ctas, nplanes) : nplanes);
+  constexpr int NT = PlaneCfg<T>::NW * 32;
+  if (mode == M_G2R) k_plane<T, N, N, M_G2R><<<grid, NT, smem, L.stream>>>(L);
+  else if (mode == M_R2G) k_plane<T, N, N, M_R2G><<<grid, NT, smem, L.stream>>>(L);
+  else k_plane<T, N, N, M_APPLY><<<grid, NT, smem, L.stream>>>(L);
   return cudaGetLastError();
 }
 template <typename T, int N2> cudaError_t prep_stick() {
@@ -261,14 +423,34 @@ template <typename T, int N2> cudaError_t prep_stick() {
     e = cudaFuncSetAttribute(k_stick<T, N2, M_R2G>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   return e;
 }
-template <typename T, int N> cudaError_t prep_plane(int xmax) {
-  const int s = (int)plane_smem_c<T, N, N>(xmax);
+template <typename T, int N> cudaError_t prep_plane(int xmax, int a_bufs) {
+  const int s = (int)plane_smem_c<T, N, N>(xmax, a_bufs);
   cudaError_t e = cudaFuncSetAttribute(k_plane<T, N, N, M_G2R>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_plane<T, N, N, M_R2G>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_plane<T, N, N, M_APPLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   return e;
+}
+
+template <typename T, int N> int occ_plane(int mode, int xmax, int a_bufs) {
+  const size_t smem = plane_smem_c<T, N, N>(xmax, a_bufs);
+  constexpr int NT = PlaneCfg<T>::NW * 32;
+  int nb = 0;
+  cudaError_t e;
+  if (mode == M_G2R) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_G2R>, NT, smem);
+  else if (mode == M_R2G) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_R2G>, NT, smem);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_APPLY>, NT, smem);
+  return e == cudaSuccess ? nb : 0;
+}
+template <typename T> int plane_occupancy_t(int mode, int n0, int n1, int xmax, int a_bufs) {
+  if (n0 != n1) return 0;
+  switch (n0) {
+#define C_(N) case N: return occ_plane<T, N>(mode, xmax, a_bufs);
+    FFTB_SIZES(C_)
+#undef C_
+  }
+  return 0;
 }
 
 template <typename T> cudaError_t launch_stick_t(int mode, const Launch& L, int tiles) {
@@ -288,7 +470,7 @@ template <typename T> cudaError_t launch_plane_t(int mode, const Launch& L) {
   }
   return cudaErrorInvalidValue;
 }
-template <typename T> cudaError_t prepare_t(int n0, int n1, int n2, int xmax) {
+template <typename T> cudaError_t prepare_t(int n0, int n1, int n2, int xmax, int a_bufs) {
   cudaError_t e = cudaErrorInvalidValue;
   switch (n2) {
 #define C_(N) case N: e = prep_stick<T, N>(); break;
@@ -297,7 +479,7 @@ template <typename T> cudaError_t prepare_t(int n0, int n1, int n2, int xmax) {
   }
   if (e != cudaSuccess || n0 != n1) return e == cudaSuccess ? cudaErrorInvalidValue : e;
   switch (n0) {
-#define C_(N) case N: return prep_plane<T, N>(xmax);
+#define C_(N) case N: return prep_plane<T, N>(xmax, a_bufs);
     FFTB_SIZES(C_)
 #undef C_
   }
@@ -306,10 +488,11 @@ template <typename T> cudaError_t prepare_t(int n0, int n1, int n2, int xmax) {
 
 #define FFTB_INSTANTIATE(T)                                                        \
   template size_t stick_smem_t<T>(int);                                            \
-  template size_t plane_smem_t<T>(int, int, int);                                  \
+  template size_t plane_smem_t<T>(int, int, int, int);                             \
   template int stick_tile_t<T>(int);                                               \
   template cudaError_t launch_stick_t<T>(int, const Launch&, int);                 \
   template cudaError_t launch_plane_t<T>(int, const Launch&);                      \
-  template cudaError_t prepare_t<T>(int, int, int, int);
+  template cudaError_t prepare_t<T>(int, int, int, int, int);                     \
+  template int plane_occupancy_t<T>(int, int, int, int, int);
 
 }  // namespace fftb

@@ -35,11 +35,11 @@
 #include "geometry.h"
 
 namespace fftb {
-template <typename T> size_t plane_smem_t(int, int, int);
+template <typename T> size_t plane_smem_t(int, int, int, int);
 template <typename T> int stick_tile_t(int);
 template <typename T> cudaError_t launch_stick_t(int, const Launch&, int);
 template <typename T> cudaError_t launch_plane_t(int, const Launch&);
-template <typename T> cudaError_t prepare_t(int, int, int, int);
+template <typename T> cudaError_t prepare_t(int, int, int, int, int);
 }  // namespace fftb
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FFTB_NOALLOC_SCRATCH_BYTES];
@@ -109,11 +109,12 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
     return err(FFTB_ERR_UNSUPPORTED, "one band's stick buffer (" + std::to_string(t_band) +
                                          " bytes) exceeds FFTB_NOALLOC_SCRATCH_BYTES");
   const int chunk = (int)std::min<size_t>((size_t)bands, FFTB_NOALLOC_SCRATCH_BYTES / t_band);
-  if (plane_smem_t<float>(n[0], n[1], G.X) > 227 * 1024)
+  const int a_bufs = plane_smem_t<float>(n[0], n[1], G.X, 2) <= 227 * 1024 ? 2 : 1;
+  if (plane_smem_t<float>(n[0], n[1], G.X, a_bufs) > 227 * 1024)
     return err(FFTB_ERR_UNSUPPORTED, "plane does not fit in shared memory");
 
   // tables, packed like a one-k-point plan
-  KInfo ki{G.S, G.X, 0, 0};
+  KInfo ki{G.S, G.X, 0, 0, 0, G.contiguous_columns ? KF_CONTIGUOUS_COLUMNS : 0};
   std::vector<int32_t> band_k((size_t)bands, 0);
   std::vector<int64_t> band_sph((size_t)bands);
   for (int b = 0; b < bands; ++b) band_sph[b] = (int64_t)b * G.ngw;
@@ -136,7 +137,7 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
                   {pos.data(), pos.size() * 4, 0},         {zs.data(), zs.size() * 4, 0},
                   {sxy.data(), sxy.size() * 4, 0},         {G.xmap.data(), G.xmap.size() * 2, 0},
                   {tw[0].data(), tw[0].size() * 4, 0},     {tw[1].data(), tw[1].size() * 4, 0},
-                  {tw[2].data(), tw[2].size() * 4, 0}};
+                  {tw[2].data(), tw[2].size() * 4, 0},     {G.col_start.data(), G.col_start.size() * 4, 0}};
   size_t total = 0;
   for (Part& p : parts) {
     p.off = total;
@@ -153,7 +154,7 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
   void* tables = nullptr;
   fftb_status st = device_arrays(dev, &scratch, &tables);
   if (st != FFTB_OK) return st;
-  ce = prepare_t<float>(n[0], n[1], n[2], G.X);
+  ce = prepare_t<float>(n[0], n[1], n[2], G.X, a_bufs);
   if (ce != cudaSuccess) return err(FFTB_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(ce));
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -172,6 +173,7 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
   L.g.ent_pos = reinterpret_cast<const int32_t*>(base + parts[4].off);
   L.g.ent_zs = reinterpret_cast<const int32_t*>(base + parts[5].off);
   L.g.stick_xy = reinterpret_cast<const int32_t*>(base + parts[6].off);
+  L.g.col_start = reinterpret_cast<const int32_t*>(base + parts[11].off);
   L.g.xmap = reinterpret_cast<const int16_t*>(base + parts[7].off);
   L.g.tw0 = base + parts[8].off;
   L.g.tw1 = base + parts[9].off;
@@ -184,6 +186,7 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
   L.sph_in = in_dev;
   L.cube_out = out_dev;
   L.T = scratch;
+  L.a_bufs = a_bufs;
   L.stream = s;
   const int ts = stick_tile_t<float>(n[2]);
   const int tiles = (smax + ts - 1) / ts;
