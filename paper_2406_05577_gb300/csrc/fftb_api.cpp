@@ -233,7 +233,7 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
     kinfo[k].stick_base = sticks_so_far;
     kinfo[k].xmap_base = (int32_t)xmap.size();
     kinfo[k].col_base = (int32_t)col_start.size();
-    kinfo[k].flags = G.contiguous_columns ? KF_CONTIGUOUS_COLUMNS : 0;
+    kinfo[k].flags = (G.contiguous_columns ? KF_CONTIGUOUS_COLUMNS : 0) | (G.canonical_sticks ? KF_CANONICAL_STICKS : 0);
     sticks_so_far += G.S;
     for (int32_t v : G.stick_ent) stick_ent.push_back((int32_t)(v + ent_base));
     for (int32_t v : G.ent_pos) ent_pos.push_back(v);

@@ -22,6 +22,10 @@ struct KInfo {
 // Every slab column's sticks have consecutive gy (always true for a cutoff
 // sphere); the plane stage then indexes stick rows directly.
 constexpr int32_t KF_CONTIGUOUS_COLUMNS = 1;
+// Every stick's entries have consecutive gz and consecutive positions in the
+// sphere list (the canonical order of a cutoff sphere); the z stage then
+// indexes the coefficient list directly.
+constexpr int32_t KF_CANONICAL_STICKS = 2;
 
 // Device tables for all k-points (concatenated) plus twiddles.
 struct Geo {

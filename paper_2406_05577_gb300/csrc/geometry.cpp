@@ -118,6 +118,9 @@ std::string build_geometry(const int32_t n[3], const int32_t* g, int64_t ngw, KG
       out.stick_xy.push_back((xi << 16) | wrap(gy, n[1]));
       out.col_start[xi + 1] = s + 1;
     }
+    if (j > 0 && out.stick_ent.back() != (int32_t)j &&
+        (gz != g[3 * order[j - 1] + 2] + 1 || i != order[j - 1] + 1))
+      out.canonical_sticks = false;
     out.ent_pos[j] = i;
     out.ent_zs[j] = (wrap(gz, n[2]) << 24) | s;
   }

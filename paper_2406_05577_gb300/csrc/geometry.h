@@ -24,6 +24,7 @@ struct KGeom {
   std::vector<int32_t> g;  // ngw * 3, the caller's order
   int32_t S = 0, X = 0;
   bool contiguous_columns = true;  // each slab's sticks have consecutive gy
+  bool canonical_sticks = true;    // each stick: consecutive gz at consecutive list positions
   std::vector<int32_t> stick_ent, ent_pos, ent_zs, col_start, stick_xy;
   std::vector<int16_t> xmap;
 };

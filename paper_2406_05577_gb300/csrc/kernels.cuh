@@ -27,71 +27,124 @@
 
 namespace fftb {
 
-template <typename T> struct Cfg;
-template <> struct Cfg<float> { static constexpr int NT = 256, EPT = 16; };
-template <> struct Cfg<double> { static constexpr int NT = 256, EPT = 8; };
-
-template <typename T, int N> __host__ __device__ constexpr int line_cap() {
-  return (Cfg<T>::NT * Cfg<T>::EPT) / N;
-}
-template <typename T, int N2> __host__ __device__ constexpr int stick_tile_c() {
-  return line_cap<T, N2>() > 128 ? 128 : line_cap<T, N2>();
-}
-
+// ------------------------------------------------------------------ z stage
+// Each occupied (x,y) stick is one length-N2 line held in registers by
+// Line<N2>::G lanes; a warp carries 32 / G consecutive sticks, a CTA 8 warps.
+// No block barrier after the twiddle table load. For a sphere stored stick
+// by stick with consecutive gz (the canonical order of a cutoff sphere) the
+// lanes index the coefficient list directly; otherwise the warp scatters
+// (gathers) its sticks' entries through zeroed scratch rows.
+constexpr int STICK_NW = 8;
+template <int N2> __host__ __device__ constexpr int stick_tile_c2() { return STICK_NW * (32 / Line<N2>::G); }
 template <typename T, int N2> constexpr size_t stick_smem_c() {
   using C = typename cplx<T>::type;
-  return sizeof(C) * ((size_t)N2 * odd_pitch(stick_tile_c<T, N2>()) + N2);
+  return sizeof(C) * ((size_t)STICK_NW * (32 / Line<N2>::G) * Line<N2>::PITCH + N2);
 }
 
-// ------------------------------------------------------------------ z stage
 template <typename T, int N2, int MODE>
-__global__ void __launch_bounds__(Cfg<T>::NT) k_stick(const Launch L) {
+__global__ void __launch_bounds__(STICK_NW * 32) k_stick(const Launch L) {
   using C = typename cplx<T>::type;
-  constexpr int NT = Cfg<T>::NT, EPT = Cfg<T>::EPT;
-  constexpr int TS = stick_tile_c<T, N2>();
-  constexpr int TSP = odd_pitch(TS);
+  using LZ = Line<N2>;
+  constexpr int WZ = 32 / LZ::G, EZ = LZ::E, NT = STICK_NW * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  C* tw = buf + N2 * TSP;
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane % LZ::G, l = lane / LZ::G;
+  C* scr = tw + N2 + warp * WZ * LZ::PITCH;
+  C* row = scr + l * LZ::PITCH;
 
   const int bl = blockIdx.y;
   const int gb = L.band0 + bl;
   const int k = L.g.band_k[gb];
   const KInfo ki = L.g.kinfo[k];
-  const int s0 = blockIdx.x * TS;
-  if (s0 >= ki.S) return;
-  const int ns = min(TS, ki.S - s0);
-
-  const C* tw_g = static_cast<const C*>(L.g.tw2);
-  for (int m = threadIdx.x; m < N2; m += NT) tw[m] = tw_g[m];
-  C* Tb = static_cast<C*>(L.T) + (size_t)bl * N2 * L.g.smax + s0;
-  const int smax = L.g.smax;
+  const int S = ki.S;
+  const int cta_s0 = blockIdx.x * stick_tile_c2<N2>();
+  if (cta_s0 >= S) return;
+  {
+    const C* tw_g = static_cast<const C*>(L.g.tw2);
+    for (int m = threadIdx.x; m < N2; m += NT) tw[m] = tw_g[m];
+  }
+  __syncthreads();
+  const int s0 = cta_s0 + warp * WZ;
+  if (s0 >= S) return;  // whole warp idle (no further block barriers)
+  const int nl = min(WZ, S - s0);
+  const int s = s0 + (l < nl ? l : 0);
+  typename LZ::template TwCache<C> tc;
+  tc.load(g, tw);
+  auto zsigned = [](int z) { return z < N2 - N2 / 2 ? z : z - N2; };
   const int32_t* sent = L.g.stick_ent + ki.stick_base + k;
-  const int e0 = sent[s0], e1 = sent[s0 + ns];
+  const int e0 = sent[s], len = sent[s + 1] - e0;
   const int64_t sph = L.g.band_sph[gb];
-
-  auto mid_ld = [&](int line, int e) -> C { return buf[e * TSP + line]; };
-  auto mid_st = [&](int line, int e, C v) { buf[e * TSP + line] = v; };
+  const bool canon = ki.flags & KF_CANONICAL_STICKS;
+  int p0 = 0, zlo = 0;
+  if (canon) {
+    p0 = L.g.ent_pos[e0];
+    zlo = zsigned((int)((uint32_t)L.g.ent_zs[e0] >> 24));
+  }
+  C* Tb = static_cast<C*>(L.T) + (size_t)bl * N2 * L.g.smax + s;
+  const int smax = L.g.smax;
+  C v[EZ];
 
   if constexpr (MODE == M_G2R) {
     const C* in = static_cast<const C*>(L.sph_in) + sph;
-    for (int m = threadIdx.x; m < N2 * TSP; m += NT) buf[m] = czero<C>();
-    __syncthreads();
-    for (int e = e0 + threadIdx.x; e < e1; e += NT) {
-      const uint32_t zs = (uint32_t)L.g.ent_zs[e];
-      buf[(int)(zs >> 24) * TSP + ((int)(zs & 0xFFFFFFu) - s0)] = in[L.g.ent_pos[e]];
+    if (canon) {
+#pragma unroll
+      for (int m = 0; m < EZ / LZ::R0; ++m)
+#pragma unroll
+        for (int j = 0; j < LZ::R0; ++j) {
+          const int d = zsigned(LZ::first_pos(g, m, j)) - zlo;
+          v[m * LZ::R0 + j] = (unsigned)d < (unsigned)len ? in[p0 + d] : czero<C>();
+        }
+    } else {
+      for (int q = lane; q < WZ * LZ::PITCH; q += 32) scr[q] = czero<C>();
+      __syncwarp();
+      const int ea = sent[s0], eb = sent[s0 + nl];
+      for (int e = ea + lane; e < eb; e += 32) {
+        const uint32_t zs = (uint32_t)L.g.ent_zs[e];
+        scr[((int)(zs & 0xFFFFFFu) - s0) * LZ::PITCH + wpad((int)(zs >> 24))] = in[L.g.ent_pos[e]];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int m = 0; m < EZ / LZ::R0; ++m)
+#pragma unroll
+        for (int j = 0; j < LZ::R0; ++j) v[m * LZ::R0 + j] = row[wpad(LZ::first_pos(g, m, j))];
+      __syncwarp();
     }
-    __syncthreads();
-    auto last = [&](int line, int e, C v) { Tb[(size_t)e * smax + line] = v; };
-    fft_lines<N2, +1, NT, EPT, false, C>(ns, tw, mid_ld, mid_ld, mid_st, last);
+    LZ::template run<+1>(v, g, row, tw, tc);
+    if (l < nl) {
+#pragma unroll
+      for (int m = 0; m < EZ / LZ::RL; ++m)
+#pragma unroll
+        for (int j = 0; j < LZ::RL; ++j) Tb[(size_t)LZ::last_pos(g, m, j) * smax] = v[m * LZ::RL + j];
+    }
   } else {
-    __syncthreads();
-    auto first = [&](int line, int e) -> C { return Tb[(size_t)e * smax + line]; };
-    fft_lines<N2, -1, NT, EPT, false, C>(ns, tw, first, mid_ld, mid_st, mid_st);
+#pragma unroll
+    for (int m = 0; m < EZ / LZ::R0; ++m)
+#pragma unroll
+      for (int j = 0; j < LZ::R0; ++j) v[m * LZ::R0 + j] = Tb[(size_t)LZ::first_pos(g, m, j) * smax];
+    LZ::template run<-1>(v, g, row, tw, tc);
     C* out = static_cast<C*>(L.sph_out) + sph;
-    for (int e = e0 + threadIdx.x; e < e1; e += NT) {
-      const uint32_t zs = (uint32_t)L.g.ent_zs[e];
-      out[L.g.ent_pos[e]] = buf[(int)(zs >> 24) * TSP + ((int)(zs & 0xFFFFFFu) - s0)];
+    if (canon) {
+      if (l < nl) {
+#pragma unroll
+        for (int m = 0; m < EZ / LZ::RL; ++m)
+#pragma unroll
+          for (int j = 0; j < LZ::RL; ++j) {
+            const int d = zsigned(LZ::last_pos(g, m, j)) - zlo;
+            if ((unsigned)d < (unsigned)len) out[p0 + d] = v[m * LZ::RL + j];
+          }
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < EZ / LZ::RL; ++m)
+#pragma unroll
+        for (int j = 0; j < LZ::RL; ++j) row[wpad(LZ::last_pos(g, m, j))] = v[m * LZ::RL + j];
+      __syncwarp();
+      const int ea = sent[s0], eb = sent[s0 + nl];
+      for (int e = ea + lane; e < eb; e += 32) {
+        const uint32_t zs = (uint32_t)L.g.ent_zs[e];
+        out[L.g.ent_pos[e]] = scr[((int)(zs & 0xFFFFFFu) - s0) * LZ::PITCH + wpad((int)(zs >> 24))];
+      }
     }
   }
 }
@@ -114,7 +167,11 @@ __global__ void __launch_bounds__(Cfg<T>::NT) k_stick(const Launch L) {
 template <typename T> struct PlaneCfg { static constexpr int NW = FFTB_PLANE_NW; };
 // resident CTAs per SM the register allocation must allow (measured best)
 template <typename T, int N0> __host__ __device__ constexpr int plane_minb() {
+#ifdef FFTB_PLANE_MINB
+  return FFTB_PLANE_MINB;
+#else
   return sizeof(T) == 8 ? 1 : (N0 <= 64 ? 3 : 2);
+#endif
 }
 
 __host__ __device__ constexpr int a_pitch(int x) { return x + ((2 - x % 16) + 16) % 16; }
@@ -392,7 +449,7 @@ template <typename T> size_t plane_smem_t(int n0, int n1, int xmax, int a_bufs) 
 }
 template <typename T> int stick_tile_t(int n2) {
   switch (n2) {
-#define C_(N) case N: return stick_tile_c<T, N>();
+#define C_(N) case N: return stick_tile_c2<N>();
     FFTB_SIZES(C_)
 #undef C_
   }
@@ -402,8 +459,8 @@ template <typename T> int stick_tile_t(int n2) {
 template <typename T, int N2> cudaError_t go_stick(int mode, const Launch& L, int tiles) {
   const size_t smem = stick_smem_c<T, N2>();
   const dim3 grid(tiles, L.nb);
-  if (mode == M_G2R) k_stick<T, N2, M_G2R><<<grid, Cfg<T>::NT, smem, L.stream>>>(L);
-  else k_stick<T, N2, M_R2G><<<grid, Cfg<T>::NT, smem, L.stream>>>(L);
+  if (mode == M_G2R) k_stick<T, N2, M_G2R><<<grid, STICK_NW * 32, smem, L.stream>>>(L);
+  else k_stick<T, N2, M_R2G><<<grid, STICK_NW * 32, smem, L.stream>>>(L);
   return cudaGetLastError();
 }
 template <typename T, int N> cudaError_t go_plane(int mode, const Launch& L) {

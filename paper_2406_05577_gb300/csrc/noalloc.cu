@@ -114,7 +114,8 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
     return err(FFTB_ERR_UNSUPPORTED, "plane does not fit in shared memory");
 
   // tables, packed like a one-k-point plan
-  KInfo ki{G.S, G.X, 0, 0, 0, G.contiguous_columns ? KF_CONTIGUOUS_COLUMNS : 0};
+  KInfo ki{G.S, G.X, 0, 0, 0,
+           (G.contiguous_columns ? KF_CONTIGUOUS_COLUMNS : 0) | (G.canonical_sticks ? KF_CANONICAL_STICKS : 0)};
   std::vector<int32_t> band_k((size_t)bands, 0);
   std::vector<int64_t> band_sph((size_t)bands);
   for (int b = 0; b < bands; ++b) band_sph[b] = (int64_t)b * G.ngw;
