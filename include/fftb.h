@@ -156,6 +156,26 @@ fftb_status fftb_plan_set_timing(fftb_plan plan, int32_t enable);
  * FFTB_STAGE_KINDS entries), then starts a new accumulation. */
 fftb_status fftb_plan_stage_times(fftb_plan plan, double* ms, int64_t* launches);
 
+/* CUDA-graph execution. When enabled, fftb_execute records its launch
+ * sequence (every band chunk, every stage) into a CUDA graph the first time
+ * it sees a given set of buffers (in, out, cube, potential) and replays the
+ * instantiated graph on later calls with the same buffers; new buffers update
+ * the graph. Recording and instantiation allocate host-side driver
+ * resources. Not used while per-kernel timing is enabled, on the legacy
+ * default stream (NULL), or when `stream` is itself being captured (the
+ * kernels then go into the caller's graph). Disabled by default. */
+fftb_status fftb_plan_set_graph(fftb_plan plan, int32_t enable);
+
+/* Autotuner: times the candidate schedules of this plan -- bands per launch
+ * chunk and persistent CTAs of the plane stage -- with `trials` timed
+ * executes each on device buffers it allocates and frees (at most 4 GiB;
+ * larger batches are tuned on a prefix of the bands), keeps the fastest and
+ * reallocates the plan's scratch to fit. If the environment variable
+ * FFTB_TUNE_CACHE names a file, results are read from and appended to it,
+ * keyed by grid, sphere sizes, bands, direction, precision and device.
+ * Synchronises the device. */
+fftb_status fftb_plan_autotune(fftb_plan plan, int32_t trials);
+
 /* Kernel launches this plan has issued so far (all executes). */
 int64_t fftb_plan_launches(fftb_plan plan);
 

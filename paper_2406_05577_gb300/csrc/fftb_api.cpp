@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
 #include <new>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -97,6 +99,15 @@ struct fftb_plan_s {
   void* d_stage_cube = nullptr;
   size_t stage_in_bytes = 0, stage_out_bytes = 0, stage_cube_bytes = 0;
   int64_t launches = 0;
+  // CUDA-graph execution (fftb_plan_set_graph)
+  bool use_graph = false;
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_in = nullptr;
+  void* g_out = nullptr;
+  void* g_cube = nullptr;
+  const void* g_V = nullptr;
+  int sms = 0;
+  int plane_occ[3] = {0, 0, 0};  // resident plane CTAs per SM: G->r, r->G, apply
   // per-kernel timing (fftb_plan_set_timing)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -130,6 +141,7 @@ void release(fftb_plan_s* p) {
   if (p->d_stage_out) cudaFree(p->d_stage_out);
   if (p->d_stage_cube) cudaFree(p->d_stage_cube);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
   delete p;
 }
 
@@ -304,9 +316,11 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
   if (e != cudaSuccess) { release(p); return cuda_fail(e, "device attribute"); }
   const int modes[3] = {M_G2R, M_R2G, M_APPLY};
+  p->sms = sms;
   for (int i = 0; i < 3; ++i) {
     const int occ = plane_occupancy(p->prec_kernel, modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs);
     if (occ < 1) { release(p); return fail(FFTB_ERR_UNSUPPORTED, "plane kernel cannot be resident on this device"); }
+    p->plane_occ[i] = occ;
     p->plane_ctas[i] = sms * occ;
   }
   e = cudaDeviceSynchronize();
@@ -418,30 +432,17 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
 
 static bool aligned(const void* q, int a) { return (reinterpret_cast<uintptr_t>(q) % (uintptr_t)a) == 0; }
 
-FFTB_EXPORT fftb_status fftb_execute(fftb_plan p, const void* in, void* out, void* cube, void* stream) {
-  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
-  if (p->total_bands == 0) return FFTB_OK;
-  if (!in || !out) return fail(FFTB_ERR_INVALID_ARG, "in and out must be device pointers");
-  if (!aligned(in, p->csize) || !aligned(out, p->csize) || (cube && !aligned(cube, p->csize)))
-    return fail(FFTB_ERR_INVALID_ARG, "buffers must be aligned to the complex element size");
-  if (in == out) return fail(FFTB_ERR_INVALID_ARG, "in and out must not overlap");
-  if (p->dir == FFTB_ROUNDTRIP && !cube) return fail(FFTB_ERR_INVALID_ARG, "ROUNDTRIP needs a cube buffer");
-  if (p->dir != FFTB_ROUNDTRIP && cube) return fail(FFTB_ERR_INVALID_ARG, "cube buffer only for ROUNDTRIP");
-  if (p->dir == FFTB_APPLY_LOCAL && !p->d_V) return fail(FFTB_ERR_INVALID_ARG, "APPLY_LOCAL needs fftb_set_potential");
-  int dev = -1;
-  cudaGetDevice(&dev);
-  if (dev != p->device) return fail(FFTB_ERR_INVALID_ARG, "current device differs from the plan's device");
-
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+// Enqueues every band chunk's stages for the first `bands` bands.
+static fftb_status enqueue(fftb_plan_s* p, int bands, const void* in, void* out, void* cube, cudaStream_t s) {
   Launch L{};
   L.g = p->g;
   L.T = p->d_T;
   L.V = p->d_V;
   L.a_bufs = p->a_bufs;
   L.stream = s;
-  for (int b0 = 0; b0 < p->total_bands; b0 += p->chunk) {
+  for (int b0 = 0; b0 < bands; b0 += p->chunk) {
     L.band0 = b0;
-    L.nb = std::min(p->chunk, p->total_bands - b0);
+    L.nb = std::min(p->chunk, bands - b0);
     cudaError_t e = cudaSuccess;
     switch (p->dir) {
       case FFTB_G_TO_R:
@@ -477,6 +478,70 @@ FFTB_EXPORT fftb_status fftb_execute(fftb_plan p, const void* in, void* out, voi
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   }
   return FFTB_OK;
+}
+
+// Direct launches, or the recorded CUDA graph of this buffer set.
+static fftb_status launch_all(fftb_plan_s* p, int bands, const void* in, void* out, void* cube, cudaStream_t s) {
+  bool graph = p->use_graph && !p->timing && s != nullptr && bands == p->total_bands;
+  if (graph) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) graph = false;
+  }
+  if (!graph) return enqueue(p, bands, in, out, cube, s);
+  const int64_t per_exec = (int64_t)((p->total_bands + p->chunk - 1) / p->chunk) * kernels_per_chunk(p->dir);
+  if (!(p->gexec && p->g_in == in && p->g_out == out && p->g_cube == cube && p->g_V == p->d_V)) {
+    const int64_t before = p->launches;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    fftb_status st = enqueue(p, bands, in, out, cube, s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    p->launches = before;
+    if (st != FFTB_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture end");
+    if (p->gexec) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(p->gexec, g, &info) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+      }
+    }
+    if (!p->gexec) e = cudaGraphInstantiate(&p->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      p->gexec = nullptr;
+      return cuda_fail(e, "graph instantiate");
+    }
+    p->g_in = in;
+    p->g_out = out;
+    p->g_cube = cube;
+    p->g_V = p->d_V;
+  }
+  cudaError_t e = cudaGraphLaunch(p->gexec, s);
+  if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  p->launches += per_exec;
+  return FFTB_OK;
+}
+
+FFTB_EXPORT fftb_status fftb_execute(fftb_plan p, const void* in, void* out, void* cube, void* stream) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (p->total_bands == 0) return FFTB_OK;
+  if (!in || !out) return fail(FFTB_ERR_INVALID_ARG, "in and out must be device pointers");
+  if (!aligned(in, p->csize) || !aligned(out, p->csize) || (cube && !aligned(cube, p->csize)))
+    return fail(FFTB_ERR_INVALID_ARG, "buffers must be aligned to the complex element size");
+  if (in == out) return fail(FFTB_ERR_INVALID_ARG, "in and out must not overlap");
+  if (p->dir == FFTB_ROUNDTRIP && !cube) return fail(FFTB_ERR_INVALID_ARG, "ROUNDTRIP needs a cube buffer");
+  if (p->dir != FFTB_ROUNDTRIP && cube) return fail(FFTB_ERR_INVALID_ARG, "cube buffer only for ROUNDTRIP");
+  if (p->dir == FFTB_APPLY_LOCAL && !p->d_V) return fail(FFTB_ERR_INVALID_ARG, "APPLY_LOCAL needs fftb_set_potential");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != p->device) return fail(FFTB_ERR_INVALID_ARG, "current device differs from the plan's device");
+
+  return launch_all(p, p->total_bands, in, out, cube, static_cast<cudaStream_t>(stream));
 }
 
 static fftb_status ensure(void** ptr, size_t* have, size_t need) {
@@ -592,5 +657,196 @@ FFTB_EXPORT fftb_status fftb_plan_stage_times(fftb_plan p, double* ms, int64_t* 
   }
   p->recs.clear();
   p->ev_used = 0;
+  return FFTB_OK;
+}
+
+FFTB_EXPORT fftb_status fftb_plan_set_graph(fftb_plan p, int32_t enable) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  p->use_graph = enable != 0;
+  return FFTB_OK;
+}
+
+namespace {
+
+std::string tune_key(const fftb_plan_s* p) {
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, p->device);
+  std::ostringstream k;
+  k << p->n[0] << "x" << p->n[1] << "x" << p->n[2] << "|S" << p->smax << "|X" << p->xmax << "|B" << p->total_bands
+    << "|K" << p->nk << "|d" << (int)p->dir << "|p" << (int)p->prec << "|" << prop.name;
+  std::string out = k.str();
+  for (char& c : out)
+    if (c == ' ') c = '_';
+  return out;
+}
+
+bool tune_cache_lookup(const std::string& key, int* chunk, int ctas[3]) {
+  const char* path = std::getenv("FFTB_TUNE_CACHE");
+  if (!path || !*path) return false;
+  std::ifstream f(path);
+  std::string line;
+  bool found = false;
+  while (std::getline(f, line)) {
+    std::istringstream ls(line);
+    std::string k;
+    int c, a, b, d;
+    if ((ls >> k >> c >> a >> b >> d) && k == key) {
+      *chunk = c;
+      ctas[0] = a;
+      ctas[1] = b;
+      ctas[2] = d;
+      found = true;  // the last entry wins
+    }
+  }
+  return found;
+}
+
+void tune_cache_store(const std::string& key, int chunk, const int ctas[3]) {
+  const char* path = std::getenv("FFTB_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::ofstream f(path, std::ios::app);
+  f << key << " " << chunk << " " << ctas[0] << " " << ctas[1] << " " << ctas[2] << "\n";
+}
+
+fftb_status resize_T(fftb_plan_s* p, int chunk) {
+  const size_t need = (size_t)chunk * p->n[2] * std::max<int32_t>(p->smax, 1) * p->csize;
+  if (need <= p->T_bytes) return FFTB_OK;
+  if (p->d_T) cudaFree(p->d_T);
+  p->d_T = nullptr;
+  p->T_bytes = 0;
+  if (cudaMalloc(&p->d_T, need) != cudaSuccess) return fail(FFTB_ERR_ALLOC, "cudaMalloc stick scratch failed");
+  p->T_bytes = need;
+  return FFTB_OK;
+}
+
+}  // namespace
+
+FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (trials < 1) return fail(FFTB_ERR_INVALID_ARG, "trials must be >= 1");
+  if (p->total_bands == 0) return FFTB_OK;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != p->device) return fail(FFTB_ERR_INVALID_ARG, "current device differs from the plan's device");
+  const std::string key = tune_key(p);
+  int chunk = 0, ctas[3] = {0, 0, 0};
+  if (tune_cache_lookup(key, &chunk, ctas)) {
+    fftb_status st = resize_T(p, chunk);
+    if (st != FFTB_OK) return st;
+    p->chunk = chunk;
+    for (int i = 0; i < 3; ++i) p->plane_ctas[i] = ctas[i];
+    if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+    return FFTB_OK;
+  }
+  // trial buffers: the whole batch, or the longest band prefix within 4 GiB
+  const int64_t vol = (int64_t)p->n[0] * p->n[1] * p->n[2];
+  int64_t max_ngw = 0;
+  for (const auto& G : p->geo) max_ngw = std::max(max_ngw, G.ngw);
+  const bool cube_io = p->dir == FFTB_G_TO_R || p->dir == FFTB_R_TO_G || p->dir == FFTB_ROUNDTRIP;
+  const size_t band_bytes = (size_t)p->csize * (2 * max_ngw + (cube_io ? vol : 0));
+  const size_t budget = (size_t)4 << 30;
+  const int bands = (int)std::max<int64_t>(1, std::min<int64_t>(p->total_bands, (int64_t)(budget / std::max<size_t>(band_bytes, 1))));
+  const size_t sph_b = (size_t)p->sphere_elems * p->csize;  // prefix offsets stay inside
+  const size_t cube_b = (size_t)bands * vol * p->csize;
+  const size_t in_b = p->dir == FFTB_R_TO_G ? cube_b : std::min(sph_b, (size_t)bands * max_ngw * p->csize + 256);
+  const size_t out_b = p->dir == FFTB_G_TO_R ? cube_b : std::min(sph_b, (size_t)bands * max_ngw * p->csize + 256);
+  void *d_in = nullptr, *d_out = nullptr, *d_cube = nullptr, *d_v = nullptr;
+  auto cleanup = [&]() {
+    if (d_in) cudaFree(d_in);
+    if (d_out) cudaFree(d_out);
+    if (d_cube) cudaFree(d_cube);
+    if (d_v) cudaFree(d_v);
+  };
+  // a band prefix may still index the whole sphere batch: size for the real offsets
+  const size_t in_full = p->dir == FFTB_R_TO_G ? cube_b : sph_b;
+  const size_t out_full = p->dir == FFTB_G_TO_R ? cube_b : sph_b;
+  (void)in_b;
+  (void)out_b;
+  if (cudaMalloc(&d_in, in_full) != cudaSuccess || cudaMalloc(&d_out, out_full) != cudaSuccess ||
+      (p->dir == FFTB_ROUNDTRIP && cudaMalloc(&d_cube, cube_b) != cudaSuccess)) {
+    cleanup();
+    return fail(FFTB_ERR_ALLOC, "autotune buffers");
+  }
+  cudaMemset(d_in, 0, in_full);
+  const void* saved_v = p->d_V;
+  if (p->dir == FFTB_APPLY_LOCAL && !p->d_V) {
+    if (cudaMalloc(&d_v, (size_t)vol * p->csize / 2) != cudaSuccess) {
+      cleanup();
+      return fail(FFTB_ERR_ALLOC, "autotune potential");
+    }
+    cudaMemset(d_v, 0, (size_t)vol * p->csize / 2);
+    p->d_V = d_v;
+  }
+  // candidates
+  std::vector<int> chunks;
+  const size_t t_band = (size_t)p->n[2] * std::max<int32_t>(p->smax, 1) * p->csize;
+  for (int c : {bands, (bands + 1) / 2, (bands + 3) / 4, (int)((24u << 20) / t_band), (int)((48u << 20) / t_band),
+                (int)((96u << 20) / t_band)}) {
+    c = std::max(1, std::min(c, bands));
+    if (std::find(chunks.begin(), chunks.end(), c) == chunks.end()) chunks.push_back(c);
+  }
+  std::vector<int> mults;
+  const int mi = p->dir == FFTB_R_TO_G ? 1 : p->dir == FFTB_APPLY_LOCAL ? 2 : 0;
+  for (int m : {p->plane_occ[mi], p->plane_occ[mi] - 1, 0})
+    if (m >= 0 && std::find(mults.begin(), mults.end(), m) == mults.end() && !(m == 0 && false)) mults.push_back(m);
+  int max_chunk = *std::max_element(chunks.begin(), chunks.end());
+  fftb_status st = resize_T(p, max_chunk);
+  if (st != FFTB_OK) {
+    p->d_V = saved_v;
+    cleanup();
+    return st;
+  }
+  const int saved_chunk = p->chunk;
+  int saved_ctas[3] = {p->plane_ctas[0], p->plane_ctas[1], p->plane_ctas[2]};
+  const bool saved_timing = p->timing, saved_graph = p->use_graph;
+  const int64_t saved_launches = p->launches;
+  p->timing = false;
+  p->use_graph = false;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_chunk = saved_chunk, best_ctas[3] = {saved_ctas[0], saved_ctas[1], saved_ctas[2]};
+  for (int c : chunks) {
+    for (int m : mults) {
+      p->chunk = c;
+      for (int i = 0; i < 3; ++i) p->plane_ctas[i] = m == 0 ? 0 : p->sms * std::min(m, p->plane_occ[i]);
+      st = enqueue(p, bands, d_in, d_out, d_cube, nullptr);
+      if (st != FFTB_OK) break;
+      cudaEventRecord(e0, nullptr);
+      for (int t = 0; t < trials && st == FFTB_OK; ++t) st = enqueue(p, bands, d_in, d_out, d_cube, nullptr);
+      cudaEventRecord(e1, nullptr);
+      cudaError_t ce = cudaEventSynchronize(e1);
+      if (st != FFTB_OK || ce != cudaSuccess) {
+        if (ce != cudaSuccess) st = cuda_fail(ce, "autotune run");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_chunk = c;
+        for (int i = 0; i < 3; ++i) best_ctas[i] = p->plane_ctas[i];
+      }
+    }
+    if (st != FFTB_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->timing = saved_timing;
+  p->use_graph = saved_graph;
+  p->launches = saved_launches;
+  p->d_V = saved_v;
+  cleanup();
+  if (st != FFTB_OK) {
+    p->chunk = saved_chunk;
+    for (int i = 0; i < 3; ++i) p->plane_ctas[i] = saved_ctas[i];
+    return st;
+  }
+  // a chunk tuned on a band prefix covers the whole batch too
+  p->chunk = best_chunk;
+  for (int i = 0; i < 3; ++i) p->plane_ctas[i] = best_ctas[i];
+  if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+  tune_cache_store(key, best_chunk, best_ctas);
   return FFTB_OK;
 }

@@ -74,6 +74,8 @@ EXPORTS = {
     "fftb_plan_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fftb_g2r_noalloc": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_double, ctypes.c_void_p,
                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "fftb_plan_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "fftb_plan_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fftb_sphere_enumerate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_double,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                              ctypes.POINTER(ctypes.c_int64)]),
@@ -206,6 +208,14 @@ def fftb_plan_stage_times(plan):
     return {k: (float(m), int(c)) for k, m, c in zip(STAGE_KINDS, ms, cnt)}
 
 
+def fftb_plan_set_graph(plan, enable):
+    _check(lib().fftb_plan_set_graph(plan, 1 if enable else 0))
+
+
+def fftb_plan_autotune(plan, trials=3):
+    _check(lib().fftb_plan_autotune(plan, int(trials)))
+
+
 def fftb_plan_launches(plan):
     return int(lib().fftb_plan_launches(plan))
 
@@ -312,6 +322,13 @@ class Plan:
 
     def launches(self):
         return fftb_plan_launches(self.handle)
+
+    def set_graph(self, enable=True):
+        fftb_plan_set_graph(self.handle, enable)
+
+    def autotune(self, trials=3):
+        fftb_plan_autotune(self.handle, trials)
+        self.info = fftb_plan_get_info(self.handle)
 
     def close(self):
         if self.handle:

@@ -194,3 +194,49 @@ def test_host_buffer_entry_point(F):
     F.fftb_execute_host(plan.handle, xin.ctypes.data, xout.ctypes.data, None, None)
     assert relerr(xout, np.prod(n) * xin) <= 1e-12
     assert plan.launches() == plan.info["kernels_per_execute"]
+
+
+def test_graph_replay_and_update(F):
+    import torch
+    n, r, bands = (32, 32, 48), 10.0, 6
+    g = oracle.sphere_gvectors(n, r)
+    c = fi.complex_gaussian((bands, len(g)), 81).astype(np.complex64)
+    plan = F.Plan(n, "roundtrip", "fp32", radius=r, bands=[bands], max_chunk_bands=4)
+    plan.set_graph(True)
+    x = torch.from_numpy(c.reshape(-1)).cuda()
+    outs = [torch.empty_like(x) for _ in range(2)]
+    cube = torch.empty(plan.info["cube_elems"], dtype=torch.complex64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan.execute(x, outs[0], cube)   # records and instantiates
+        plan.execute(x, outs[0], cube)   # replays
+        plan.execute(x, outs[1], cube)   # new buffers: graph update
+    torch.cuda.synchronize()
+    want = np.prod(n) * c.reshape(-1).astype(np.complex128)
+    for o in outs:
+        assert relerr(o.cpu().numpy(), want) <= TOL["fp32"]
+    assert relerr(cube.cpu().numpy(), oracle.g2r(g, c.astype(np.complex128), n).reshape(-1)) <= TOL["fp32"]
+    assert plan.launches() == 3 * plan.info["kernels_per_execute"]
+
+
+def test_autotune_keeps_results(F, tmp_path, monkeypatch):
+    import torch
+    monkeypatch.setenv("FFTB_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    n, r = (24, 24, 24), 6.0
+    ks = fi.kshifts(3, seed=9)
+    bands = [5, 2, 7]
+    gs = [oracle.sphere_gvectors(n, r, k) for k in ks]
+    cs = [fi.complex_gaussian((b, len(gk)), 90 + i) for i, (gk, b) in enumerate(zip(gs, bands))]
+    x = np.concatenate([c.reshape(-1) for c in cs])
+    for attempt in range(2):  # second plan reads the cache
+        plan = F.Plan(n, "g2r", "fp64", radius=r, kshift=ks, bands=bands)
+        plan.autotune(2)
+        assert 1 <= plan.info["chunk_bands"] <= 14
+        xd = torch.from_numpy(x).cuda()
+        out = torch.empty(plan.info["cube_elems"], dtype=torch.complex128, device="cuda")
+        plan.execute(xd, out)
+        torch.cuda.synchronize()
+        want = np.concatenate([oracle.g2r(gk, c, n).reshape(-1) for gk, c in zip(gs, cs)])
+        assert relerr(out.cpu().numpy(), want) <= TOL["fp64"]
+    lines = (tmp_path / "tune.txt").read_text().splitlines()
+    assert len(lines) == 1 and lines[0].startswith("24x24x24|")
