@@ -1,12 +1,15 @@
-"""Benchmark: batched pruned sphere <-> cube FFT, G -> r -> G, bands/s.
+"""Benchmark: batched pruned sphere <-> cube FFT, bands/s.
 
-Workload (one GPU): 64^3 grid, cutoff |G| <= 16 (17077 G vectors), 64 bands,
-FP32, coefficients complex Gaussian x exp(-|G|^2/(2*64)), round trip
-G -> r -> G with the real-space cube written to HBM and read back. A step is
-one fftb_execute of the whole batch. Under torchrun each rank runs its own 64
-bands on its own GPU (bands are independent: weak scaling, no collective on
-the data path).
+Default workload (the headline): 64^3 grid, cutoff |G| <= 16 (17077 G
+vectors), 64 bands, FP32, coefficients complex Gaussian x exp(-|G|^2/(2*64)),
+round trip G -> r -> G with the real-space cube written to HBM and read back.
+A step is one fftb_execute of the whole batch. Other workloads
+(``--workload``): 96^3 with 8 k-points and uneven band counts in one graph-
+replayed, autotuned launch sequence; 128^3 local-potential apply
+V(r) psi(r) with 256 bands; 160^3 with 512 bands streamed in band chunks.
 
+Under torchrun each rank runs its own copy of the workload on its own GPU
+(bands are independent: weak scaling, no collective on the data path).
 Timing follows the paper's protocol (Sec. 4.2: warm-up iterations, then
 timed iterations, mean) with CUDA events on the launching stream; L2 is
 flushed between timed steps. ``--impl reference`` times the FP64 CPU oracle
@@ -32,14 +35,61 @@ sys.path.insert(0, ROOT)
 import fftb_inputs as fi  # noqa: E402
 
 METRIC = "sphere-FFT bands/sec (G->r->G) and % HBM roofline, mixed vs FP64 at L2<=1e-5"
-N, RADIUS, BANDS, SEED = (64, 64, 64), 16.0, 64, 2
-WORKLOAD = "64^3 grid, |G|<=16 (17077 G), 64 bands, G->r->G round trip, cube kept in HBM"
 L2_FLUSH_BYTES = 256 << 20
 
 
-def workload_inputs(g):
-    c = fi.complex_gaussian((BANDS, len(g)), SEED) * fi.gaussian_envelope(g, 8.0)[None, :]
-    return c
+class Workload:
+    """One benchmark configuration: grid, spheres, bands, direction."""
+
+    def __init__(self, name):
+        self.name = name
+        if name == "sphere64_rt":
+            self.n, self.radius, self.kshift, self.bands = (64, 64, 64), 16.0, None, [64]
+            self.direction, self.desc = "roundtrip", \
+                "64^3 grid, |G|<=16 (17077 G), 64 bands, G->r->G round trip, cube kept in HBM"
+            self.envelope, self.seed, self.graph, self.tune = 8.0, 2, False, False
+        elif name == "sphere96_multik":
+            self.n, self.radius = (96, 96, 96), 24.0
+            self.kshift = fi.kshifts(8, 3)
+            self.bands = [int(b) for b in fi.band_counts(8, 16, 128, 3)]
+            self.direction = "roundtrip"
+            self.desc = ("96^3 grid, 8 k-points k~U[-0.5,0.5)^3, |G+k|<=24, bands per k-point U{16..128} "
+                         f"({sum(self.bands)} total), G->r->G, one graph-replayed autotuned launch sequence")
+            self.envelope, self.seed, self.graph, self.tune = None, 3, True, True
+        elif name == "sphere128_apply":
+            self.n, self.radius, self.kshift, self.bands = (128, 128, 128), 32.0, None, [256]
+            self.direction = "apply"
+            self.desc = ("128^3 grid, |G|<=32 (137065 G), 256 bands, psi_G -> V(r) psi(r) -> G sphere, "
+                         "V = 32 Gaussians of width 4, cube never stored")
+            self.envelope, self.seed, self.graph, self.tune = None, 4, False, False
+        elif name == "sphere160_large":
+            self.n, self.radius, self.kshift, self.bands = (160, 160, 160), 40.0, None, [512]
+            self.direction = "roundtrip"
+            self.desc = ("160^3 grid, |G|<=40 (267761 G), 512 bands, G->r->G with the 16.8 GB cube set "
+                         "kept in HBM, processed in band chunks")
+            self.envelope, self.seed, self.graph, self.tune = None, 5, False, True
+        else:
+            raise SystemExit(f"unknown workload {name}")
+        self.total_bands = sum(self.bands)
+        self.nk = len(self.bands)
+
+    def plan_kw(self):
+        kw = dict(radius=self.radius, bands=self.bands)
+        if self.kshift is not None:
+            kw["kshift"] = self.kshift
+        return kw
+
+    def coefficients(self, spheres):
+        parts = []
+        for k, (g, b) in enumerate(zip(spheres, self.bands)):
+            c = fi.complex_gaussian((b, len(g)), self.seed + 100 * k)
+            if self.envelope:
+                c = c * fi.gaussian_envelope(g, self.envelope)[None, :]
+            parts.append(c)
+        return parts
+
+    def potential(self):
+        return fi.gaussian_potential(self.n, 32, 4.0, seed=self.seed)
 
 
 def peaks():
@@ -52,19 +102,19 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fft_core.cuh", "kernels.cuh"):
+    for f in ("fft_core.cuh", "line_fft.cuh", "kernels.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2406_05577_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
+def ncu_traffic(workload, kernel):
     """DRAM bytes per band of one kernel from the committed ncu summary, or
-    None when the kernel source changed since the capture."""
+    None when the kernel sources changed since the capture."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    if d.get("kernel_source_hash") != kernel_source_hash():
+    if d.get("kernel_source_hash") != kernel_source_hash() or d.get("workload") != workload:
         return None
     k = d.get("kernels", {}).get(kernel)
     return None if k is None else k.get("dram_bytes_per_band")
@@ -76,12 +126,13 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, bus_id=None):
+    def __init__(self):
         self.rows = []
         self.proc = None
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
-        if bus_id:
-            cmd += ["-i", bus_id]
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis and vis.split(",")[0].strip().isdigit():
+            cmd += ["-i", vis.split(",")[0].strip()]
         try:
             self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
@@ -113,13 +164,25 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def time_oracle(g, c, budget_s):
-    """Bands/s of the FP64 oracle round trip over a bounded sample."""
+def oracle_step(w, spheres, parts, v, bands_idx):
+    """The FP64 oracle on the listed (k, band) pairs of the workload."""
     import oracle
+    for k, b in bands_idx:
+        if w.direction == "apply":
+            oracle.apply_potential(spheres[k], parts[k][b], v, w.n)
+        else:
+            oracle.roundtrip(spheres[k], parts[k][b], w.n)
+
+
+def band_list(w):
+    return [(k, b) for k in range(w.nk) for b in range(w.bands[k])]
+
+
+def time_oracle(w, spheres, parts, v, budget_s):
+    allb = band_list(w)
     done, t0 = 0, time.perf_counter()
     while True:
-        b = done % BANDS
-        oracle.roundtrip(g, c[b], N)
+        oracle_step(w, spheres, parts, v, [allb[done % len(allb)]])
         done += 1
         el = time.perf_counter() - t0
         if el >= budget_s:
@@ -131,14 +194,18 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    g = oracle.sphere_gvectors(N, RADIUS)
-    c = workload_inputs(g)
-    sample = 16
+    w = Workload(args.workload)
+    ks = w.kshift if w.kshift is not None else [(0.0, 0.0, 0.0)]
+    spheres = [oracle.sphere_gvectors(w.n, w.radius, k) for k in ks]
+    parts = w.coefficients(spheres)
+    v = w.potential().astype(np.float32).astype(np.float64) if w.direction == "apply" else None
+    allb = band_list(w)
+    sample = {"sphere64_rt": 16, "sphere96_multik": 4, "sphere128_apply": 2, "sphere160_large": 1}[w.name]
     times = []
     for step in range(args.warmup + args.steps):
+        idx = [allb[(step * sample + i) % len(allb)] for i in range(sample)]
         t0 = time.perf_counter()
-        for b in range(sample):
-            oracle.roundtrip(g, c[(step * sample + b) % BANDS], N)
+        oracle_step(w, spheres, parts, v, idx)
         if step >= args.warmup:
             times.append(time.perf_counter() - t0)
     ms = 1e3 * sum(times) / len(times)
@@ -146,7 +213,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "bands/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": list(N), "radius": RADIUS, "bands": BANDS,
+            "config": {"workload": w.desc, "grid": list(w.n), "radius": w.radius, "bands": w.total_bands,
                        "precision": "fp64 (CPU oracle)", "step_sample_bands": sample},
             "cpu_baseline": {"value": value, "unit": "bands/s", "cores": 1, "kind": "oracle",
                              "sample": f"{sample} bands of the workload per step, numpy pocketfft FP64"},
@@ -154,13 +221,30 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def stage_bytes(kind, plan_info, ngw, S):
-    """Algorithmic (compulsory) bytes per band of one kernel kind."""
-    c = plan_info["complex_bytes"]
-    vol = N[0] * N[1] * N[2]
-    return {"stick_g2r": (ngw + S * N[2]) * c, "plane_g2r": (S * N[2] + vol) * c,
-            "plane_r2g": (vol + S * N[2]) * c, "stick_r2g": (S * N[2] + ngw) * c,
-            "plane_apply": 2 * S * N[2] * c}[kind]
+def stage_bytes(kind, w, info, ngws, sticks):
+    """Algorithmic (compulsory) bytes of one stage kind over the whole batch."""
+    c = info["complex_bytes"]
+    vol = w.n[0] * w.n[1] * w.n[2]
+    n2 = w.n[2]
+    sph = sum(b * g for b, g in zip(w.bands, ngws))
+    stk = sum(b * s * n2 for b, s in zip(w.bands, sticks))
+    cube = w.total_bands * vol
+    return {"stick_g2r": (sph + stk) * c, "plane_g2r": (stk + cube) * c, "plane_r2g": (cube + stk) * c,
+            "stick_r2g": (stk + sph) * c, "plane_apply": 2 * stk * c + vol * c // 2}[kind]
+
+
+def make_plan(fftb, w, prec, dev):
+    import torch
+    plan = fftb.Plan(w.n, w.direction, prec, **w.plan_kw())
+    v_dev = None
+    if w.direction == "apply":
+        v_dev = torch.from_numpy(w.potential().astype(np.float32 if prec == "fp32" else np.float64)).to(dev)
+        plan.set_potential(v_dev)
+    if w.tune:
+        plan.autotune(3)
+    if w.graph:
+        plan.set_graph(True)
+    return plan, v_dev
 
 
 def run_ours(args):
@@ -179,32 +263,38 @@ def run_ours(args):
     build.build()
     from paper_2406_05577_gb300 import fftb
 
-    plan = fftb.Plan(N, "roundtrip", "fp32", radius=RADIUS, bands=[BANDS])
+    w = Workload(args.workload)
+    plan, v_dev = make_plan(fftb, w, "fp32", dev)
     info = plan.info
-    g = plan.sphere(0)
-    S = info["max_sticks"]
-    c = workload_inputs(g).astype(np.complex64)
-    x = torch.from_numpy(c.reshape(-1)).to(dev)
+    spheres = [plan.sphere(k) for k in range(w.nk)]
+    ngws = [len(g) for g in spheres]
+    sticks = [fftb.fftb_sphere_sticks(w.n, g)[0] for g in spheres]
+    parts = w.coefficients(spheres)
+    c = np.concatenate([p.reshape(-1) for p in parts]).astype(np.complex64)
+    x = torch.from_numpy(c).to(dev)
     out = torch.empty_like(x)
-    cube = torch.empty(info["cube_elems"], dtype=torch.complex64, device=dev)
+    cube = None
+    if w.direction == "roundtrip":
+        cube = torch.empty(info["cube_elems"], dtype=torch.complex64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     for _ in range(args.warmup):
         plan.execute(x, out, cube)
     torch.cuda.synchronize(dev)
-    # correctness of this very run: round trip returns N0 N1 N2 * c
-    err = (torch.linalg.vector_norm(out - float(np.prod(N)) * x) /
-           torch.linalg.vector_norm(float(np.prod(N)) * x)).item()
+    # correctness of this very run
+    if w.direction == "roundtrip":
+        vol = float(np.prod(w.n))
+        err = (torch.linalg.vector_norm(out - vol * x) / torch.linalg.vector_norm(vol * x)).item()
+    else:
+        import oracle
+        v64 = w.potential().astype(np.float32).astype(np.float64)
+        got = out[: 2 * ngws[0]].cpu().numpy().astype(np.complex128).reshape(2, -1)
+        want = oracle.apply_potential(spheres[0], c[: 2 * ngws[0]].astype(np.complex128).reshape(2, -1), v64, w.n)
+        err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
 
-    bus = None
-    try:
-        bus = torch.cuda.get_device_properties(dev).pci_bus_id  # may not exist on older torch
-    except Exception:
-        bus = None
-    sampler = ClockSampler(None)
-    fftb.fftb_plan_set_timing(plan.handle, True)
-    fftb.fftb_plan_stage_times(plan.handle)  # reset
+    # timed region 1: steps bracketed by events, L2 flushed in between
+    sampler = ClockSampler()
     launches0 = plan.launches()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
@@ -220,90 +310,109 @@ def run_ours(args):
         dist.barrier()
     clocks = sampler.stop()
     launches = plan.launches() - launches0
-    stage = fftb.fftb_plan_stage_times(plan.handle)
-    fftb.fftb_plan_set_timing(plan.handle, False)
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = sum(step_ms) / len(step_ms)
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = t.item()
-    value = world * BANDS / (ms / 1e3)
+    value = world * w.total_bands / (ms / 1e3)
 
-    # dominant kernel roofline (algorithmic bytes / live event duration)
+    # per-kernel event times over the same steps (graphs off while timing)
+    fftb.fftb_plan_set_timing(plan.handle, True)
+    fftb.fftb_plan_stage_times(plan.handle)
+    for i in range(args.steps):
+        flush.zero_()
+        plan.execute(x, out, cube)
+    stage = fftb.fftb_plan_stage_times(plan.handle)
+    fftb.fftb_plan_set_timing(plan.handle, False)
+
     hbm, peak_kind = peaks()
     dom = max((k for k in stage if stage[k][1] > 0), key=lambda k: stage[k][0])
     dom_ms, dom_n = stage[dom]
-    per_launch_bands = BANDS / (dom_n / args.steps)
-    alg = stage_bytes(dom, info, len(g), S) * per_launch_bands
+    alg = stage_bytes(dom, w, info, ngws, sticks) / (dom_n / args.steps)  # per launch
     achieved = alg / (dom_ms / dom_n / 1e3) / 1e9
-    traffic_band = ncu_traffic(dom)
-    vol = N[0] * N[1] * N[2]
-    step_bytes = 2 * (len(g) + vol) * 8 * BANDS
+    traffic_band = ncu_traffic(w.name, dom)
+    launch_bands = w.total_bands / (dom_n / args.steps)
+    vol = w.n[0] * w.n[1] * w.n[2]
+    sph_elems = sum(b * g for b, g in zip(w.bands, ngws))
+    if w.direction == "apply":
+        step_bytes = 2 * sph_elems * 8 + vol * 4
+    else:
+        step_bytes = 2 * (sph_elems + w.total_bands * vol) * 8
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "peak_source": peak_kind,
-                "traffic": None if traffic_band is None else traffic_band * per_launch_bands,
+                "traffic": None if traffic_band is None else traffic_band * launch_bands,
                 "stage_ms_per_step": {k: v[0] / args.steps for k, v in stage.items() if v[1]},
                 "step_compulsory_gbs": step_bytes / (ms / 1e3) / 1e9,
                 "step_compulsory_frac": step_bytes / (ms / 1e3) / 1e9 / hbm}
 
-    line = None
     if rank == 0:
         # FP64 GPU path on the same workload (the comparison the metric names)
-        p64 = fftb.Plan(N, "roundtrip", "fp64", radius=RADIUS, bands=[BANDS])
-        x64 = torch.from_numpy(workload_inputs(g).reshape(-1)).to(dev)
-        o64 = torch.empty_like(x64)
-        cube64 = torch.empty(p64.info["cube_elems"], dtype=torch.complex128, device=dev)
-        for _ in range(3):
-            p64.execute(x64, o64, cube64)
-        e64 = []
-        for _ in range(5):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            p64.execute(x64, o64, cube64)
-            b.record(stream)
-            e64.append((a, b))
-        torch.cuda.synchronize(dev)
-        ms64 = sum(a.elapsed_time(b) for a, b in e64) / len(e64)
-        del cube64, o64, x64, p64
+        fp64 = None
+        try:
+            p64, v64d = make_plan(fftb, w, "fp64", dev)
+            x64 = torch.from_numpy(np.concatenate([p.reshape(-1) for p in parts])).to(dev)
+            o64 = torch.empty_like(x64)
+            cube64 = None
+            if w.direction == "roundtrip":
+                cube64 = torch.empty(p64.info["cube_elems"], dtype=torch.complex128, device=dev)
+            for _ in range(2):
+                p64.execute(x64, o64, cube64)
+            e64 = []
+            for _ in range(3):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                p64.execute(x64, o64, cube64)
+                b.record(stream)
+                e64.append((a, b))
+            torch.cuda.synchronize(dev)
+            ms64 = sum(a.elapsed_time(b) for a, b in e64) / len(e64)
+            fp64 = {"value": w.total_bands / (ms64 / 1e3), "ms_per_step": ms64, "ratio_fp32_over_fp64": ms64 / ms}
+            del cube64, o64, x64, p64, v64d
+        except fftb.FFTBError as e:
+            fp64 = {"unavailable": str(e)}
 
         # end to end through the C ABI with host buffers (copies in the timed region)
-        pin_in = torch.from_numpy(c.reshape(-1)).pin_memory()
+        pin_in = torch.from_numpy(c).pin_memory()
         pin_out = torch.empty_like(pin_in).pin_memory()
+        cptr = None if cube is None else cube.data_ptr()
         for _ in range(2):
-            fftb.fftb_execute_host(plan.handle, pin_in.data_ptr(), pin_out.data_ptr(), cube.data_ptr(),
-                                   stream.cuda_stream)
+            fftb.fftb_execute_host(plan.handle, pin_in.data_ptr(), pin_out.data_ptr(), cptr, stream.cuda_stream)
         t_e2e = []
-        for _ in range(args.steps):
+        for _ in range(max(3, min(args.steps, 10))):
             flush.zero_()
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            fftb.fftb_execute_host(plan.handle, pin_in.data_ptr(), pin_out.data_ptr(), cube.data_ptr(),
-                                   stream.cuda_stream)
+            fftb.fftb_execute_host(plan.handle, pin_in.data_ptr(), pin_out.data_ptr(), cptr, stream.cuda_stream)
             t_e2e.append(time.perf_counter() - t0)
         e2e_s = sum(t_e2e) / len(t_e2e)
         nbytes = pin_in.numel() * 8
 
         cpu = None
         if world == 1:
-            import oracle  # noqa: F401
-            rate, done, el = time_oracle(g, workload_inputs(g), budget_s=10.0)
+            import oracle
+            ks = w.kshift if w.kshift is not None else [(0.0, 0.0, 0.0)]
+            osph = [oracle.sphere_gvectors(w.n, w.radius, k) for k in ks]
+            v64 = w.potential().astype(np.float32).astype(np.float64) if w.direction == "apply" else None
+            rate, done, el = time_oracle(w, osph, w.coefficients(osph), v64, budget_s=10.0)
             cpu = {"value": rate, "unit": "bands/s", "cores": 1, "kind": "oracle",
-                   "sample": f"{done} band round trips of the workload ({el:.1f} s), numpy pocketfft FP64"}
+                   "sample": f"{done} band transforms of the workload ({el:.1f} s), numpy pocketfft FP64"}
 
         line = {"metric": METRIC, "value": value, "unit": "bands/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "grid": list(N), "radius": RADIUS, "ngw": int(len(g)),
-                           "bands_per_gpu": BANDS, "precision": "fp32", "parallelism": f"bands x{world}",
+                "config": {"workload": w.desc, "name": w.name, "grid": list(w.n), "radius": w.radius,
+                           "ngw": ngws, "bands_per_gpu": w.total_bands, "precision": "fp32",
+                           "parallelism": f"bands x{world}", "chunk_bands": plan.info["chunk_bands"],
+                           "graph": w.graph, "autotuned": w.tune,
                            "l2": "flushed between timed steps (256 MiB write)"},
-                "rel_l2_roundtrip": err,
-                "fp64_gpu": {"value": BANDS / (ms64 / 1e3), "ms_per_step": ms64,
-                             "ratio_fp32_over_fp64": ms64 / ms},
+                "rel_l2": err,
+                "fp64_gpu": fp64,
                 "roofline": roofline,
                 "cpu_baseline": cpu,
-                "e2e": {"value": BANDS / e2e_s, "unit": "bands/s", "h2d_bytes_per_step": nbytes,
+                "e2e": {"value": w.total_bands / e2e_s, "unit": "bands/s", "h2d_bytes_per_step": nbytes,
                         "d2h_bytes_per_step": nbytes},
                 "gpu_launches": launches,
                 "clocks": clocks}
@@ -319,6 +428,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sphere64_rt",
+                    choices=["sphere64_rt", "sphere96_multik", "sphere128_apply", "sphere160_large"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
