@@ -27,6 +27,7 @@ template <typename T> cudaError_t launch_stick_t(int, const Launch&, int);
 template <typename T> cudaError_t launch_plane_t(int, const Launch&);
 template <typename T> cudaError_t prepare_t(int, int, int, int, int);
 template <typename T> int plane_occupancy_t(int, int, int, int, int);
+template <typename T> int stick_occupancy_t(int);
 
 static const int kSizes[] = {12, 16, 20, 24, 32, 40, 48, 64, 96, 128, 160};
 
@@ -43,6 +44,9 @@ size_t plane_smem(int prec, int n0, int n1, int xmax, int a_bufs) {
 int stick_tile(int prec, int n2) { return prec == P_F64 ? stick_tile_t<double>(n2) : stick_tile_t<float>(n2); }
 cudaError_t prepare_kernels(int prec, int n0, int n1, int n2, int xmax, int a_bufs) {
   return prec == P_F64 ? prepare_t<double>(n0, n1, n2, xmax, a_bufs) : prepare_t<float>(n0, n1, n2, xmax, a_bufs);
+}
+int stick_occupancy(int prec, int n2) {
+  return prec == P_F64 ? stick_occupancy_t<double>(n2) : stick_occupancy_t<float>(n2);
 }
 int plane_occupancy(int prec, int mode, int n0, int n1, int xmax, int a_bufs) {
   return prec == P_F64 ? plane_occupancy_t<double>(mode, n0, n1, xmax, a_bufs)
@@ -108,6 +112,7 @@ struct fftb_plan_s {
   const void* g_V = nullptr;
   int sms = 0;
   int plane_occ[3] = {0, 0, 0};  // resident plane CTAs per SM: G->r, r->G, apply
+  int stick_occ = 1;             // resident z-stage CTAs per SM
   // per-kernel timing (fftb_plan_set_timing)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -227,38 +232,43 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   p->chunk = chunk;
 
   // ---- host tables
-  std::vector<int32_t> band_k, stick_ent, ent_pos, ent_zs, col_start, stick_xy;
-  std::vector<int64_t> band_sph;
+  std::vector<int32_t> stick_info, ent_pos, ent_zs, col_info, stick_xy;
+  std::vector<BandInfo> band;
   std::vector<int16_t> xmap;
   int32_t sticks_so_far = 0;
   std::vector<KInfo> kinfo(p->nk);
   int64_t sph = 0, ent_base = 0;
   for (int k = 0; k < p->nk; ++k) {
     const KGeom& G = p->geo[k];
+    const size_t first_band = band.size();
     for (int b = 0; b < p->bands[k]; ++b) {
-      band_k.push_back(k);
-      band_sph.push_back(sph + (int64_t)b * G.ngw);
+      BandInfo bi{};
+      bi.sph = sph + (int64_t)b * G.ngw;
+      band.push_back(bi);
     }
     sph += (int64_t)p->bands[k] * G.ngw;
     kinfo[k].S = G.S;
     kinfo[k].X = G.X;
     kinfo[k].stick_base = sticks_so_far;
     kinfo[k].xmap_base = (int32_t)xmap.size();
-    kinfo[k].col_base = (int32_t)col_start.size();
+    kinfo[k].col_base = (int32_t)(col_info.size() / 4);
     kinfo[k].flags = (G.contiguous_columns ? KF_CONTIGUOUS_COLUMNS : 0) | (G.canonical_sticks ? KF_CANONICAL_STICKS : 0);
     sticks_so_far += G.S;
-    for (int32_t v : G.stick_ent) stick_ent.push_back((int32_t)(v + ent_base));
+    stick_records(G, d->n, (int32_t)ent_base, stick_info);
     for (int32_t v : G.ent_pos) ent_pos.push_back(v);
     for (int32_t v : G.ent_zs) ent_zs.push_back(v);
     for (int16_t v : G.xmap) xmap.push_back(v);
-    for (int32_t v : G.col_start) col_start.push_back(v);
+    slab_records(G, d->n, col_info);
+    for (size_t b = first_band; b < band.size(); ++b) band[b].ki = kinfo[k];
     for (int32_t v : G.stick_xy) stick_xy.push_back(v);
     ent_base += G.ngw;
   }
   if (ent_base >= (int64_t(1) << 31)) { release(p); return fail(FFTB_ERR_UNSUPPORTED, "total sphere entries above 2^31"); }
-  if (band_k.empty()) { band_k.push_back(0); band_sph.push_back(0); }
+  if (band.empty()) band.push_back(BandInfo{});
   if (ent_pos.empty()) { ent_pos.push_back(0); ent_zs.push_back(0); }
   if (stick_xy.empty()) stick_xy.push_back(0);
+  if (stick_info.empty()) stick_info.assign(4, 0);
+  if (col_info.empty()) col_info.assign(4, 0);
   std::vector<unsigned char> tw[3];
   for (int dd = 0; dd < 3; ++dd) {
     if (p->prec_kernel == P_F64) make_twiddles<double>(p->n[dd], tw[dd]);
@@ -267,12 +277,12 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
 
   struct Part { const void* src; size_t bytes; size_t off; };
   std::vector<Part> parts = {
-      {band_k.data(), band_k.size() * 4, 0},       {band_sph.data(), band_sph.size() * 8, 0},
-      {kinfo.data(), kinfo.size() * sizeof(KInfo), 0}, {stick_ent.data(), stick_ent.size() * 4, 0},
+      {band.data(), band.size() * sizeof(BandInfo), 0}, {nullptr, 0, 0},
+      {kinfo.data(), kinfo.size() * sizeof(KInfo), 0}, {stick_info.data(), stick_info.size() * 4, 0},
       {ent_pos.data(), ent_pos.size() * 4, 0},     {ent_zs.data(), ent_zs.size() * 4, 0},
       {stick_xy.data(), stick_xy.size() * 4, 0},   {xmap.data(), xmap.size() * 2, 0},
       {tw[0].data(), tw[0].size(), 0},             {tw[1].data(), tw[1].size(), 0},
-      {tw[2].data(), tw[2].size(), 0},             {col_start.data(), col_start.size() * 4, 0}};
+      {tw[2].data(), tw[2].size(), 0},             {col_info.data(), col_info.size() * 4, 0}};
   size_t total = 0;
   for (auto& pt : parts) {
     pt.off = total;
@@ -284,19 +294,18 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaMalloc tables failed"); }
   p->tables_bytes = total;
   std::vector<unsigned char> blob(total, 0);
-  for (auto& pt : parts) std::memcpy(blob.data() + pt.off, pt.src, pt.bytes);
+  for (auto& pt : parts)
+    if (pt.bytes) std::memcpy(blob.data() + pt.off, pt.src, pt.bytes);
   e = cudaMemcpy(p->d_tables, blob.data(), total, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { release(p); return cuda_fail(e, "cudaMemcpy tables"); }
   unsigned char* base = static_cast<unsigned char*>(p->d_tables);
   Geo& g = p->g;
-  g.band_k = reinterpret_cast<const int32_t*>(base + parts[0].off);
-  g.band_sph = reinterpret_cast<const int64_t*>(base + parts[1].off);
-  g.kinfo = reinterpret_cast<const KInfo*>(base + parts[2].off);
-  g.stick_ent = reinterpret_cast<const int32_t*>(base + parts[3].off);
+  g.band = reinterpret_cast<const BandInfo*>(base + parts[0].off);
+  g.stick_info = reinterpret_cast<const int4*>(base + parts[3].off);
   g.ent_pos = reinterpret_cast<const int32_t*>(base + parts[4].off);
   g.ent_zs = reinterpret_cast<const int32_t*>(base + parts[5].off);
   g.stick_xy = reinterpret_cast<const int32_t*>(base + parts[6].off);
-  g.col_start = reinterpret_cast<const int32_t*>(base + parts[11].off);
+  g.col_info = reinterpret_cast<const int4*>(base + parts[11].off);
   g.xmap = reinterpret_cast<const int16_t*>(base + parts[7].off);
   g.tw0 = base + parts[8].off;
   g.tw1 = base + parts[9].off;
@@ -317,6 +326,8 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   if (e != cudaSuccess) { release(p); return cuda_fail(e, "device attribute"); }
   const int modes[3] = {M_G2R, M_R2G, M_APPLY};
   p->sms = sms;
+  p->stick_occ = std::max(1, stick_occupancy(p->prec_kernel, p->n[2]));
+  p->tiles = 0;  // z stage: one warp per task unless the autotuner prefers persistent CTAs
   for (int i = 0; i < 3; ++i) {
     const int occ = plane_occupancy(p->prec_kernel, modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs);
     if (occ < 1) { release(p); return fail(FFTB_ERR_UNSUPPORTED, "plane kernel cannot be resident on this device"); }
@@ -680,7 +691,7 @@ std::string tune_key(const fftb_plan_s* p) {
   return out;
 }
 
-bool tune_cache_lookup(const std::string& key, int* chunk, int ctas[3]) {
+bool tune_cache_lookup(const std::string& key, int* chunk, int ctas[3], int* tiles) {
   const char* path = std::getenv("FFTB_TUNE_CACHE");
   if (!path || !*path) return false;
   std::ifstream f(path);
@@ -689,23 +700,24 @@ bool tune_cache_lookup(const std::string& key, int* chunk, int ctas[3]) {
   while (std::getline(f, line)) {
     std::istringstream ls(line);
     std::string k;
-    int c, a, b, d;
-    if ((ls >> k >> c >> a >> b >> d) && k == key) {
+    int c, a, b, d, t;
+    if ((ls >> k >> c >> a >> b >> d >> t) && k == key) {
       *chunk = c;
       ctas[0] = a;
       ctas[1] = b;
       ctas[2] = d;
+      *tiles = t;
       found = true;  // the last entry wins
     }
   }
   return found;
 }
 
-void tune_cache_store(const std::string& key, int chunk, const int ctas[3]) {
+void tune_cache_store(const std::string& key, int chunk, const int ctas[3], int tiles) {
   const char* path = std::getenv("FFTB_TUNE_CACHE");
   if (!path || !*path) return;
   std::ofstream f(path, std::ios::app);
-  f << key << " " << chunk << " " << ctas[0] << " " << ctas[1] << " " << ctas[2] << "\n";
+  f << key << " " << chunk << " " << ctas[0] << " " << ctas[1] << " " << ctas[2] << " " << tiles << "\n";
 }
 
 fftb_status resize_T(fftb_plan_s* p, int chunk) {
@@ -729,11 +741,12 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   cudaGetDevice(&dev);
   if (dev != p->device) return fail(FFTB_ERR_INVALID_ARG, "current device differs from the plan's device");
   const std::string key = tune_key(p);
-  int chunk = 0, ctas[3] = {0, 0, 0};
-  if (tune_cache_lookup(key, &chunk, ctas)) {
+  int chunk = 0, ctas[3] = {0, 0, 0}, tiles = 0;
+  if (tune_cache_lookup(key, &chunk, ctas, &tiles)) {
     fftb_status st = resize_T(p, chunk);
     if (st != FFTB_OK) return st;
     p->chunk = chunk;
+    p->tiles = tiles;
     for (int i = 0; i < 3; ++i) p->plane_ctas[i] = ctas[i];
     if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
     return FFTB_OK;
@@ -788,7 +801,7 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   std::vector<int> mults;
   const int mi = p->dir == FFTB_R_TO_G ? 1 : p->dir == FFTB_APPLY_LOCAL ? 2 : 0;
   for (int m : {p->plane_occ[mi], p->plane_occ[mi] - 1, 0})
-    if (m >= 0 && std::find(mults.begin(), mults.end(), m) == mults.end() && !(m == 0 && false)) mults.push_back(m);
+    if (m >= 0 && std::find(mults.begin(), mults.end(), m) == mults.end()) mults.push_back(m);
   int max_chunk = *std::max_element(chunks.begin(), chunks.end());
   fftb_status st = resize_T(p, max_chunk);
   if (st != FFTB_OK) {
@@ -796,7 +809,7 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
     cleanup();
     return st;
   }
-  const int saved_chunk = p->chunk;
+  const int saved_chunk = p->chunk, saved_tiles = p->tiles;
   int saved_ctas[3] = {p->plane_ctas[0], p->plane_ctas[1], p->plane_ctas[2]};
   const bool saved_timing = p->timing, saved_graph = p->use_graph;
   const int64_t saved_launches = p->launches;
@@ -806,9 +819,11 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int best_chunk = saved_chunk, best_ctas[3] = {saved_ctas[0], saved_ctas[1], saved_ctas[2]};
+  int best_chunk = saved_chunk, best_ctas[3] = {saved_ctas[0], saved_ctas[1], saved_ctas[2]}, best_tiles = saved_tiles;
   for (int c : chunks) {
-    for (int m : mults) {
+    for (int mm = 0; mm < 2 * (int)mults.size(); ++mm) {
+      const int m = mults[mm / 2];
+      p->tiles = (mm & 1) ? p->sms * p->stick_occ : 0;
       p->chunk = c;
       for (int i = 0; i < 3; ++i) p->plane_ctas[i] = m == 0 ? 0 : p->sms * std::min(m, p->plane_occ[i]);
       st = enqueue(p, bands, d_in, d_out, d_cube, nullptr);
@@ -826,6 +841,7 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
       if (ms < best) {
         best = ms;
         best_chunk = c;
+        best_tiles = p->tiles;
         for (int i = 0; i < 3; ++i) best_ctas[i] = p->plane_ctas[i];
       }
     }
@@ -840,13 +856,15 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   cleanup();
   if (st != FFTB_OK) {
     p->chunk = saved_chunk;
+    p->tiles = saved_tiles;
     for (int i = 0; i < 3; ++i) p->plane_ctas[i] = saved_ctas[i];
     return st;
   }
   // a chunk tuned on a band prefix covers the whole batch too
   p->chunk = best_chunk;
+  p->tiles = best_tiles;
   for (int i = 0; i < 3; ++i) p->plane_ctas[i] = best_ctas[i];
   if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
-  tune_cache_store(key, best_chunk, best_ctas);
+  tune_cache_store(key, best_chunk, best_ctas, best_tiles);
   return FFTB_OK;
 }

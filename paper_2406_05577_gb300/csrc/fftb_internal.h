@@ -16,7 +16,7 @@ struct KInfo {
   int32_t X;           // occupied x values (y-z slabs)
   int32_t stick_base;  // sticks of earlier k-points; stick_ent uses stick_base + k
   int32_t xmap_base;   // first entry of this k in xmap (k * N0)
-  int32_t col_base;    // first entry of this k in col_start (sum of X + 1 over earlier k)
+  int32_t col_base;    // first entry of this k in col_info (sum of X over earlier k)
   int32_t flags;       // KF_* bits
 };
 // Every slab column's sticks have consecutive gy (always true for a cutoff
@@ -27,16 +27,23 @@ constexpr int32_t KF_CONTIGUOUS_COLUMNS = 1;
 // indexes the coefficient list directly.
 constexpr int32_t KF_CANONICAL_STICKS = 2;
 
+// Per band: its k-point's geometry and the offset of its sphere (complex
+// elements), read by the kernels in one 32-byte load.
+struct __align__(16) BandInfo {
+  KInfo ki;
+  int64_t sph;
+};
+
 // Device tables for all k-points (concatenated) plus twiddles.
 struct Geo {
-  const int32_t* band_k;     // [total_bands] k-point of each band
-  const int64_t* band_sph;   // [total_bands] offset of each band's sphere (complex elements)
-  const KInfo* kinfo;        // [n_k]
-  const int32_t* stick_ent;  // [sum(S_k + 1)] global entry offset of each stick (CSR)
+  const BandInfo* band;      // [total_bands]
+  const int4* stick_info;    // [sum S_k] per stick: first entry, end entry (global),
+                             //   list position of the first entry, signed gz of it
   const int32_t* ent_pos;    // [sum ngw] position of the entry within its k's sphere list
   const int32_t* ent_zs;     // [sum ngw] (z index << 24) | local stick index
   const int16_t* xmap;       // [n_k * N0] slab index of x, or -1
-  const int32_t* col_start;  // [sum (X_k + 1)] first stick of each slab (local stick index)
+  const int4* col_info;      // [sum X_k] per slab: first stick (local), sticks, signed gy of
+                             //   the first stick, 0
   const int32_t* stick_xy;   // [sum S_k] (xi << 16) | y index
   const void* tw0;           // [N0] e^{+2 pi j m / N0} in the plan's real type
   const void* tw1;           // [N1]
@@ -70,11 +77,14 @@ bool plane_size_supported(int n0, int n1);
 size_t stick_smem(int prec, int n2);
 size_t plane_smem(int prec, int n0, int n1, int xmax, int a_bufs);
 int stick_tile(int prec, int n2);
+// Resident z-stage CTAs per SM (after prepare_kernels).
+int stick_occupancy(int prec, int n2);
 // Raise the dynamic shared-memory limit of the kernels a plan uses.
 cudaError_t prepare_kernels(int prec, int n0, int n1, int n2, int xmax, int a_bufs);
 // Resident plane-stage CTAs per SM for this geometry (after prepare_kernels).
 int plane_occupancy(int prec, int mode, int n0, int n1, int xmax, int a_bufs);
-cudaError_t launch_stick(int prec, int mode, const Launch& L, int tiles);
+// ctas: persistent z-stage CTAs (0: one warp per task)
+cudaError_t launch_stick(int prec, int mode, const Launch& L, int ctas);
 cudaError_t launch_plane(int prec, int mode, const Launch& L);
 // Sets the calling thread's message for fftb_last_error().
 void set_last_error(const std::string& msg);

@@ -131,4 +131,26 @@ std::string build_geometry(const int32_t n[3], const int32_t* g, int64_t ngw, KG
   return "";
 }
 
+static inline int32_t signed_index(int32_t v, int32_t n) { return v < n - n / 2 ? v : v - n; }
+
+void stick_records(const KGeom& g, const int32_t n[3], int32_t ent_base, std::vector<int32_t>& out4) {
+  for (int32_t s = 0; s < g.S; ++s) {
+    const int32_t e0 = g.stick_ent[s], e1 = g.stick_ent[s + 1];
+    out4.push_back(e0 + ent_base);
+    out4.push_back(e1 + ent_base);
+    out4.push_back(g.ent_pos[e0]);
+    out4.push_back(signed_index((int32_t)((uint32_t)g.ent_zs[e0] >> 24), n[2]));
+  }
+}
+
+void slab_records(const KGeom& g, const int32_t n[3], std::vector<int32_t>& out4) {
+  for (int32_t xi = 0; xi < g.X; ++xi) {
+    const int32_t sa = g.col_start[xi], sb = g.col_start[xi + 1];
+    out4.push_back(sa);
+    out4.push_back(sb - sa);
+    out4.push_back(sb > sa ? signed_index(g.stick_xy[sa] & 0xFFFF, n[1]) : 0);
+    out4.push_back(0);
+  }
+}
+
 }  // namespace fftb

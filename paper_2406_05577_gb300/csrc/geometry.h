@@ -29,6 +29,13 @@ struct KGeom {
   std::vector<int16_t> xmap;
 };
 
+// Per-stick and per-slab records the kernels read in one 16-byte load:
+//   stick: {first entry + ent_base, end entry + ent_base, list position of the
+//           first entry, signed gz of the first entry}
+//   slab : {first stick, number of sticks, signed gy of the first stick, 0}
+void stick_records(const KGeom& g, const int32_t n[3], int32_t ent_base, std::vector<int32_t>& out4);
+void slab_records(const KGeom& g, const int32_t n[3], std::vector<int32_t>& out4);
+
 // Cutoff sphere |G + k| <= r (Sec. 2.2), components in [-N/2, N/2), in
 // canonical order (gy, gx, gz ascending). Returns "" or an error message
 // (the sphere does not fit the grid and would alias).

@@ -52,98 +52,109 @@ __global__ void __launch_bounds__(STICK_NW * 32) k_stick(const Launch L) {
   const int g = lane % LZ::G, l = lane / LZ::G;
   C* scr = tw + N2 + warp * WZ * LZ::PITCH;
   C* row = scr + l * LZ::PITCH;
-
-  const int bl = blockIdx.y;
-  const int gb = L.band0 + bl;
-  const int k = L.g.band_k[gb];
-  const KInfo ki = L.g.kinfo[k];
-  const int S = ki.S;
-  const int cta_s0 = blockIdx.x * stick_tile_c2<N2>();
-  if (cta_s0 >= S) return;
   {
     const C* tw_g = static_cast<const C*>(L.g.tw2);
     for (int m = threadIdx.x; m < N2; m += NT) tw[m] = tw_g[m];
   }
   __syncthreads();
-  const int s0 = cta_s0 + warp * WZ;
-  if (s0 >= S) return;  // whole warp idle (no further block barriers)
-  const int nl = min(WZ, S - s0);
-  const int s = s0 + (l < nl ? l : 0);
   typename LZ::template TwCache<C> tc;
   tc.load(g, tw);
   auto zsigned = [](int z) { return z < N2 - N2 / 2 ? z : z - N2; };
-  const int32_t* sent = L.g.stick_ent + ki.stick_base + k;
-  const int e0 = sent[s], len = sent[s + 1] - e0;
-  const int64_t sph = L.g.band_sph[gb];
-  const bool canon = ki.flags & KF_CANONICAL_STICKS;
-  int p0 = 0, zlo = 0;
-  if (canon) {
-    p0 = L.g.ent_pos[e0];
-    zlo = zsigned((int)((uint32_t)L.g.ent_zs[e0] >> 24));
-  }
-  C* Tb = static_cast<C*>(L.T) + (size_t)bl * N2 * L.g.smax + s;
   const int smax = L.g.smax;
-  C v[EZ];
 
-  if constexpr (MODE == M_G2R) {
-    const C* in = static_cast<const C*>(L.sph_in) + sph;
-    if (canon) {
+  // tasks = (band, group of WZ sticks); each warp takes a contiguous range, so
+  // consecutive tasks usually share the band and its tables
+  const int gpb = (smax + WZ - 1) / WZ;
+  const int ntask = L.nb * gpb;
+  const int nwarps = gridDim.x * STICK_NW;
+  const int per = (ntask + nwarps - 1) / nwarps;
+  const int t0 = (blockIdx.x * STICK_NW + warp) * per;
+  const int t1 = min(ntask, t0 + per);
+  int cur_bl = -1, S = 0, stick_base = 0;
+  bool canon = false;
+  int64_t sph = 0;
+#pragma unroll 1
+  for (int t = t0; t < t1; ++t) {
+    const int bl = t / gpb, s0 = (t - bl * gpb) * WZ;
+    if (bl != cur_bl) {
+      cur_bl = bl;
+      const BandInfo bi = L.g.band[L.band0 + bl];
+      S = bi.ki.S;
+      stick_base = bi.ki.stick_base;
+      canon = bi.ki.flags & KF_CANONICAL_STICKS;
+      sph = bi.sph;
+    }
+    if (s0 >= S) continue;  // uniform across the warp
+    const int nl = min(WZ, S - s0);
+    const int s = s0 + (l < nl ? l : 0);
+    const int4 si = L.g.stick_info[stick_base + s];  // first entry, end entry, list position, signed gz
+    const int len = si.y - si.x;
+    C* Tb = static_cast<C*>(L.T) + (size_t)bl * N2 * smax + s;
+    C v[EZ];
+
+    if constexpr (MODE == M_G2R) {
+      const C* in = static_cast<const C*>(L.sph_in) + sph;
+      if (canon) {
 #pragma unroll
-      for (int m = 0; m < EZ / LZ::R0; ++m)
+        for (int m = 0; m < EZ / LZ::R0; ++m)
 #pragma unroll
-        for (int j = 0; j < LZ::R0; ++j) {
-          const int d = zsigned(LZ::first_pos(g, m, j)) - zlo;
-          v[m * LZ::R0 + j] = (unsigned)d < (unsigned)len ? in[p0 + d] : czero<C>();
+          for (int j = 0; j < LZ::R0; ++j) {
+            const int d = zsigned(LZ::first_pos(g, m, j)) - si.w;
+            v[m * LZ::R0 + j] = (unsigned)d < (unsigned)len ? in[si.z + d] : czero<C>();
+          }
+      } else {
+        const int ea = __shfl_sync(0xffffffffu, si.x, 0);
+        const int eb = __shfl_sync(0xffffffffu, si.y, (nl - 1) * LZ::G);
+        for (int q = lane; q < WZ * LZ::PITCH; q += 32) scr[q] = czero<C>();
+        __syncwarp();
+        for (int e = ea + lane; e < eb; e += 32) {
+          const uint32_t zs = (uint32_t)L.g.ent_zs[e];
+          scr[((int)(zs & 0xFFFFFFu) - s0) * LZ::PITCH + wpad((int)(zs >> 24))] = in[L.g.ent_pos[e]];
         }
-    } else {
-      for (int q = lane; q < WZ * LZ::PITCH; q += 32) scr[q] = czero<C>();
-      __syncwarp();
-      const int ea = sent[s0], eb = sent[s0 + nl];
-      for (int e = ea + lane; e < eb; e += 32) {
-        const uint32_t zs = (uint32_t)L.g.ent_zs[e];
-        scr[((int)(zs & 0xFFFFFFu) - s0) * LZ::PITCH + wpad((int)(zs >> 24))] = in[L.g.ent_pos[e]];
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < EZ / LZ::R0; ++m)
+#pragma unroll
+          for (int j = 0; j < LZ::R0; ++j) v[m * LZ::R0 + j] = row[wpad(LZ::first_pos(g, m, j))];
+        __syncwarp();
       }
-      __syncwarp();
-#pragma unroll
-      for (int m = 0; m < EZ / LZ::R0; ++m)
-#pragma unroll
-        for (int j = 0; j < LZ::R0; ++j) v[m * LZ::R0 + j] = row[wpad(LZ::first_pos(g, m, j))];
-      __syncwarp();
-    }
-    LZ::template run<+1>(v, g, row, tw, tc);
-    if (l < nl) {
-#pragma unroll
-      for (int m = 0; m < EZ / LZ::RL; ++m)
-#pragma unroll
-        for (int j = 0; j < LZ::RL; ++j) Tb[(size_t)LZ::last_pos(g, m, j) * smax] = v[m * LZ::RL + j];
-    }
-  } else {
-#pragma unroll
-    for (int m = 0; m < EZ / LZ::R0; ++m)
-#pragma unroll
-      for (int j = 0; j < LZ::R0; ++j) v[m * LZ::R0 + j] = Tb[(size_t)LZ::first_pos(g, m, j) * smax];
-    LZ::template run<-1>(v, g, row, tw, tc);
-    C* out = static_cast<C*>(L.sph_out) + sph;
-    if (canon) {
+      LZ::template run<+1>(v, g, row, tw, tc);
       if (l < nl) {
 #pragma unroll
         for (int m = 0; m < EZ / LZ::RL; ++m)
 #pragma unroll
-          for (int j = 0; j < LZ::RL; ++j) {
-            const int d = zsigned(LZ::last_pos(g, m, j)) - zlo;
-            if ((unsigned)d < (unsigned)len) out[p0 + d] = v[m * LZ::RL + j];
-          }
+          for (int j = 0; j < LZ::RL; ++j) Tb[(size_t)LZ::last_pos(g, m, j) * smax] = v[m * LZ::RL + j];
       }
     } else {
 #pragma unroll
-      for (int m = 0; m < EZ / LZ::RL; ++m)
+      for (int m = 0; m < EZ / LZ::R0; ++m)
 #pragma unroll
-        for (int j = 0; j < LZ::RL; ++j) row[wpad(LZ::last_pos(g, m, j))] = v[m * LZ::RL + j];
-      __syncwarp();
-      const int ea = sent[s0], eb = sent[s0 + nl];
-      for (int e = ea + lane; e < eb; e += 32) {
-        const uint32_t zs = (uint32_t)L.g.ent_zs[e];
-        out[L.g.ent_pos[e]] = scr[((int)(zs & 0xFFFFFFu) - s0) * LZ::PITCH + wpad((int)(zs >> 24))];
+        for (int j = 0; j < LZ::R0; ++j) v[m * LZ::R0 + j] = Tb[(size_t)LZ::first_pos(g, m, j) * smax];
+      LZ::template run<-1>(v, g, row, tw, tc);
+      C* out = static_cast<C*>(L.sph_out) + sph;
+      if (canon) {
+        if (l < nl) {
+#pragma unroll
+          for (int m = 0; m < EZ / LZ::RL; ++m)
+#pragma unroll
+            for (int j = 0; j < LZ::RL; ++j) {
+              const int d = zsigned(LZ::last_pos(g, m, j)) - si.w;
+              if ((unsigned)d < (unsigned)len) out[si.z + d] = v[m * LZ::RL + j];
+            }
+        }
+      } else {
+        const int ea = __shfl_sync(0xffffffffu, si.x, 0);
+        const int eb = __shfl_sync(0xffffffffu, si.y, (nl - 1) * LZ::G);
+#pragma unroll
+        for (int m = 0; m < EZ / LZ::RL; ++m)
+#pragma unroll
+          for (int j = 0; j < LZ::RL; ++j) row[wpad(LZ::last_pos(g, m, j))] = v[m * LZ::RL + j];
+        __syncwarp();
+        for (int e = ea + lane; e < eb; e += 32) {
+          const uint32_t zs = (uint32_t)L.g.ent_zs[e];
+          out[L.g.ent_pos[e]] = scr[((int)(zs & 0xFFFFFFu) - s0) * LZ::PITCH + wpad((int)(zs >> 24))];
+        }
+        __syncwarp();
       }
     }
   }
@@ -238,12 +249,11 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
     const int bl = p / n2;
     const int z = p - bl * n2;
     const int gb = L.band0 + bl;
-    const int k = L.g.band_k[gb];
-    const KInfo ki = L.g.kinfo[k];
+    const KInfo ki = L.g.band[gb].ki;
     const int X = ki.X;
     const int XP = a_pitch(X);
-    if (k != cur_k) {  // uniform across the CTA
-      cur_k = k;
+    if (ki.xmap_base != cur_k) {  // a new k-point (uniform across the CTA)
+      cur_k = ki.xmap_base;
       const int16_t* xm = L.g.xmap + ki.xmap_base;
 #pragma unroll
       for (int q = 0; q < (EX + 3) / 4; ++q) { xin.w[q] = 0; xout.w[q] = 0; }
@@ -263,7 +273,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
         }
     }
     C* A = A0 + parity * abuf;
-    const int32_t* cs = L.g.col_start + ki.col_base;
+    const int4* __restrict__ cinfo = L.g.col_info + ki.col_base;
     const int32_t* sxy = L.g.stick_xy + ki.stick_base;
     C* Tz = static_cast<C*>(L.T) + ((size_t)bl * n2 + z) * L.g.smax;
     const size_t plane = ((size_t)gb * n2 + z) * (size_t)(N1 * N0);
@@ -278,11 +288,11 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
       for (int t = warp; t < ty; t += NW) {
         const int c0 = t * WY, nl = min(WY, X - c0);
         C v[EY];
+        const int col = c0 + (ly < nl ? ly : 0);
+        const int4 ci = cinfo[col];  // first stick, sticks, signed gy of the first
         if (ki.flags & KF_CONTIGUOUS_COLUMNS) {
           // each column's sticks are consecutive in gy: index them directly
-          const int col = c0 + (ly < nl ? ly : 0);
-          const int sa = cs[col], len = cs[col + 1] - sa;
-          const int ylo = ysigned(sxy[sa] & 0xFFFF);
+          const int sa = ci.x, len = ci.y, ylo = ci.z;
 #pragma unroll
           for (int m = 0; m < EY / LY::R0; ++m)
 #pragma unroll
@@ -291,10 +301,11 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
               v[m * LY::R0 + j] = (unsigned)d < (unsigned)len ? Tz[sa + d] : czero<C>();
             }
         } else {
+          const int sbeg = __shfl_sync(0xffffffffu, ci.x, 0);
+          const int send = __shfl_sync(0xffffffffu, ci.x + ci.y, (nl - 1) * LY::G);
           for (int q = lane; q < WY * LY::PITCH; q += 32) scr[q] = czero<C>();
           __syncwarp();
-          const int s1 = cs[c0 + nl];
-          for (int s = cs[c0] + lane; s < s1; s += 32) {
+          for (int s = sbeg + lane; s < send; s += 32) {
             const int xy = sxy[s];
             scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)] = Tz[s];
           }
@@ -390,6 +401,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
       for (int t = warp; t < ty; t += NW) {
         const int c0 = t * WY, nl = min(WY, X - c0);
         const int col = c0 + (ly < nl ? ly : 0);
+        const int4 ci = cinfo[col];
         C v[EY];
 #pragma unroll
         for (int m = 0; m < EY / LY::R0; ++m)
@@ -398,8 +410,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
         LY::template run<-1>(v, gy, rowy, tw1, tcy);
         if (ki.flags & KF_CONTIGUOUS_COLUMNS) {
           if (ly < nl) {
-            const int sa = cs[col], len = cs[col + 1] - sa;
-            const int ylo = ysigned(sxy[sa] & 0xFFFF);
+            const int sa = ci.x, len = ci.y, ylo = ci.z;
 #pragma unroll
             for (int m = 0; m < EY / LY::RL; ++m)
 #pragma unroll
@@ -414,8 +425,9 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
             for (int j = 0; j < LY::RL; ++j) rowy[wpad(LY::last_pos(gy, m, j))] = v[m * LY::RL + j];
           __syncwarp();
-          const int s1 = cs[c0 + nl];
-          for (int s = cs[c0] + lane; s < s1; s += 32) {
+          const int sbeg = __shfl_sync(0xffffffffu, ci.x, 0);
+          const int send = __shfl_sync(0xffffffffu, ci.x + ci.y, (nl - 1) * LY::G);
+          for (int s = sbeg + lane; s < send; s += 32) {
             const int xy = sxy[s];
             Tz[s] = scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)];
           }
@@ -456,9 +468,11 @@ template <typename T> int stick_tile_t(int n2) {
   return 0;
 }
 
-template <typename T, int N2> cudaError_t go_stick(int mode, const Launch& L, int tiles) {
+template <typename T, int N2> cudaError_t go_stick(int mode, const Launch& L, int ctas) {
   const size_t smem = stick_smem_c<T, N2>();
-  const dim3 grid(tiles, L.nb);
+  const int gpb = (L.g.smax + (32 / Line<N2>::G) - 1) / (32 / Line<N2>::G);
+  const int need = (L.nb * gpb + STICK_NW - 1) / STICK_NW;  // one task per warp
+  const dim3 grid(ctas > 0 ? min(ctas, need) : need);
   if (mode == M_G2R) k_stick<T, N2, M_G2R><<<grid, STICK_NW * 32, smem, L.stream>>>(L);
   else k_stick<T, N2, M_R2G><<<grid, STICK_NW * 32, smem, L.stream>>>(L);
   return cudaGetLastError();
@@ -499,6 +513,21 @@ template <typename T, int N> int occ_plane(int mode, int xmax, int a_bufs) {
   else if (mode == M_R2G) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_R2G>, NT, smem);
   else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_APPLY>, NT, smem);
   return e == cudaSuccess ? nb : 0;
+}
+template <typename T, int N2> int occ_stick() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stick<T, N2, M_G2R>, STICK_NW * 32, stick_smem_c<T, N2>()) !=
+      cudaSuccess)
+    return 0;
+  return nb;
+}
+template <typename T> int stick_occupancy_t(int n2) {
+  switch (n2) {
+#define C_(N) case N: return occ_stick<T, N>();
+    FFTB_SIZES(C_)
+#undef C_
+  }
+  return 0;
 }
 template <typename T> int plane_occupancy_t(int mode, int n0, int n1, int xmax, int a_bufs) {
   if (n0 != n1) return 0;
@@ -550,6 +579,7 @@ template <typename T> cudaError_t prepare_t(int n0, int n1, int n2, int xmax, in
   template cudaError_t launch_stick_t<T>(int, const Launch&, int);                 \
   template cudaError_t launch_plane_t<T>(int, const Launch&);                      \
   template cudaError_t prepare_t<T>(int, int, int, int, int);                     \
-  template int plane_occupancy_t<T>(int, int, int, int, int);
+  template int plane_occupancy_t<T>(int, int, int, int, int);                     \
+  template int stick_occupancy_t<T>(int);
 
 }  // namespace fftb

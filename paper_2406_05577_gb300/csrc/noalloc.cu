@@ -116,9 +116,11 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
   // tables, packed like a one-k-point plan
   KInfo ki{G.S, G.X, 0, 0, 0,
            (G.contiguous_columns ? KF_CONTIGUOUS_COLUMNS : 0) | (G.canonical_sticks ? KF_CANONICAL_STICKS : 0)};
-  std::vector<int32_t> band_k((size_t)bands, 0);
-  std::vector<int64_t> band_sph((size_t)bands);
-  for (int b = 0; b < bands; ++b) band_sph[b] = (int64_t)b * G.ngw;
+  std::vector<BandInfo> band((size_t)bands);
+  for (int b = 0; b < bands; ++b) {
+    band[b].ki = ki;
+    band[b].sph = (int64_t)b * G.ngw;
+  }
   std::vector<float> tw[3];
   for (int d = 0; d < 3; ++d) {
     tw[d].resize(2 * (size_t)n[d]);
@@ -128,17 +130,21 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
       tw[d][2 * m + 1] = (float)std::sin(a);
     }
   }
-  std::vector<int32_t> one_zero(1, 0);
+  std::vector<int32_t> one_zero(1, 0), sinfo, cinfo;
+  stick_records(G, n, 0, sinfo);
+  slab_records(G, n, cinfo);
+  if (sinfo.empty()) sinfo.assign(4, 0);
+  if (cinfo.empty()) cinfo.assign(4, 0);
   const std::vector<int32_t>& pos = G.ent_pos.empty() ? one_zero : G.ent_pos;
   const std::vector<int32_t>& zs = G.ent_zs.empty() ? one_zero : G.ent_zs;
   const std::vector<int32_t>& sxy = G.stick_xy.empty() ? one_zero : G.stick_xy;
   struct Part { const void* p; size_t bytes; size_t off; };
-  Part parts[] = {{band_k.data(), band_k.size() * 4, 0},  {band_sph.data(), band_sph.size() * 8, 0},
-                  {&ki, sizeof(KInfo), 0},                {G.stick_ent.data(), G.stick_ent.size() * 4, 0},
+  Part parts[] = {{band.data(), band.size() * sizeof(BandInfo), 0}, {nullptr, 0, 0},
+                  {&ki, sizeof(KInfo), 0},                {sinfo.data(), sinfo.size() * 4, 0},
                   {pos.data(), pos.size() * 4, 0},         {zs.data(), zs.size() * 4, 0},
                   {sxy.data(), sxy.size() * 4, 0},         {G.xmap.data(), G.xmap.size() * 2, 0},
                   {tw[0].data(), tw[0].size() * 4, 0},     {tw[1].data(), tw[1].size() * 4, 0},
-                  {tw[2].data(), tw[2].size() * 4, 0},     {G.col_start.data(), G.col_start.size() * 4, 0}};
+                  {tw[2].data(), tw[2].size() * 4, 0},     {cinfo.data(), cinfo.size() * 4, 0}};
   size_t total = 0;
   for (Part& p : parts) {
     p.off = total;
@@ -160,21 +166,20 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<unsigned char> blob(total, 0);
-  for (const Part& p : parts) std::memcpy(blob.data() + p.off, p.p, p.bytes);
+  for (const Part& p : parts)
+    if (p.bytes) std::memcpy(blob.data() + p.off, p.p, p.bytes);
   // pageable source: the call returns once the bytes are staged, so blob may go
   ce = cudaMemcpyAsync(tables, blob.data(), total, cudaMemcpyHostToDevice, s);
   if (ce != cudaSuccess) return err(FFTB_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(ce));
 
   unsigned char* base = static_cast<unsigned char*>(tables);
   Launch L{};
-  L.g.band_k = reinterpret_cast<const int32_t*>(base + parts[0].off);
-  L.g.band_sph = reinterpret_cast<const int64_t*>(base + parts[1].off);
-  L.g.kinfo = reinterpret_cast<const KInfo*>(base + parts[2].off);
-  L.g.stick_ent = reinterpret_cast<const int32_t*>(base + parts[3].off);
+  L.g.band = reinterpret_cast<const BandInfo*>(base + parts[0].off);
+  L.g.stick_info = reinterpret_cast<const int4*>(base + parts[3].off);
   L.g.ent_pos = reinterpret_cast<const int32_t*>(base + parts[4].off);
   L.g.ent_zs = reinterpret_cast<const int32_t*>(base + parts[5].off);
   L.g.stick_xy = reinterpret_cast<const int32_t*>(base + parts[6].off);
-  L.g.col_start = reinterpret_cast<const int32_t*>(base + parts[11].off);
+  L.g.col_info = reinterpret_cast<const int4*>(base + parts[11].off);
   L.g.xmap = reinterpret_cast<const int16_t*>(base + parts[7].off);
   L.g.tw0 = base + parts[8].off;
   L.g.tw1 = base + parts[9].off;
@@ -189,12 +194,10 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
   L.T = scratch;
   L.a_bufs = a_bufs;
   L.stream = s;
-  const int ts = stick_tile_t<float>(n[2]);
-  const int tiles = (smax + ts - 1) / ts;
   for (int b0 = 0; b0 < bands; b0 += chunk) {
     L.band0 = b0;
     L.nb = std::min(chunk, bands - b0);
-    ce = launch_stick_t<float>(M_G2R, L, tiles);
+    ce = launch_stick_t<float>(M_G2R, L, 0);
     if (ce == cudaSuccess) ce = launch_plane_t<float>(M_G2R, L);
     if (ce != cudaSuccess) return err(FFTB_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(ce));
   }
