@@ -348,31 +348,42 @@ def run_ours(args):
                 "step_compulsory_frac": step_bytes / (ms / 1e3) / 1e9 / hbm}
 
     if rank == 0:
-        # FP64 GPU path on the same workload (the comparison the metric names)
-        fp64 = None
-        try:
-            p64, v64d = make_plan(fftb, w, "fp64", dev)
-            x64 = torch.from_numpy(np.concatenate([p.reshape(-1) for p in parts])).to(dev)
-            o64 = torch.empty_like(x64)
-            cube64 = None
+        # FP64 GPU path and the split-precision tensor-core path on the same workload
+        def time_plan(prec, reps=3):
+            p2, vd2 = make_plan(fftb, w, prec, dev)
+            cdt = torch.complex128 if prec == "fp64" else torch.complex64
+            x2 = torch.from_numpy(np.concatenate([p.reshape(-1) for p in parts])).to(cdt).to(dev)
+            o2 = torch.empty_like(x2)
+            cube2 = None
             if w.direction == "roundtrip":
-                cube64 = torch.empty(p64.info["cube_elems"], dtype=torch.complex128, device=dev)
+                cube2 = torch.empty(p2.info["cube_elems"], dtype=cdt, device=dev)
             for _ in range(2):
-                p64.execute(x64, o64, cube64)
-            e64 = []
-            for _ in range(3):
+                p2.execute(x2, o2, cube2)
+            evs2 = []
+            for _ in range(reps):
                 flush.zero_()
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                p64.execute(x64, o64, cube64)
+                p2.execute(x2, o2, cube2)
                 b.record(stream)
-                e64.append((a, b))
+                evs2.append((a, b))
             torch.cuda.synchronize(dev)
-            ms64 = sum(a.elapsed_time(b) for a, b in e64) / len(e64)
-            fp64 = {"value": w.total_bands / (ms64 / 1e3), "ms_per_step": ms64, "ratio_fp32_over_fp64": ms64 / ms}
-            del cube64, o64, x64, p64, v64d
+            ms2 = sum(a.elapsed_time(b) for a, b in evs2) / len(evs2)
+            e2 = None
+            if w.direction == "roundtrip":
+                vol = float(np.prod(w.n))
+                e2 = (torch.linalg.vector_norm(o2 - vol * x2) / torch.linalg.vector_norm(vol * x2)).item()
+            del o2, x2, cube2, p2, vd2
+            return {"value": w.total_bands / (ms2 / 1e3), "ms_per_step": ms2, "ratio_vs_fp32": ms2 / ms,
+                    "rel_l2_roundtrip": e2}
+        try:
+            fp64 = time_plan("fp64")
         except fftb.FFTBError as e:
             fp64 = {"unavailable": str(e)}
+        try:
+            mixed_tc = time_plan("mixed", reps=5)
+        except fftb.FFTBError as e:
+            mixed_tc = {"unavailable": str(e)}
 
         # end to end through the C ABI with host buffers (copies in the timed region)
         pin_in = torch.from_numpy(c).pin_memory()
@@ -410,6 +421,7 @@ def run_ours(args):
                            "l2": "flushed between timed steps (256 MiB write)"},
                 "rel_l2": err,
                 "fp64_gpu": fp64,
+                "mixed_tc_gpu": mixed_tc,
                 "roofline": roofline,
                 "cpu_baseline": cpu,
                 "e2e": {"value": w.total_bands / e2e_s, "unit": "bands/s", "h2d_bytes_per_step": nbytes,

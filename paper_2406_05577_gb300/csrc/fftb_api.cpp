@@ -20,14 +20,18 @@
 
 namespace fftb {
 
-template <typename T> size_t stick_smem_t(int);
-template <typename T> size_t plane_smem_t(int, int, int, int);
-template <typename T> int stick_tile_t(int);
-template <typename T> cudaError_t launch_stick_t(int, const Launch&, int);
-template <typename T> cudaError_t launch_plane_t(int, const Launch&);
-template <typename T> cudaError_t prepare_t(int, int, int, int, int);
-template <typename T> int plane_occupancy_t(int, int, int, int, int);
-template <typename T> int stick_occupancy_t(int);
+template <typename T, bool TC> size_t stick_smem_t(int);
+template <typename T, bool TC> size_t plane_smem_t(int, int, int, int);
+template <typename T, bool TC> int stick_tile_t(int);
+template <typename T, bool TC> cudaError_t launch_stick_t(int, const Launch&, int);
+template <typename T, bool TC> cudaError_t launch_plane_t(int, const Launch&);
+template <typename T, bool TC> cudaError_t prepare_t(int, int, int, int, int);
+template <typename T, bool TC> int plane_occupancy_t(int, int, int, int, int);
+template <typename T, bool TC> int stick_occupancy_t(int);
+
+// P_F64 -> double, P_F32 -> float, P_TC -> float with tensor-core radix-8 passes
+#define FFTB_BY_PREC(prec, call)                                                           \
+  ((prec) == P_F64 ? call<double, false> : (prec) == P_TC ? call<float, true> : call<float, false>)
 
 static const int kSizes[] = {12, 16, 20, 24, 32, 40, 48, 64, 96, 128, 160};
 
@@ -37,27 +41,22 @@ bool grid_size_supported(int n) {
   return false;
 }
 bool plane_size_supported(int n0, int n1) { return n0 == n1 && grid_size_supported(n0); }
-size_t stick_smem(int prec, int n2) { return prec == P_F64 ? stick_smem_t<double>(n2) : stick_smem_t<float>(n2); }
+size_t stick_smem(int prec, int n2) { return FFTB_BY_PREC(prec, stick_smem_t)(n2); }
 size_t plane_smem(int prec, int n0, int n1, int xmax, int a_bufs) {
-  return prec == P_F64 ? plane_smem_t<double>(n0, n1, xmax, a_bufs) : plane_smem_t<float>(n0, n1, xmax, a_bufs);
+  return FFTB_BY_PREC(prec, plane_smem_t)(n0, n1, xmax, a_bufs);
 }
-int stick_tile(int prec, int n2) { return prec == P_F64 ? stick_tile_t<double>(n2) : stick_tile_t<float>(n2); }
+int stick_tile(int prec, int n2) { return FFTB_BY_PREC(prec, stick_tile_t)(n2); }
 cudaError_t prepare_kernels(int prec, int n0, int n1, int n2, int xmax, int a_bufs) {
-  return prec == P_F64 ? prepare_t<double>(n0, n1, n2, xmax, a_bufs) : prepare_t<float>(n0, n1, n2, xmax, a_bufs);
+  return FFTB_BY_PREC(prec, prepare_t)(n0, n1, n2, xmax, a_bufs);
 }
-int stick_occupancy(int prec, int n2) {
-  return prec == P_F64 ? stick_occupancy_t<double>(n2) : stick_occupancy_t<float>(n2);
-}
+int stick_occupancy(int prec, int n2) { return FFTB_BY_PREC(prec, stick_occupancy_t)(n2); }
 int plane_occupancy(int prec, int mode, int n0, int n1, int xmax, int a_bufs) {
-  return prec == P_F64 ? plane_occupancy_t<double>(mode, n0, n1, xmax, a_bufs)
-                       : plane_occupancy_t<float>(mode, n0, n1, xmax, a_bufs);
+  return FFTB_BY_PREC(prec, plane_occupancy_t)(mode, n0, n1, xmax, a_bufs);
 }
 cudaError_t launch_stick(int prec, int mode, const Launch& L, int tiles) {
-  return prec == P_F64 ? launch_stick_t<double>(mode, L, tiles) : launch_stick_t<float>(mode, L, tiles);
+  return FFTB_BY_PREC(prec, launch_stick_t)(mode, L, tiles);
 }
-cudaError_t launch_plane(int prec, int mode, const Launch& L) {
-  return prec == P_F64 ? launch_plane_t<double>(mode, L) : launch_plane_t<float>(mode, L);
-}
+cudaError_t launch_plane(int prec, int mode, const Launch& L) { return FFTB_BY_PREC(prec, launch_plane_t)(mode, L); }
 
 static thread_local std::string g_last_error;
 
@@ -166,7 +165,6 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   if (d->layout != 0) return fail(FFTB_ERR_UNSUPPORTED, "only the band-major layout (0) is implemented");
   if (d->max_chunk_bands < 0) return fail(FFTB_ERR_INVALID_ARG, "max_chunk_bands must be >= 0");
   if (d->g_list && !d->g_count) return fail(FFTB_ERR_INVALID_ARG, "g_list given without g_count");
-  if (prec == FFTB_MIXED_TC) return fail(FFTB_ERR_UNSUPPORTED, "MIXED_TC precision is not built yet");
   if (!grid_size_supported(d->n[0]) || !grid_size_supported(d->n[1]) || !grid_size_supported(d->n[2]) ||
       !plane_size_supported(d->n[0], d->n[1]))
     return fail(FFTB_ERR_UNSUPPORTED,
@@ -178,7 +176,7 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   p->nk = d->n_kpoints;
   p->dir = dir;
   p->prec = prec;
-  p->prec_kernel = (prec == FFTB_FP64) ? P_F64 : P_F32;
+  p->prec_kernel = (prec == FFTB_FP64) ? P_F64 : (prec == FFTB_MIXED_TC) ? P_TC : P_F32;
   p->csize = (prec == FFTB_FP64) ? 16 : 8;
   p->geo.resize(p->nk);
   p->bands.resize(p->nk);

@@ -68,7 +68,7 @@ struct Launch {
   cudaStream_t stream;
 };
 
-enum Prec { P_F64 = 0, P_F32 = 1 };
+enum Prec { P_F64 = 0, P_F32 = 1, P_TC = 2 };
 enum Mode { M_G2R = 1, M_R2G = -1, M_APPLY = 2 };
 
 bool grid_size_supported(int n);

@@ -2,5 +2,5 @@
 #include "kernels.cuh"
 
 namespace fftb {
-FFTB_INSTANTIATE(float)
+FFTB_INSTANTIATE(float, false)
 }  // namespace fftb

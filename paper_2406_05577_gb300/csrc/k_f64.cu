@@ -2,5 +2,5 @@
 #include "kernels.cuh"
 
 namespace fftb {
-FFTB_INSTANTIATE(double)
+FFTB_INSTANTIATE(double, false)
 }  // namespace fftb

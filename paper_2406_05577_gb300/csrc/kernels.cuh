@@ -41,7 +41,7 @@ template <typename T, int N2> constexpr size_t stick_smem_c() {
   return sizeof(C) * ((size_t)STICK_NW * (32 / Line<N2>::G) * Line<N2>::PITCH + N2);
 }
 
-template <typename T, int N2, int MODE>
+template <typename T, int N2, int MODE, bool TC = false>
 __global__ void __launch_bounds__(STICK_NW * 32) k_stick(const Launch L) {
   using C = typename cplx<T>::type;
   using LZ = Line<N2>;
@@ -59,6 +59,8 @@ __global__ void __launch_bounds__(STICK_NW * 32) k_stick(const Launch L) {
   __syncthreads();
   typename LZ::template TwCache<C> tc;
   tc.load(g, tw);
+  typename LZ::template TcW<MODE == M_G2R ? +1 : -1> tcw;
+  if constexpr (TC) tcw.load(tw);
   auto zsigned = [](int z) { return z < N2 - N2 / 2 ? z : z - N2; };
   const int smax = L.g.smax;
 
@@ -118,7 +120,8 @@ __global__ void __launch_bounds__(STICK_NW * 32) k_stick(const Launch L) {
           for (int j = 0; j < LZ::R0; ++j) v[m * LZ::R0 + j] = row[wpad(LZ::first_pos(g, m, j))];
         __syncwarp();
       }
-      LZ::template run<+1>(v, g, row, tw, tc);
+      if constexpr (TC) LZ::template run_tc<+1>(v, g, row, scr, tw, tc, tcw);
+      else LZ::template run<+1>(v, g, row, tw, tc);
       if (l < nl) {
 #pragma unroll
         for (int m = 0; m < EZ / LZ::RL; ++m)
@@ -130,7 +133,8 @@ __global__ void __launch_bounds__(STICK_NW * 32) k_stick(const Launch L) {
       for (int m = 0; m < EZ / LZ::R0; ++m)
 #pragma unroll
         for (int j = 0; j < LZ::R0; ++j) v[m * LZ::R0 + j] = Tb[(size_t)LZ::first_pos(g, m, j) * smax];
-      LZ::template run<-1>(v, g, row, tw, tc);
+      if constexpr (TC) LZ::template run_tc<-1>(v, g, row, scr, tw, tc, tcw);
+      else LZ::template run<-1>(v, g, row, tw, tc);
       C* out = static_cast<C*>(L.sph_out) + sph;
       if (canon) {
         if (l < nl) {
@@ -203,7 +207,7 @@ template <int E> struct XiPack {
   __device__ __forceinline__ int get(int q) const { return (int)((w[q >> 2] >> (8 * (q & 3))) & 0xFFu); }
 };
 
-template <typename T, int N0, int N1, int MODE>
+template <typename T, int N0, int N1, int MODE, bool TC = false>
 __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k_plane(const Launch L) {
   using C = typename cplx<T>::type;
   using LY = Line<N1>;
@@ -237,6 +241,15 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   typename LX::template TwCache<C> tcx;
   tcy.load(gy, tw1);
   tcx.load(gx, tw0);
+  // tensor-core DFT8 operands (MIXED_TC): forward sign for G->r, inverse for r->G
+  typename LY::template TcW<+1> wy_p;
+  typename LX::template TcW<+1> wx_p;
+  typename LY::template TcW<-1> wy_m;
+  typename LX::template TcW<-1> wx_m;
+  if constexpr (TC) {
+    if constexpr (MODE != M_R2G) { wy_p.load(tw1); wx_p.load(tw0); }
+    if constexpr (MODE != M_G2R) { wy_m.load(tw1); wx_m.load(tw0); }
+  }
   // signed y of this lane's first-pass / last-pass y positions (direct stick I/O)
   auto ysigned = [](int y) { return y < N1 - N1 / 2 ? y : y - N1; };
 
@@ -316,7 +329,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
             for (int j = 0; j < LY::R0; ++j) v[m * LY::R0 + j] = rowy[wpad(LY::first_pos(gy, m, j))];
           __syncwarp();
         }
-        LY::template run<+1>(v, gy, rowy, tw1, tcy);
+        if constexpr (TC) LY::template run_tc<+1>(v, gy, rowy, scr, tw1, tcy, wy_p);
+        else LY::template run<+1>(v, gy, rowy, tw1, tcy);
         if (ly < nl) {
 #pragma unroll
           for (int m = 0; m < EY / LY::RL; ++m)
@@ -336,7 +350,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
           const int xi = xin.get(q);
           v[q] = (live && xi != 255) ? A[row * XP + xi] : czero<C>();
         }
-        LX::template run<+1>(v, gx, rowx, tw0, tcx);
+        if constexpr (TC) LX::template run_tc<+1>(v, gx, rowx, scr, tw0, tcx, wx_p);
+        else LX::template run<+1>(v, gx, rowx, tw0, tcx);
         if constexpr (MODE == M_G2R) {
           if (live) {
             C* out = static_cast<C*>(L.cube_out) + plane + (size_t)row * N0;
@@ -361,7 +376,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
             for (int j = 0; j < LX::R0; ++j) v[m * LX::R0 + j] = rowx[wpad(LX::first_pos(gx, m, j))];
           __syncwarp();
-          LX::template run<-1>(v, gx, rowx, tw0, tcx);
+          if constexpr (TC) LX::template run_tc<-1>(v, gx, rowx, scr, tw0, tcx, wx_m);
+          else LX::template run<-1>(v, gx, rowx, tw0, tcx);
           if (live) {
 #pragma unroll
             for (int q = 0; q < EX; ++q) {
@@ -384,7 +400,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
           for (int j = 0; j < LX::R0; ++j)
             v[m * LX::R0 + j] = live ? in[LX::first_pos(gx, m, j)] : czero<C>();
-        LX::template run<-1>(v, gx, rowx, tw0, tcx);
+        if constexpr (TC) LX::template run_tc<-1>(v, gx, rowx, scr, tw0, tcx, wx_m);
+        else LX::template run<-1>(v, gx, rowx, tw0, tcx);
         if (live) {
 #pragma unroll
           for (int q = 0; q < EX; ++q) {
@@ -407,7 +424,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
         for (int m = 0; m < EY / LY::R0; ++m)
 #pragma unroll
           for (int j = 0; j < LY::R0; ++j) v[m * LY::R0 + j] = A[LY::first_pos(gy, m, j) * XP + col];
-        LY::template run<-1>(v, gy, rowy, tw1, tcy);
+        if constexpr (TC) LY::template run_tc<-1>(v, gy, rowy, scr, tw1, tcy, wy_m);
+        else LY::template run<-1>(v, gy, rowy, tw1, tcy);
         if (ki.flags & KF_CONTIGUOUS_COLUMNS) {
           if (ly < nl) {
             const int sa = ci.x, len = ci.y, ylo = ci.z;
@@ -442,7 +460,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 // ---------------------------------------------------------------- dispatch
 #define FFTB_SIZES(X) X(12) X(16) X(20) X(24) X(32) X(40) X(48) X(64) X(96) X(128) X(160)
 
-template <typename T> size_t stick_smem_t(int n2) {
+template <typename T, bool TC> size_t stick_smem_t(int n2) {
   switch (n2) {
 #define C_(N) case N: return stick_smem_c<T, N>();
     FFTB_SIZES(C_)
@@ -450,7 +468,7 @@ template <typename T> size_t stick_smem_t(int n2) {
   }
   return 0;
 }
-template <typename T> size_t plane_smem_t(int n0, int n1, int xmax, int a_bufs) {
+template <typename T, bool TC> size_t plane_smem_t(int n0, int n1, int xmax, int a_bufs) {
   if (n0 != n1) return 0;
   switch (n0) {
 #define C_(N) case N: return plane_smem_c<T, N, N>(xmax, a_bufs);
@@ -459,7 +477,7 @@ template <typename T> size_t plane_smem_t(int n0, int n1, int xmax, int a_bufs) 
   }
   return 0;
 }
-template <typename T> int stick_tile_t(int n2) {
+template <typename T, bool TC> int stick_tile_t(int n2) {
   switch (n2) {
 #define C_(N) case N: return stick_tile_c2<N>();
     FFTB_SIZES(C_)
@@ -468,118 +486,118 @@ template <typename T> int stick_tile_t(int n2) {
   return 0;
 }
 
-template <typename T, int N2> cudaError_t go_stick(int mode, const Launch& L, int ctas) {
+template <typename T, bool TC, int N2> cudaError_t go_stick(int mode, const Launch& L, int ctas) {
   const size_t smem = stick_smem_c<T, N2>();
   const int gpb = (L.g.smax + (32 / Line<N2>::G) - 1) / (32 / Line<N2>::G);
   const int need = (L.nb * gpb + STICK_NW - 1) / STICK_NW;  // one task per warp
   const dim3 grid(ctas > 0 ? min(ctas, need) : need);
-  if (mode == M_G2R) k_stick<T, N2, M_G2R><<<grid, STICK_NW * 32, smem, L.stream>>>(L);
-  else k_stick<T, N2, M_R2G><<<grid, STICK_NW * 32, smem, L.stream>>>(L);
+  if (mode == M_G2R) k_stick<T, N2, M_G2R, TC><<<grid, STICK_NW * 32, smem, L.stream>>>(L);
+  else k_stick<T, N2, M_R2G, TC><<<grid, STICK_NW * 32, smem, L.stream>>>(L);
   return cudaGetLastError();
 }
-template <typename T, int N> cudaError_t go_plane(int mode, const Launch& L) {
+template <typename T, bool TC, int N> cudaError_t go_plane(int mode, const Launch& L) {
   const size_t smem = plane_smem_c<T, N, N>(L.g.xmax, L.a_bufs);
   const int nplanes = L.nb * L.g.n2;
   const dim3 grid(L.plane_ctas > 0 ? min(L.plane_ctas, nplanes) : nplanes);
   constexpr int NT = PlaneCfg<T>::NW * 32;
-  if (mode == M_G2R) k_plane<T, N, N, M_G2R><<<grid, NT, smem, L.stream>>>(L);
-  else if (mode == M_R2G) k_plane<T, N, N, M_R2G><<<grid, NT, smem, L.stream>>>(L);
-  else k_plane<T, N, N, M_APPLY><<<grid, NT, smem, L.stream>>>(L);
+  if (mode == M_G2R) k_plane<T, N, N, M_G2R, TC><<<grid, NT, smem, L.stream>>>(L);
+  else if (mode == M_R2G) k_plane<T, N, N, M_R2G, TC><<<grid, NT, smem, L.stream>>>(L);
+  else k_plane<T, N, N, M_APPLY, TC><<<grid, NT, smem, L.stream>>>(L);
   return cudaGetLastError();
 }
-template <typename T, int N2> cudaError_t prep_stick() {
+template <typename T, bool TC, int N2> cudaError_t prep_stick() {
   const int s = (int)stick_smem_c<T, N2>();
-  cudaError_t e = cudaFuncSetAttribute(k_stick<T, N2, M_G2R>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaError_t e = cudaFuncSetAttribute(k_stick<T, N2, M_G2R, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_stick<T, N2, M_R2G>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+    e = cudaFuncSetAttribute(k_stick<T, N2, M_R2G, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   return e;
 }
-template <typename T, int N> cudaError_t prep_plane(int xmax, int a_bufs) {
+template <typename T, bool TC, int N> cudaError_t prep_plane(int xmax, int a_bufs) {
   const int s = (int)plane_smem_c<T, N, N>(xmax, a_bufs);
-  cudaError_t e = cudaFuncSetAttribute(k_plane<T, N, N, M_G2R>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaError_t e = cudaFuncSetAttribute(k_plane<T, N, N, M_G2R, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_plane<T, N, N, M_R2G>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+    e = cudaFuncSetAttribute(k_plane<T, N, N, M_R2G, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_plane<T, N, N, M_APPLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+    e = cudaFuncSetAttribute(k_plane<T, N, N, M_APPLY, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   return e;
 }
 
-template <typename T, int N> int occ_plane(int mode, int xmax, int a_bufs) {
+template <typename T, bool TC, int N> int occ_plane(int mode, int xmax, int a_bufs) {
   const size_t smem = plane_smem_c<T, N, N>(xmax, a_bufs);
   constexpr int NT = PlaneCfg<T>::NW * 32;
   int nb = 0;
   cudaError_t e;
-  if (mode == M_G2R) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_G2R>, NT, smem);
-  else if (mode == M_R2G) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_R2G>, NT, smem);
-  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_APPLY>, NT, smem);
+  if (mode == M_G2R) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_G2R, TC>, NT, smem);
+  else if (mode == M_R2G) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_R2G, TC>, NT, smem);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_APPLY, TC>, NT, smem);
   return e == cudaSuccess ? nb : 0;
 }
-template <typename T, int N2> int occ_stick() {
+template <typename T, bool TC, int N2> int occ_stick() {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stick<T, N2, M_G2R>, STICK_NW * 32, stick_smem_c<T, N2>()) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stick<T, N2, M_G2R, TC>, STICK_NW * 32, stick_smem_c<T, N2>()) !=
       cudaSuccess)
     return 0;
   return nb;
 }
-template <typename T> int stick_occupancy_t(int n2) {
+template <typename T, bool TC> int stick_occupancy_t(int n2) {
   switch (n2) {
-#define C_(N) case N: return occ_stick<T, N>();
+#define C_(N) case N: return occ_stick<T, TC, N>();
     FFTB_SIZES(C_)
 #undef C_
   }
   return 0;
 }
-template <typename T> int plane_occupancy_t(int mode, int n0, int n1, int xmax, int a_bufs) {
+template <typename T, bool TC> int plane_occupancy_t(int mode, int n0, int n1, int xmax, int a_bufs) {
   if (n0 != n1) return 0;
   switch (n0) {
-#define C_(N) case N: return occ_plane<T, N>(mode, xmax, a_bufs);
+#define C_(N) case N: return occ_plane<T, TC, N>(mode, xmax, a_bufs);
     FFTB_SIZES(C_)
 #undef C_
   }
   return 0;
 }
 
-template <typename T> cudaError_t launch_stick_t(int mode, const Launch& L, int tiles) {
+template <typename T, bool TC> cudaError_t launch_stick_t(int mode, const Launch& L, int tiles) {
   switch (L.g.n2) {
-#define C_(N) case N: return go_stick<T, N>(mode, L, tiles);
+#define C_(N) case N: return go_stick<T, TC, N>(mode, L, tiles);
     FFTB_SIZES(C_)
 #undef C_
   }
   return cudaErrorInvalidValue;
 }
-template <typename T> cudaError_t launch_plane_t(int mode, const Launch& L) {
+template <typename T, bool TC> cudaError_t launch_plane_t(int mode, const Launch& L) {
   if (L.g.n0 != L.g.n1) return cudaErrorInvalidValue;
   switch (L.g.n0) {
-#define C_(N) case N: return go_plane<T, N>(mode, L);
+#define C_(N) case N: return go_plane<T, TC, N>(mode, L);
     FFTB_SIZES(C_)
 #undef C_
   }
   return cudaErrorInvalidValue;
 }
-template <typename T> cudaError_t prepare_t(int n0, int n1, int n2, int xmax, int a_bufs) {
+template <typename T, bool TC> cudaError_t prepare_t(int n0, int n1, int n2, int xmax, int a_bufs) {
   cudaError_t e = cudaErrorInvalidValue;
   switch (n2) {
-#define C_(N) case N: e = prep_stick<T, N>(); break;
+#define C_(N) case N: e = prep_stick<T, TC, N>(); break;
     FFTB_SIZES(C_)
 #undef C_
   }
   if (e != cudaSuccess || n0 != n1) return e == cudaSuccess ? cudaErrorInvalidValue : e;
   switch (n0) {
-#define C_(N) case N: return prep_plane<T, N>(xmax, a_bufs);
+#define C_(N) case N: return prep_plane<T, TC, N>(xmax, a_bufs);
     FFTB_SIZES(C_)
 #undef C_
   }
   return cudaErrorInvalidValue;
 }
 
-#define FFTB_INSTANTIATE(T)                                                        \
-  template size_t stick_smem_t<T>(int);                                            \
-  template size_t plane_smem_t<T>(int, int, int, int);                             \
-  template int stick_tile_t<T>(int);                                               \
-  template cudaError_t launch_stick_t<T>(int, const Launch&, int);                 \
-  template cudaError_t launch_plane_t<T>(int, const Launch&);                      \
-  template cudaError_t prepare_t<T>(int, int, int, int, int);                     \
-  template int plane_occupancy_t<T>(int, int, int, int, int);                     \
-  template int stick_occupancy_t<T>(int);
+#define FFTB_INSTANTIATE(T, TC)                                                    \
+  template size_t stick_smem_t<T, TC>(int);                                        \
+  template size_t plane_smem_t<T, TC>(int, int, int, int);                         \
+  template int stick_tile_t<T, TC>(int);                                           \
+  template cudaError_t launch_stick_t<T, TC>(int, const Launch&, int);             \
+  template cudaError_t launch_plane_t<T, TC>(int, const Launch&);                  \
+  template cudaError_t prepare_t<T, TC>(int, int, int, int, int);                  \
+  template int plane_occupancy_t<T, TC>(int, int, int, int, int);                  \
+  template int stick_occupancy_t<T, TC>(int);
 
 }  // namespace fftb

@@ -11,6 +11,8 @@
 // lane (G = 1) exchanges by register renaming only.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "fft_core.cuh"
 
 namespace fftb {
@@ -34,6 +36,39 @@ FFTB_LP(96, 12, 6, 4, 4, 0);
 FFTB_LP(128, 16, 16, 8, 0, 0);
 FFTB_LP(160, 20, 4, 4, 2, 5);
 #undef FFTB_LP
+
+// ----------------------------------------------------------- tensor cores
+// A radix-8 pass as a dense product on the tensor cores (split precision):
+// 16 butterflies (rows) x 8 complex inputs = a 16 x 16 real matrix A, the
+// DFT8 matrix as a 16 x 16 real matrix W (real index 2 j + re/im), one
+// mma.sync.m16n8k16 per 8 output columns. A and W are split into FP16 hi + lo
+// parts (x = hi + lo + O(2^-22 x)); D = A_hi W_hi + A_hi W_lo + A_lo W_hi is
+// accumulated in FP32. Each row is scaled by a power of two first so that its
+// largest component lies in [2^13, 2^14) (inside FP16 range, lo parts normal),
+// and unscaled exactly afterwards.
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ uint32_t h2u(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
+// split (x, y) into packed FP16 hi and lo
+__device__ __forceinline__ void split2(float x, float y, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(x, y);
+  const float2 hf = __half22float2(h);
+  hi = h2u(h);
+  lo = h2u(__floats2half2_rn(x - hf.x, y - hf.y));
+}
+// 2^e such that m * 2^e < 2^15 (m >= 0), and its inverse
+__device__ __forceinline__ void row_scale(float m, float& s, float& inv) {
+  int ex = (__float_as_int(m) >> 23) & 0xFF;      // biased exponent of m
+  int es = 141 - ex + 127;                        // 2^(14 - (ex - 127)), biased
+  es = es < 1 ? 1 : (es > 254 ? 254 : es);
+  s = __int_as_float(es << 23);
+  inv = __int_as_float((254 - es) << 23);         // 2^-(es - 127)
+}
 
 template <int N> struct Line {
   static constexpr int E = LP<N>::E;
@@ -136,6 +171,160 @@ template <int N> struct Line {
       exchange<p>(v, g, row);
       passes<p + 1, S>(v, g, row, tw, tc);
     }
+  }
+
+  // ---- tensor-core radix-8 pass (MIXED_TC precision)
+  // W fragments of this lane (B operand, col layout): n-tile nt covers output
+  // columns 2 k' + c' for k' in [4 nt, 4 nt + 4); lane holds rows k = 2 t, 2 t + 1,
+  // 2 t + 8, 2 t + 9 (t = lane & 3) of column n = lane >> 2.
+  template <int S> struct TcW {
+    uint32_t hi[2][2], lo[2][2];
+    __device__ __forceinline__ void load(const float2* __restrict__ tw) {
+      const int lane = threadIdx.x & 31, t = lane & 3, gq = lane >> 2;
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int kp = 4 * nt + (gq >> 1), cp = gq & 1;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = t + 4 * h;
+          const float2 w = tw[((j * kp) & 7) * (N / 8)];   // e^{+2 pi i j k'/8}
+          const float wr = w.x, wi = float(S) * w.y;
+          // rows k = 2 j (re input), 2 j + 1 (im input) of column (k', c')
+          const float e0 = cp == 0 ? wr : wi;        // re input -> re out: wr ; -> im out: wi
+          const float e1 = cp == 0 ? -wi : wr;       // im input -> re out: -wi; -> im out: wr
+          split2(e0, e1, hi[nt][h], lo[nt][h]);
+        }
+      }
+    }
+  };
+
+  // Pass p (radix 8) for all WL = 32 / G lines of the warp, in place in the
+  // warp's scratch rows (base = first row). Inputs and outputs stay where the
+  // Stockham pass would read and write them.
+  template <int p, int S>
+  __device__ __forceinline__ static void tc_pass(float2* base, const float2* __restrict__ tw, const TcW<S>& W) {
+    static_assert(radix<p>() == 8, "tensor-core pass is radix 8");
+    constexpr int P = span<p>(), NB = N / 8, WL = 32 / G, TILES = WL * NB / 16, STEP = N / (P * 8);
+    static_assert((WL * NB) % 16 == 0, "butterflies per warp must fill 16-row tiles");
+    const int lane = threadIdx.x & 31, t = lane & 3, gq = lane >> 2;
+    float2 x[TILES][2][2];  // [tile][row half][input j = t + 4 h]
+#pragma unroll
+    for (int ti = 0; ti < TILES; ++ti)
+#pragma unroll
+      for (int rh = 0; rh < 2; ++rh) {
+        const int b = 16 * ti + gq + 8 * rh, line = b / NB, i = b - line * NB;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = t + 4 * h;
+          float2 val = base[line * PITCH + wpad(i + j * NB)];
+          if constexpr (P > 1) {
+            const float2 w = tw[j * (i % P) * STEP];
+            val = (S > 0) ? cmul(val, w) : cmulc(val, w);
+          }
+          x[ti][rh][h] = val;
+        }
+      }
+    __syncwarp();
+#pragma unroll
+    for (int ti = 0; ti < TILES; ++ti) {
+      float s[2], inv[2];
+#pragma unroll
+      for (int rh = 0; rh < 2; ++rh) {
+        float m = fmaxf(fmaxf(fabsf(x[ti][rh][0].x), fabsf(x[ti][rh][0].y)),
+                        fmaxf(fabsf(x[ti][rh][1].x), fabsf(x[ti][rh][1].y)));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+        row_scale(m, s[rh], inv[rh]);
+      }
+      uint32_t ah[4], al[4];
+      split2(x[ti][0][0].x * s[0], x[ti][0][0].y * s[0], ah[0], al[0]);   // row gq,     j = t
+      split2(x[ti][1][0].x * s[1], x[ti][1][0].y * s[1], ah[1], al[1]);   // row gq + 8, j = t
+      split2(x[ti][0][1].x * s[0], x[ti][0][1].y * s[0], ah[2], al[2]);   // row gq,     j = t + 4
+      split2(x[ti][1][1].x * s[1], x[ti][1][1].y * s[1], ah[3], al[3]);   // row gq + 8, j = t + 4
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        mma16816(d, ah, W.hi[nt][0], W.hi[nt][1]);
+        mma16816(d, ah, W.lo[nt][0], W.lo[nt][1]);
+        mma16816(d, al, W.hi[nt][0], W.hi[nt][1]);
+        const int kp = 4 * nt + t;  // output complex index held by this lane
+#pragma unroll
+        for (int rh = 0; rh < 2; ++rh) {
+          const int b = 16 * ti + gq + 8 * rh, line = b / NB, i = b - line * NB, k = i % P;
+          base[line * PITCH + wpad((i - k) * 8 + k + kp * P)] = make_float2(d[2 * rh] * inv[rh], d[2 * rh + 1] * inv[rh]);
+        }
+      }
+    }
+  }
+
+  // positions the lane loads for pass q (q = NP means the final last_pos order)
+  template <int q, typename C>
+  __device__ __forceinline__ static void load_for(C (&v)[E], int g, const C* row) {
+    if constexpr (q < NP) {
+      constexpr int Rq = radix<q>(), NBq = N / Rq;
+#pragma unroll
+      for (int m = 0; m < E / Rq; ++m)
+#pragma unroll
+        for (int j = 0; j < Rq; ++j) v[m * Rq + j] = row[wpad(g + m * G + j * NBq)];
+    } else {
+#pragma unroll
+      for (int m = 0; m < E / RL; ++m)
+#pragma unroll
+        for (int j = 0; j < RL; ++j) v[m * RL + j] = row[wpad(last_pos(g, m, j))];
+    }
+  }
+  // store pass p's outputs (lane layout) where the Stockham pass puts them
+  template <int p, typename C>
+  __device__ __forceinline__ static void store_out(const C (&v)[E], int g, C* row) {
+    constexpr int R = radix<p>(), P = span<p>();
+#pragma unroll
+    for (int m = 0; m < E / R; ++m) {
+      const int i = g + m * G, k = i % P;
+#pragma unroll
+      for (int j = 0; j < R; ++j) row[wpad((i - k) * R + k + j * P)] = v[m * R + j];
+    }
+  }
+
+  // row (the lane's line) lies inside the warp's scratch that starts at base:
+  // the two alias, so neither is __restrict__.
+  template <int p, int S>
+  __device__ __forceinline__ static void tc_passes(float2 (&v)[E], int g, float2* row, float2* base,
+                                                   const float2* __restrict__ tw, const TwCache<float2>& tc,
+                                                   const TcW<S>& W) {
+    if constexpr (radix<p>() == 8 && G > 1) {
+      if constexpr (p == 0) {
+#pragma unroll
+        for (int m = 0; m < E / R0; ++m)
+#pragma unroll
+          for (int j = 0; j < R0; ++j) row[wpad(first_pos(g, m, j))] = v[m * R0 + j];
+        __syncwarp();
+      }
+      tc_pass<p, S>(base, tw, W);
+      __syncwarp();
+      load_for<p + 1>(v, g, row);
+      __syncwarp();
+      if constexpr (p + 1 < NP) tc_passes<p + 1, S>(v, g, row, base, tw, tc, W);
+    } else {
+      compute<p, S>(v, g, tw, tc);
+      if constexpr (p + 1 < NP) {
+        store_out<p>(v, g, row);
+        __syncwarp();
+        if constexpr (!(radix<p + 1>() == 8 && G > 1)) {
+          load_for<p + 1>(v, g, row);
+          __syncwarp();
+        }
+        tc_passes<p + 1, S>(v, g, row, base, tw, tc, W);
+      }
+    }
+  }
+
+  // As run(), with every radix-8 pass on the tensor cores (MIXED_TC).
+  // base = the warp's first scratch row; W = TcW<S>::load for this table.
+  template <int S>
+  __device__ __forceinline__ static void run_tc(float2 (&v)[E], int g, float2* row, float2* base,
+                                                const float2* __restrict__ tw, const TwCache<float2>& tc,
+                                                const TcW<S>& W) {
+    tc_passes<0, S>(v, g, row, base, tw, tc, W);
   }
 
   // v in first_pos order -> DFT (sign S) in last_pos order. All lanes of the

@@ -13,7 +13,7 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 2e-6}
+TOL = {"fp64": 1e-12, "fp32": 2e-6, "mixed": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +34,7 @@ def relerr(a, b):
 
 def to_dev(x, prec):
     import torch
-    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    dt = torch.complex128 if prec == "fp64" else torch.complex64  # fp32 and mixed store complex64
     return torch.from_numpy(np.ascontiguousarray(x)).to(dt).cuda()
 
 
@@ -240,3 +240,43 @@ def test_autotune_keeps_results(F, tmp_path, monkeypatch):
         assert relerr(out.cpu().numpy(), want) <= TOL["fp64"]
     lines = (tmp_path / "tune.txt").read_text().splitlines()
     assert len(lines) == 1 and lines[0].startswith("24x24x24|")
+
+
+@pytest.mark.parametrize("n,r,k,bands", [((64, 64, 64), 16.0, (0.3, -0.2, 0.1), 6),
+                                         ((128, 128, 128), 32.0, None, 2),
+                                         ((64, 64, 32), 12.0, None, 4),
+                                         ((24, 24, 24), 6.0, None, 3)])
+def test_mixed_tc_vs_oracle(F, n, r, k, bands):
+    """Split-precision tensor-core radix-8 passes: relative L2 <= 1e-5."""
+    tol = 1e-5
+    g = oracle.sphere_gvectors(n, r, k if k else (0, 0, 0))
+    c = fi.complex_gaussian((bands, len(g)), 111).astype(np.complex64).astype(np.complex128)
+    kw = dict(radius=r, bands=[bands])
+    if k:
+        kw["kshift"] = [k]
+    _, cube, _ = run_plan(F, n, "g2r", "mixed", c, **kw)
+    want = oracle.g2r(g, c, n).reshape(-1)
+    e1 = relerr(cube, want)
+    R = rounded(fi.complex_gaussian((bands, n[2], n[1], n[0]), 112), "fp32")
+    _, sph, _ = run_plan(F, n, "r2g", "mixed", R, **kw)
+    e2 = relerr(sph, oracle.r2g(g, R, n).reshape(-1))
+    _, back, _ = run_plan(F, n, "roundtrip", "mixed", c, **kw)
+    e3 = relerr(back, np.prod(n) * c.reshape(-1))
+    assert max(e1, e2, e3) <= tol, (e1, e2, e3)
+
+
+def test_mixed_tc_apply_vs_oracle(F):
+    import torch
+    n, r, bands = (64, 64, 64), 16.0, 4
+    g = oracle.sphere_gvectors(n, r)
+    c = fi.complex_gaussian((bands, len(g)), 121).astype(np.complex64).astype(np.complex128)
+    v = fi.gaussian_potential(n, 32, 4.0, seed=122).astype(np.float32)
+    plan = F.Plan(n, "apply", "mixed", radius=r, bands=[bands])
+    vd = torch.from_numpy(v).cuda()
+    plan.set_potential(vd)
+    x = torch.from_numpy(c.astype(np.complex64).reshape(-1)).cuda()
+    out = torch.empty_like(x)
+    plan.execute(x, out)
+    torch.cuda.synchronize()
+    want = oracle.apply_potential(g, c, v.astype(np.float64), n)
+    assert relerr(out.cpu().numpy(), want) <= 1e-5
