@@ -79,10 +79,12 @@ class Workload:
             kw["kshift"] = self.kshift
         return kw
 
-    def coefficients(self, spheres):
+    def coefficients(self, spheres, rank=0):
+        """This rank's bands: rank r holds bands [r B, (r + 1) B) of a global
+        batch of world * B bands (weak scaling), drawn with per-rank seeds."""
         parts = []
         for k, (g, b) in enumerate(zip(spheres, self.bands)):
-            c = fi.complex_gaussian((b, len(g)), self.seed + 100 * k)
+            c = fi.complex_gaussian((b, len(g)), self.seed + 100 * k + 7919 * rank)
             if self.envelope:
                 c = c * fi.gaussian_envelope(g, self.envelope)[None, :]
             parts.append(c)
@@ -269,7 +271,7 @@ def run_ours(args):
     spheres = [plan.sphere(k) for k in range(w.nk)]
     ngws = [len(g) for g in spheres]
     sticks = [fftb.fftb_sphere_sticks(w.n, g)[0] for g in spheres]
-    parts = w.coefficients(spheres)
+    parts = w.coefficients(spheres, rank)
     c = np.concatenate([p.reshape(-1) for p in parts]).astype(np.complex64)
     x = torch.from_numpy(c).to(dev)
     out = torch.empty_like(x)
@@ -312,10 +314,8 @@ def run_ours(args):
     launches = plan.launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    from paper_2406_05577_gb300.shard import max_over_ranks
+    ms = max_over_ranks(ms, device=dev)
     value = world * w.total_bands / (ms / 1e3)
 
     # per-kernel event times over the same steps (graphs off while timing)
