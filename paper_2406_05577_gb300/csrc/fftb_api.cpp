@@ -21,12 +21,12 @@
 namespace fftb {
 
 template <typename T, bool TC> size_t stick_smem_t(int);
-template <typename T, bool TC> size_t plane_smem_t(int, int, int, int);
+template <typename T, bool TC> size_t plane_smem_t(int, int, int, int, bool);
 template <typename T, bool TC> int stick_tile_t(int);
 template <typename T, bool TC> cudaError_t launch_stick_t(int, const Launch&, int);
 template <typename T, bool TC> cudaError_t launch_plane_t(int, const Launch&);
-template <typename T, bool TC> cudaError_t prepare_t(int, int, int, int, int);
-template <typename T, bool TC> int plane_occupancy_t(int, int, int, int, int);
+template <typename T, bool TC> cudaError_t prepare_t(int, int, int, int, int, bool);
+template <typename T, bool TC> int plane_occupancy_t(int, int, int, int, int, bool);
 template <typename T, bool TC> int stick_occupancy_t(int);
 
 // P_F64 -> double, P_F32 -> float, P_TC -> float with tensor-core radix-8 passes
@@ -42,16 +42,16 @@ bool grid_size_supported(int n) {
 }
 bool plane_size_supported(int n0, int n1) { return n0 == n1 && grid_size_supported(n0); }
 size_t stick_smem(int prec, int n2) { return FFTB_BY_PREC(prec, stick_smem_t)(n2); }
-size_t plane_smem(int prec, int n0, int n1, int xmax, int a_bufs) {
-  return FFTB_BY_PREC(prec, plane_smem_t)(n0, n1, xmax, a_bufs);
+size_t plane_smem(int prec, int n0, int n1, int xmax, int a_bufs, bool a_glob) {
+  return FFTB_BY_PREC(prec, plane_smem_t)(n0, n1, xmax, a_bufs, a_glob);
 }
 int stick_tile(int prec, int n2) { return FFTB_BY_PREC(prec, stick_tile_t)(n2); }
-cudaError_t prepare_kernels(int prec, int n0, int n1, int n2, int xmax, int a_bufs) {
-  return FFTB_BY_PREC(prec, prepare_t)(n0, n1, n2, xmax, a_bufs);
+cudaError_t prepare_kernels(int prec, int n0, int n1, int n2, int xmax, int a_bufs, bool a_glob) {
+  return FFTB_BY_PREC(prec, prepare_t)(n0, n1, n2, xmax, a_bufs, a_glob);
 }
 int stick_occupancy(int prec, int n2) { return FFTB_BY_PREC(prec, stick_occupancy_t)(n2); }
-int plane_occupancy(int prec, int mode, int n0, int n1, int xmax, int a_bufs) {
-  return FFTB_BY_PREC(prec, plane_occupancy_t)(mode, n0, n1, xmax, a_bufs);
+int plane_occupancy(int prec, int mode, int n0, int n1, int xmax, int a_bufs, bool a_glob) {
+  return FFTB_BY_PREC(prec, plane_occupancy_t)(mode, n0, n1, xmax, a_bufs, a_glob);
 }
 cudaError_t launch_stick(int prec, int mode, const Launch& L, int tiles) {
   return FFTB_BY_PREC(prec, launch_stick_t)(mode, L, tiles);
@@ -89,6 +89,9 @@ struct fftb_plan_s {
   int device = 0;
   int32_t plane_ctas[3] = {0, 0, 0};  // persistent CTAs: G->r, r->G, apply
   int32_t a_bufs = 2;                 // slab-plane buffers of the plane stage
+  bool a_glob = false;                // slab planes in global memory (FP64, large planes)
+  void* d_A = nullptr;                // those slab planes, one block per persistent CTA
+  size_t A_bytes = 0;
   // device memory
   void* d_tables = nullptr;
   size_t tables_bytes = 0;
@@ -141,6 +144,7 @@ void release(fftb_plan_s* p) {
   if (!p) return;
   if (p->d_tables) cudaFree(p->d_tables);
   if (p->d_T) cudaFree(p->d_T);
+  if (p->d_A) cudaFree(p->d_A);
   if (p->d_stage_in) cudaFree(p->d_stage_in);
   if (p->d_stage_out) cudaFree(p->d_stage_out);
   if (p->d_stage_cube) cudaFree(p->d_stage_cube);
@@ -214,8 +218,12 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
 
   const size_t smem_limit = 227 * 1024;
   if (plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, 2) > smem_limit) p->a_bufs = 1;
+  if (plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, p->a_bufs) > smem_limit && p->prec_kernel == P_F64) {
+    p->a_bufs = 2;  // slab planes in global memory, double buffered
+    p->a_glob = true;
+  }
   if (stick_smem(p->prec_kernel, p->n[2]) > smem_limit ||
-      plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, p->a_bufs) > smem_limit) {
+      plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, p->a_bufs, p->a_glob) > smem_limit) {
     release(p);
     return fail(FFTB_ERR_UNSUPPORTED, "plane of this size and precision does not fit in shared memory");
   }
@@ -317,7 +325,7 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   p->T_bytes = (size_t)chunk * p->n[2] * smax_pitch * p->csize;
   e = cudaMalloc(&p->d_T, p->T_bytes);
   if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaMalloc stick scratch failed"); }
-  e = prepare_kernels(p->prec_kernel, p->n[0], p->n[1], p->n[2], p->xmax, p->a_bufs);
+  e = prepare_kernels(p->prec_kernel, p->n[0], p->n[1], p->n[2], p->xmax, p->a_bufs, p->a_glob);
   if (e != cudaSuccess) { release(p); return cuda_fail(e, "kernel attributes"); }
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -327,10 +335,17 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   p->stick_occ = std::max(1, stick_occupancy(p->prec_kernel, p->n[2]));
   p->tiles = 0;  // z stage: one warp per task unless the autotuner prefers persistent CTAs
   for (int i = 0; i < 3; ++i) {
-    const int occ = plane_occupancy(p->prec_kernel, modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs);
+    const int occ = plane_occupancy(p->prec_kernel, modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs, p->a_glob);
     if (occ < 1) { release(p); return fail(FFTB_ERR_UNSUPPORTED, "plane kernel cannot be resident on this device"); }
     p->plane_occ[i] = occ;
     p->plane_ctas[i] = sms * occ;
+  }
+  if (p->a_glob) {
+    // one double-buffered slab-plane block per persistent CTA (the most any mode launches)
+    const int ctas = std::max(p->plane_ctas[0], std::max(p->plane_ctas[1], p->plane_ctas[2]));
+    p->A_bytes = (size_t)ctas * p->a_bufs * p->n[1] * (size_t)(p->xmax + 16) * p->csize;
+    e = cudaMalloc(&p->d_A, p->A_bytes);
+    if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaMalloc slab planes failed"); }
   }
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) { release(p); return cuda_fail(e, "plan synchronise"); }
@@ -448,6 +463,7 @@ static fftb_status enqueue(fftb_plan_s* p, int bands, const void* in, void* out,
   L.T = p->d_T;
   L.V = p->d_V;
   L.a_bufs = p->a_bufs;
+  L.a_glob = p->d_A;
   L.stream = s;
   for (int b0 = 0; b0 < bands; b0 += p->chunk) {
     L.band0 = b0;
@@ -799,7 +815,8 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   std::vector<int> mults;
   const int mi = p->dir == FFTB_R_TO_G ? 1 : p->dir == FFTB_APPLY_LOCAL ? 2 : 0;
   for (int m : {p->plane_occ[mi], p->plane_occ[mi] - 1, 0})
-    if (m >= 0 && std::find(mults.begin(), mults.end(), m) == mults.end()) mults.push_back(m);
+    if ((m > 0 || (m == 0 && !p->a_glob)) && std::find(mults.begin(), mults.end(), m) == mults.end())
+      mults.push_back(m);
   int max_chunk = *std::max_element(chunks.begin(), chunks.end());
   fftb_status st = resize_T(p, max_chunk);
   if (st != FFTB_OK) {

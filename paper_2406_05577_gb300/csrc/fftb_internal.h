@@ -65,6 +65,7 @@ struct Launch {
   const void* V;        // potential (apply)
   int32_t plane_ctas;   // persistent plane-stage CTAs (0: one per plane)
   int32_t a_bufs;       // slab-plane buffers of the plane stage (1 or 2)
+  void* a_glob;         // slab planes in global memory (per CTA), or NULL: shared memory
   cudaStream_t stream;
 };
 
@@ -75,14 +76,16 @@ bool grid_size_supported(int n);
 bool plane_size_supported(int n0, int n1);
 // Dynamic shared memory (bytes) of each kernel for one k geometry.
 size_t stick_smem(int prec, int n2);
-size_t plane_smem(int prec, int n0, int n1, int xmax, int a_bufs);
+// a_glob: the slab planes live in global memory (only the warp scratch and
+// twiddles are in shared memory)
+size_t plane_smem(int prec, int n0, int n1, int xmax, int a_bufs, bool a_glob = false);
 int stick_tile(int prec, int n2);
 // Resident z-stage CTAs per SM (after prepare_kernels).
 int stick_occupancy(int prec, int n2);
 // Raise the dynamic shared-memory limit of the kernels a plan uses.
-cudaError_t prepare_kernels(int prec, int n0, int n1, int n2, int xmax, int a_bufs);
+cudaError_t prepare_kernels(int prec, int n0, int n1, int n2, int xmax, int a_bufs, bool a_glob = false);
 // Resident plane-stage CTAs per SM for this geometry (after prepare_kernels).
-int plane_occupancy(int prec, int mode, int n0, int n1, int xmax, int a_bufs);
+int plane_occupancy(int prec, int mode, int n0, int n1, int xmax, int a_bufs, bool a_glob = false);
 // ctas: persistent z-stage CTAs (0: one warp per task)
 cudaError_t launch_stick(int prec, int mode, const Launch& L, int ctas);
 cudaError_t launch_plane(int prec, int mode, const Launch& L);

@@ -196,9 +196,10 @@ template <int N0, int N1> __host__ __device__ constexpr int plane_scratch() {
              : (32 / Line<N0>::G) * Line<N0>::PITCH;
 }
 
-template <typename T, int N0, int N1> size_t plane_smem_c(int xmax, int a_bufs) {
+template <typename T, int N0, int N1> size_t plane_smem_c(int xmax, int a_bufs, bool ag = false) {
   using C = typename cplx<T>::type;
-  return sizeof(C) * ((size_t)a_bufs * N1 * a_pitch(xmax) + (size_t)PlaneCfg<T>::NW * plane_scratch<N0, N1>() + N0 + N1);
+  return sizeof(C) * ((ag ? 0 : (size_t)a_bufs * N1 * a_pitch(xmax)) + (size_t)PlaneCfg<T>::NW * plane_scratch<N0, N1>() +
+                      N0 + N1);
 }
 
 // packed per-lane slab indices: byte q of w[q / 4] = xi of position q, 255 = empty
@@ -207,7 +208,7 @@ template <int E> struct XiPack {
   __device__ __forceinline__ int get(int q) const { return (int)((w[q >> 2] >> (8 * (q & 3))) & 0xFFu); }
 };
 
-template <typename T, int N0, int N1, int MODE, bool TC = false>
+template <typename T, int N0, int N1, int MODE, bool TC = false, bool AG = false>
 __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k_plane(const Launch L) {
   using C = typename cplx<T>::type;
   using LY = Line<N1>;
@@ -223,10 +224,12 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   const int gy = lane % LY::G, ly = lane / LY::G;
   const int gx = lane % LX::G, lx = lane / LX::G;
   const int abuf = N1 * a_pitch(L.g.xmax);
-  C* A0 = reinterpret_cast<C*>(smem_raw);
   const int nbuf = L.a_bufs;
-  C* scr = A0 + nbuf * abuf + warp * SCR;
-  C* tw0 = A0 + nbuf * abuf + NW * SCR;
+  // slab planes: shared memory, or (AG) this CTA's block of a global buffer
+  C* A0 = AG ? static_cast<C*>(L.a_glob) + (size_t)blockIdx.x * nbuf * abuf : reinterpret_cast<C*>(smem_raw);
+  C* sbase = reinterpret_cast<C*>(smem_raw) + (AG ? 0 : nbuf * abuf);
+  C* scr = sbase + warp * SCR;
+  C* tw0 = sbase + NW * SCR;
   C* tw1 = tw0 + N0;
   {
     const C* t0 = static_cast<const C*>(L.g.tw0);
@@ -468,10 +471,10 @@ template <typename T, bool TC> size_t stick_smem_t(int n2) {
   }
   return 0;
 }
-template <typename T, bool TC> size_t plane_smem_t(int n0, int n1, int xmax, int a_bufs) {
+template <typename T, bool TC> size_t plane_smem_t(int n0, int n1, int xmax, int a_bufs, bool ag) {
   if (n0 != n1) return 0;
   switch (n0) {
-#define C_(N) case N: return plane_smem_c<T, N, N>(xmax, a_bufs);
+#define C_(N) case N: return plane_smem_c<T, N, N>(xmax, a_bufs, ag);
     FFTB_SIZES(C_)
 #undef C_
   }
@@ -496,6 +499,19 @@ template <typename T, bool TC, int N2> cudaError_t go_stick(int mode, const Laun
   return cudaGetLastError();
 }
 template <typename T, bool TC, int N> cudaError_t go_plane(int mode, const Launch& L) {
+  if constexpr (sizeof(T) == 8 && !TC) {
+    if (L.a_glob) {  // double-precision slab planes too large for shared memory
+      const size_t smem = plane_smem_c<T, N, N>(L.g.xmax, L.a_bufs, true);
+      const int nplanes = L.nb * L.g.n2;
+      const dim3 grid(min(L.plane_ctas, nplanes));
+      constexpr int NT = PlaneCfg<T>::NW * 32;
+      if (mode == M_G2R) k_plane<T, N, N, M_G2R, false, true><<<grid, NT, smem, L.stream>>>(L);
+      else if (mode == M_R2G) k_plane<T, N, N, M_R2G, false, true><<<grid, NT, smem, L.stream>>>(L);
+      else k_plane<T, N, N, M_APPLY, false, true><<<grid, NT, smem, L.stream>>>(L);
+      return cudaGetLastError();
+    }
+  }
+  if (L.a_glob) return cudaErrorInvalidValue;
   const size_t smem = plane_smem_c<T, N, N>(L.g.xmax, L.a_bufs);
   const int nplanes = L.nb * L.g.n2;
   const dim3 grid(L.plane_ctas > 0 ? min(L.plane_ctas, nplanes) : nplanes);
@@ -512,7 +528,19 @@ template <typename T, bool TC, int N2> cudaError_t prep_stick() {
     e = cudaFuncSetAttribute(k_stick<T, N2, M_R2G, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   return e;
 }
-template <typename T, bool TC, int N> cudaError_t prep_plane(int xmax, int a_bufs) {
+template <typename T, bool TC, int N> cudaError_t prep_plane(int xmax, int a_bufs, bool ag) {
+  if constexpr (sizeof(T) == 8 && !TC) {
+    if (ag) {
+      const int s = (int)plane_smem_c<T, N, N>(xmax, a_bufs, true);
+      cudaError_t e = cudaFuncSetAttribute(k_plane<T, N, N, M_G2R, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_plane<T, N, N, M_R2G, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_plane<T, N, N, M_APPLY, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+      return e;
+    }
+  }
+  if (ag) return cudaErrorInvalidValue;
   const int s = (int)plane_smem_c<T, N, N>(xmax, a_bufs);
   cudaError_t e = cudaFuncSetAttribute(k_plane<T, N, N, M_G2R, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   if (e == cudaSuccess)
@@ -522,11 +550,21 @@ template <typename T, bool TC, int N> cudaError_t prep_plane(int xmax, int a_buf
   return e;
 }
 
-template <typename T, bool TC, int N> int occ_plane(int mode, int xmax, int a_bufs) {
-  const size_t smem = plane_smem_c<T, N, N>(xmax, a_bufs);
+template <typename T, bool TC, int N> int occ_plane(int mode, int xmax, int a_bufs, bool ag) {
   constexpr int NT = PlaneCfg<T>::NW * 32;
   int nb = 0;
   cudaError_t e;
+  if constexpr (sizeof(T) == 8 && !TC) {
+    if (ag) {
+      const size_t sm = plane_smem_c<T, N, N>(xmax, a_bufs, true);
+      if (mode == M_G2R) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_G2R, false, true>, NT, sm);
+      else if (mode == M_R2G) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_R2G, false, true>, NT, sm);
+      else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_APPLY, false, true>, NT, sm);
+      return e == cudaSuccess ? nb : 0;
+    }
+  }
+  if (ag) return 0;
+  const size_t smem = plane_smem_c<T, N, N>(xmax, a_bufs);
   if (mode == M_G2R) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_G2R, TC>, NT, smem);
   else if (mode == M_R2G) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_R2G, TC>, NT, smem);
   else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_APPLY, TC>, NT, smem);
@@ -547,10 +585,10 @@ template <typename T, bool TC> int stick_occupancy_t(int n2) {
   }
   return 0;
 }
-template <typename T, bool TC> int plane_occupancy_t(int mode, int n0, int n1, int xmax, int a_bufs) {
+template <typename T, bool TC> int plane_occupancy_t(int mode, int n0, int n1, int xmax, int a_bufs, bool ag) {
   if (n0 != n1) return 0;
   switch (n0) {
-#define C_(N) case N: return occ_plane<T, TC, N>(mode, xmax, a_bufs);
+#define C_(N) case N: return occ_plane<T, TC, N>(mode, xmax, a_bufs, ag);
     FFTB_SIZES(C_)
 #undef C_
   }
@@ -574,7 +612,7 @@ template <typename T, bool TC> cudaError_t launch_plane_t(int mode, const Launch
   }
   return cudaErrorInvalidValue;
 }
-template <typename T, bool TC> cudaError_t prepare_t(int n0, int n1, int n2, int xmax, int a_bufs) {
+template <typename T, bool TC> cudaError_t prepare_t(int n0, int n1, int n2, int xmax, int a_bufs, bool ag) {
   cudaError_t e = cudaErrorInvalidValue;
   switch (n2) {
 #define C_(N) case N: e = prep_stick<T, TC, N>(); break;
@@ -583,7 +621,7 @@ template <typename T, bool TC> cudaError_t prepare_t(int n0, int n1, int n2, int
   }
   if (e != cudaSuccess || n0 != n1) return e == cudaSuccess ? cudaErrorInvalidValue : e;
   switch (n0) {
-#define C_(N) case N: return prep_plane<T, TC, N>(xmax, a_bufs);
+#define C_(N) case N: return prep_plane<T, TC, N>(xmax, a_bufs, ag);
     FFTB_SIZES(C_)
 #undef C_
   }
@@ -592,12 +630,12 @@ template <typename T, bool TC> cudaError_t prepare_t(int n0, int n1, int n2, int
 
 #define FFTB_INSTANTIATE(T, TC)                                                    \
   template size_t stick_smem_t<T, TC>(int);                                        \
-  template size_t plane_smem_t<T, TC>(int, int, int, int);                         \
+  template size_t plane_smem_t<T, TC>(int, int, int, int, bool);                   \
   template int stick_tile_t<T, TC>(int);                                           \
   template cudaError_t launch_stick_t<T, TC>(int, const Launch&, int);             \
   template cudaError_t launch_plane_t<T, TC>(int, const Launch&);                  \
-  template cudaError_t prepare_t<T, TC>(int, int, int, int, int);                  \
-  template int plane_occupancy_t<T, TC>(int, int, int, int, int);                  \
+  template cudaError_t prepare_t<T, TC>(int, int, int, int, int, bool);            \
+  template int plane_occupancy_t<T, TC>(int, int, int, int, int, bool);            \
   template int stick_occupancy_t<T, TC>(int);
 
 }  // namespace fftb

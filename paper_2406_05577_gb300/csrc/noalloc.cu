@@ -35,11 +35,11 @@
 #include "geometry.h"
 
 namespace fftb {
-template <typename T, bool TC> size_t plane_smem_t(int, int, int, int);
+template <typename T, bool TC> size_t plane_smem_t(int, int, int, int, bool);
 template <typename T, bool TC> int stick_tile_t(int);
 template <typename T, bool TC> cudaError_t launch_stick_t(int, const Launch&, int);
 template <typename T, bool TC> cudaError_t launch_plane_t(int, const Launch&);
-template <typename T, bool TC> cudaError_t prepare_t(int, int, int, int, int);
+template <typename T, bool TC> cudaError_t prepare_t(int, int, int, int, int, bool);
 }  // namespace fftb
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FFTB_NOALLOC_SCRATCH_BYTES];
@@ -109,8 +109,8 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
     return err(FFTB_ERR_UNSUPPORTED, "one band's stick buffer (" + std::to_string(t_band) +
                                          " bytes) exceeds FFTB_NOALLOC_SCRATCH_BYTES");
   const int chunk = (int)std::min<size_t>((size_t)bands, FFTB_NOALLOC_SCRATCH_BYTES / t_band);
-  const int a_bufs = plane_smem_t<float, false>(n[0], n[1], G.X, 2) <= 227 * 1024 ? 2 : 1;
-  if (plane_smem_t<float, false>(n[0], n[1], G.X, a_bufs) > 227 * 1024)
+  const int a_bufs = plane_smem_t<float, false>(n[0], n[1], G.X, 2, false) <= 227 * 1024 ? 2 : 1;
+  if (plane_smem_t<float, false>(n[0], n[1], G.X, a_bufs, false) > 227 * 1024)
     return err(FFTB_ERR_UNSUPPORTED, "plane does not fit in shared memory");
 
   // tables, packed like a one-k-point plan
@@ -161,7 +161,7 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
   void* tables = nullptr;
   fftb_status st = device_arrays(dev, &scratch, &tables);
   if (st != FFTB_OK) return st;
-  ce = prepare_t<float, false>(n[0], n[1], n[2], G.X, a_bufs);
+  ce = prepare_t<float, false>(n[0], n[1], n[2], G.X, a_bufs, false);
   if (ce != cudaSuccess) return err(FFTB_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(ce));
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);

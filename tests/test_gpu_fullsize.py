@@ -144,3 +144,22 @@ def test_160_g2r_sampled_fp32(F):
     sel = np.random.default_rng(13).choice(len(g), 6, replace=False)
     want = oracle.r2g_points(g[sel], Rr.astype(np.complex128), n)
     assert relerr(o2.cpu().numpy()[sel], want) <= 2e-6
+
+
+def test_160_fp64_roundtrip_sampled(F):
+    """160^3 FP64 (slab planes too large for shared memory: kept in global memory)."""
+    import torch
+    n, r, bands = (160, 160, 160), 40.0, 2
+    plan = F.Plan(n, "roundtrip", "fp64", radius=r, bands=[bands])
+    g = plan.sphere(0)
+    c = fi.complex_gaussian((bands, len(g)), 6)
+    x = torch.from_numpy(c.reshape(-1)).cuda()
+    out = torch.empty_like(x)
+    cube = torch.empty(plan.info["cube_elems"], dtype=torch.complex128, device="cuda")
+    plan.execute(x, out, cube)
+    torch.cuda.synchronize()
+    assert relerr(out.cpu().numpy(), 160 ** 3 * c.reshape(-1)) <= 1e-12
+    R = cube.view(bands, 160, 160, 160).cpu().numpy()
+    pts = sample_points(n, 12, 21)
+    want = oracle.g2r_points(g, c, n, pts)
+    assert relerr(R[:, pts[:, 2], pts[:, 1], pts[:, 0]], want) <= 1e-12
