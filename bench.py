@@ -240,7 +240,7 @@ def make_plan(fftb, w, prec, dev):
     plan = fftb.Plan(w.n, w.direction, prec, **w.plan_kw())
     v_dev = None
     if w.direction == "apply":
-        v_dev = torch.from_numpy(w.potential().astype(np.float32 if prec == "fp32" else np.float64)).to(dev)
+        v_dev = torch.from_numpy(w.potential().astype(np.float64 if prec == "fp64" else np.float32)).to(dev)
         plan.set_potential(v_dev)
     if w.tune:
         plan.autotune(3)
