@@ -95,6 +95,8 @@ typedef struct {
   int32_t chunk_bands;     /* bands per launch chunk                                */
   int32_t kernels_per_execute; /* kernel launches one fftb_execute issues           */
   int32_t complex_bytes;   /* 8 (FP32, MIXED_TC) or 16 (FP64)                       */
+  int32_t stick_ctas;      /* z-stage CTAs per launch (0: one warp per stick group)  */
+  int32_t plane_ctas;      /* persistent plane-stage CTAs of this direction (0: one per plane) */
 } fftb_plan_info_t;
 
 /* Builds the spheres, stick/slab tables and twiddles on the host, uploads

@@ -333,7 +333,7 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   const int modes[3] = {M_G2R, M_R2G, M_APPLY};
   p->sms = sms;
   p->stick_occ = std::max(1, stick_occupancy(p->prec_kernel, p->n[2]));
-  p->tiles = 0;  // z stage: one warp per task unless the autotuner prefers persistent CTAs
+  p->tiles = sms * p->stick_occ;  // z stage: one wave of persistent CTAs (the autotuner may pick one warp per task pair)
   for (int i = 0; i < 3; ++i) {
     const int occ = plane_occupancy(p->prec_kernel, modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs, p->a_glob);
     if (occ < 1) { release(p); return fail(FFTB_ERR_UNSUPPORTED, "plane kernel cannot be resident on this device"); }
@@ -389,6 +389,8 @@ FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) 
   const int nchunks = p->total_bands > 0 ? (p->total_bands + p->chunk - 1) / p->chunk : 0;
   info->kernels_per_execute = nchunks * kernels_per_chunk(p->dir);
   info->complex_bytes = p->csize;
+  info->stick_ctas = p->tiles;
+  info->plane_ctas = p->plane_ctas[p->dir == FFTB_R_TO_G ? 1 : p->dir == FFTB_APPLY_LOCAL ? 2 : 0];
   return FFTB_OK;
 }
 

@@ -64,20 +64,18 @@ __global__ void __launch_bounds__(STICK_NW * 32) k_stick(const Launch L) {
   auto zsigned = [](int z) { return z < N2 - N2 / 2 ? z : z - N2; };
   const int smax = L.g.smax;
 
-  // tasks = (band, group of WZ sticks); each warp takes a contiguous range, so
-  // consecutive tasks usually share the band and its tables
+  // tasks = (band, group of WZ sticks), dealt to warps with a grid stride so
+  // that the warps active at any moment work on neighbouring stick groups
+  // (their stick-row stores meet in L2)
   const int gpb = (smax + WZ - 1) / WZ;
   const int ntask = L.nb * gpb;
   const int nwarps = gridDim.x * STICK_NW;
-  const int per = (ntask + nwarps - 1) / nwarps;
-  const int t0 = (blockIdx.x * STICK_NW + warp) * per;
-  const int t1 = min(ntask, t0 + per);
+  const int t0 = blockIdx.x * STICK_NW + warp;
+  const int t1 = ntask;
   int cur_bl = -1, S = 0, stick_base = 0;
   bool canon = false;
   int64_t sph = 0;
-#pragma unroll 1
-  for (int t = t0; t < t1; ++t) {
-    const int bl = t / gpb, s0 = (t - bl * gpb) * WZ;
+  auto band_of = [&](int bl) {
     if (bl != cur_bl) {
       cur_bl = bl;
       const BandInfo bi = L.g.band[L.band0 + bl];
@@ -86,69 +84,77 @@ __global__ void __launch_bounds__(STICK_NW * 32) k_stick(const Launch L) {
       canon = bi.ki.flags & KF_CANONICAL_STICKS;
       sph = bi.sph;
     }
-    if (s0 >= S) continue;  // uniform across the warp
-    const int nl = min(WZ, S - s0);
-    const int s = s0 + (l < nl ? l : 0);
-    const int4 si = L.g.stick_info[stick_base + s];  // first entry, end entry, list position, signed gz
-    const int len = si.y - si.x;
-    C* Tb = static_cast<C*>(L.T) + (size_t)bl * N2 * smax + s;
-    C v[EZ];
-
+  };
+  struct Task {
+    int bl, s0, nl;
+    int4 si;  // first entry, end entry, list position, signed gz of this lane's stick
+    int64_t sph;
+    bool live, canon;
+  };
+  auto meta = [&](int t) {
+    Task k{};
+    if (t >= ntask) return k;  // past the last task: dead, no table reads
+    k.bl = t / gpb;
+    k.s0 = (t - k.bl * gpb) * WZ;
+    band_of(k.bl);
+    k.live = k.s0 < S;
+    k.canon = canon;
+    k.sph = sph;
+    k.nl = k.live ? min(WZ, S - k.s0) : 0;
+    const int s = k.s0 + (l < k.nl ? l : 0);
+    k.si = k.live ? L.g.stick_info[stick_base + s] : make_int4(0, 0, 0, 0);
+    return k;
+  };
+  // global loads of a task into registers (canonical G->r or any r->G)
+  auto load = [&](const Task& k, C (&v)[EZ]) {
     if constexpr (MODE == M_G2R) {
-      const C* in = static_cast<const C*>(L.sph_in) + sph;
-      if (canon) {
+      const C* in = static_cast<const C*>(L.sph_in) + k.sph;
+      const int len = k.si.y - k.si.x;
 #pragma unroll
-        for (int m = 0; m < EZ / LZ::R0; ++m)
+      for (int m = 0; m < EZ / LZ::R0; ++m)
 #pragma unroll
-          for (int j = 0; j < LZ::R0; ++j) {
-            const int d = zsigned(LZ::first_pos(g, m, j)) - si.w;
-            v[m * LZ::R0 + j] = (unsigned)d < (unsigned)len ? in[si.z + d] : czero<C>();
-          }
-      } else {
-        const int ea = __shfl_sync(0xffffffffu, si.x, 0);
-        const int eb = __shfl_sync(0xffffffffu, si.y, (nl - 1) * LZ::G);
-        for (int q = lane; q < WZ * LZ::PITCH; q += 32) scr[q] = czero<C>();
-        __syncwarp();
-        for (int e = ea + lane; e < eb; e += 32) {
-          const uint32_t zs = (uint32_t)L.g.ent_zs[e];
-          scr[((int)(zs & 0xFFFFFFu) - s0) * LZ::PITCH + wpad((int)(zs >> 24))] = in[L.g.ent_pos[e]];
+        for (int j = 0; j < LZ::R0; ++j) {
+          const int d = zsigned(LZ::first_pos(g, m, j)) - k.si.w;
+          v[m * LZ::R0 + j] = (unsigned)d < (unsigned)len ? in[k.si.z + d] : czero<C>();
         }
-        __syncwarp();
+    } else {
+      const C* Tb = static_cast<const C*>(L.T) + (size_t)k.bl * N2 * smax + k.s0 + (l < k.nl ? l : 0);
 #pragma unroll
-        for (int m = 0; m < EZ / LZ::R0; ++m)
+      for (int m = 0; m < EZ / LZ::R0; ++m)
 #pragma unroll
-          for (int j = 0; j < LZ::R0; ++j) v[m * LZ::R0 + j] = row[wpad(LZ::first_pos(g, m, j))];
-        __syncwarp();
-      }
+        for (int j = 0; j < LZ::R0; ++j) v[m * LZ::R0 + j] = Tb[(size_t)LZ::first_pos(g, m, j) * smax];
+    }
+  };
+  // transform and write a task whose inputs are in v
+  auto finish = [&](const Task& k, C (&v)[EZ]) {
+    if constexpr (MODE == M_G2R) {
       if constexpr (TC) LZ::template run_tc<+1>(v, g, row, scr, tw, tc, tcw);
       else LZ::template run<+1>(v, g, row, tw, tc);
-      if (l < nl) {
+      if (l < k.nl) {
+        C* Tb = static_cast<C*>(L.T) + (size_t)k.bl * N2 * smax + k.s0 + l;
 #pragma unroll
         for (int m = 0; m < EZ / LZ::RL; ++m)
 #pragma unroll
           for (int j = 0; j < LZ::RL; ++j) Tb[(size_t)LZ::last_pos(g, m, j) * smax] = v[m * LZ::RL + j];
       }
     } else {
-#pragma unroll
-      for (int m = 0; m < EZ / LZ::R0; ++m)
-#pragma unroll
-        for (int j = 0; j < LZ::R0; ++j) v[m * LZ::R0 + j] = Tb[(size_t)LZ::first_pos(g, m, j) * smax];
       if constexpr (TC) LZ::template run_tc<-1>(v, g, row, scr, tw, tc, tcw);
       else LZ::template run<-1>(v, g, row, tw, tc);
-      C* out = static_cast<C*>(L.sph_out) + sph;
-      if (canon) {
-        if (l < nl) {
+      C* out = static_cast<C*>(L.sph_out) + k.sph;
+      if (k.canon) {
+        if (l < k.nl) {
+          const int len = k.si.y - k.si.x;
 #pragma unroll
           for (int m = 0; m < EZ / LZ::RL; ++m)
 #pragma unroll
             for (int j = 0; j < LZ::RL; ++j) {
-              const int d = zsigned(LZ::last_pos(g, m, j)) - si.w;
-              if ((unsigned)d < (unsigned)len) out[si.z + d] = v[m * LZ::RL + j];
+              const int d = zsigned(LZ::last_pos(g, m, j)) - k.si.w;
+              if ((unsigned)d < (unsigned)len) out[k.si.z + d] = v[m * LZ::RL + j];
             }
         }
       } else {
-        const int ea = __shfl_sync(0xffffffffu, si.x, 0);
-        const int eb = __shfl_sync(0xffffffffu, si.y, (nl - 1) * LZ::G);
+        const int ea = __shfl_sync(0xffffffffu, k.si.x, 0);
+        const int eb = __shfl_sync(0xffffffffu, k.si.y, (k.nl - 1) * LZ::G);
 #pragma unroll
         for (int m = 0; m < EZ / LZ::RL; ++m)
 #pragma unroll
@@ -156,10 +162,50 @@ __global__ void __launch_bounds__(STICK_NW * 32) k_stick(const Launch L) {
         __syncwarp();
         for (int e = ea + lane; e < eb; e += 32) {
           const uint32_t zs = (uint32_t)L.g.ent_zs[e];
-          out[L.g.ent_pos[e]] = scr[((int)(zs & 0xFFFFFFu) - s0) * LZ::PITCH + wpad((int)(zs >> 24))];
+          out[L.g.ent_pos[e]] = scr[((int)(zs & 0xFFFFFFu) - k.s0) * LZ::PITCH + wpad((int)(zs >> 24))];
         }
         __syncwarp();
       }
+    }
+  };
+  // a non-canonical G->r task gathers its entries through the warp scratch
+  auto scatter_load = [&](const Task& k, C (&v)[EZ]) {
+    const C* in = static_cast<const C*>(L.sph_in) + k.sph;
+    const int ea = __shfl_sync(0xffffffffu, k.si.x, 0);
+    const int eb = __shfl_sync(0xffffffffu, k.si.y, (k.nl - 1) * LZ::G);
+    for (int q = lane; q < WZ * LZ::PITCH; q += 32) scr[q] = czero<C>();
+    __syncwarp();
+    for (int e = ea + lane; e < eb; e += 32) {
+      const uint32_t zs = (uint32_t)L.g.ent_zs[e];
+      scr[((int)(zs & 0xFFFFFFu) - k.s0) * LZ::PITCH + wpad((int)(zs >> 24))] = in[L.g.ent_pos[e]];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < EZ / LZ::R0; ++m)
+#pragma unroll
+      for (int j = 0; j < LZ::R0; ++j) v[m * LZ::R0 + j] = row[wpad(LZ::first_pos(g, m, j))];
+    __syncwarp();
+  };
+
+  // two-deep software pipeline: the next task's records and inputs are in
+  // flight while the current task is transformed and written
+  if (t0 >= t1) return;
+  C va[EZ], vb[EZ];
+  Task ka = meta(t0), kb{};
+  if (ka.live && (MODE == M_R2G || ka.canon)) load(ka, va);
+#pragma unroll 1
+  for (int t = t0; t < t1; t += 2 * nwarps) {
+    kb = meta(t + nwarps);
+    if (kb.live && (MODE == M_R2G || kb.canon)) load(kb, vb);
+    if (ka.live) {
+      if (!(MODE == M_R2G || ka.canon)) scatter_load(ka, va);
+      finish(ka, va);
+    }
+    ka = meta(t + 2 * nwarps);
+    if (ka.live && (MODE == M_R2G || ka.canon)) load(ka, va);
+    if (kb.live) {
+      if (!(MODE == M_R2G || kb.canon)) scatter_load(kb, vb);
+      finish(kb, vb);
     }
   }
 }

@@ -51,6 +51,8 @@ class fftb_plan_info_t(ctypes.Structure):
         ("chunk_bands", ctypes.c_int32),
         ("kernels_per_execute", ctypes.c_int32),
         ("complex_bytes", ctypes.c_int32),
+        ("stick_ctas", ctypes.c_int32),
+        ("plane_ctas", ctypes.c_int32),
     ]
 
 
