@@ -47,7 +47,7 @@ class Workload:
             self.n, self.radius, self.kshift, self.bands = (64, 64, 64), 16.0, None, [64]
             self.direction, self.desc = "roundtrip", \
                 "64^3 grid, |G|<=16 (17077 G), 64 bands, G->r->G round trip, cube kept in HBM"
-            self.envelope, self.seed, self.graph, self.tune = 8.0, 2, False, False
+            self.envelope, self.seed, self.graph, self.tune = 8.0, 2, False, True
         elif name == "sphere96_multik":
             self.n, self.radius = (96, 96, 96), 24.0
             self.kshift = fi.kshifts(8, 3)
@@ -61,7 +61,7 @@ class Workload:
             self.direction = "apply"
             self.desc = ("128^3 grid, |G|<=32 (137065 G), 256 bands, psi_G -> V(r) psi(r) -> G sphere, "
                          "V = 32 Gaussians of width 4, cube never stored")
-            self.envelope, self.seed, self.graph, self.tune = None, 4, False, False
+            self.envelope, self.seed, self.graph, self.tune = None, 4, False, True
         elif name == "sphere160_large":
             self.n, self.radius, self.kshift, self.bands = (160, 160, 160), 40.0, None, [512]
             self.direction = "roundtrip"
@@ -104,7 +104,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fft_core.cuh", "line_fft.cuh", "kernels.cuh"):
+    for f in ("fft_core.cuh", "line_fft.cuh", "kernels.cuh", "async_copy.cuh", "k_f32_pf.cu"):
         h.update(open(os.path.join(ROOT, "paper_2406_05577_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -97,6 +97,10 @@ typedef struct {
   int32_t complex_bytes;   /* 8 (FP32, MIXED_TC) or 16 (FP64)                       */
   int32_t stick_ctas;      /* z-stage CTAs per launch (0: one warp per stick group)  */
   int32_t plane_ctas;      /* persistent plane-stage CTAs of this direction (0: one per plane) */
+  int32_t prefetch;        /* plane stages that prefetch their inputs with bulk asynchronous
+                              copies: bit 0 G->r, bit 1 r->G, bit 2 apply               */
+  int32_t slab_buffers;    /* slab planes per plane-stage CTA in shared memory (1 or 2;
+                              0: kept in global memory)                                 */
 } fftb_plan_info_t;
 
 /* Builds the spheres, stick/slab tables and twiddles on the host, uploads
@@ -168,8 +172,9 @@ fftb_status fftb_plan_stage_times(fftb_plan plan, double* ms, int64_t* launches)
  * kernels then go into the caller's graph). Disabled by default. */
 fftb_status fftb_plan_set_graph(fftb_plan plan, int32_t enable);
 
-/* Autotuner: times the candidate schedules of this plan -- bands per launch
- * chunk and persistent CTAs of the plane stage -- with `trials` timed
+/* Autotuner: times the candidate schedules of this plan -- first the kernel
+ * variant (slab-plane buffers, prefetch level), then bands per launch chunk,
+ * persistent CTAs of the plane stage and z-stage CTAs -- with `trials` timed
  * executes each on device buffers it allocates and frees (at most 4 GiB;
  * larger batches are tuned on a prefix of the bands), keeps the fastest and
  * reallocates the plan's scratch to fit. If the environment variable
@@ -177,6 +182,46 @@ fftb_status fftb_plan_set_graph(fftb_plan plan, int32_t enable);
  * keyed by grid, sphere sizes, bands, direction, precision and device.
  * Synchronises the device. */
 fftb_status fftb_plan_autotune(fftb_plan plan, int32_t trials);
+
+/* Bulk-copy prefetch in the plane stage (FP32 plans). A prefetching plane
+ * kernel receives each plane's stick row (G->r, apply) or each warp's next
+ * cube rows (r->G; cube buffers 16-byte aligned, grids of 64 and up)
+ * through cp.async.bulk copies completed on shared-memory mbarriers, issued
+ * one step ahead of their use; the other kernels load with ordinary
+ * instructions. level 0: never; 1 (default): where the staging buffers fit
+ * in shared memory without lowering the resident CTAs per SM; 2: wherever
+ * they fit. Changing the level resets the persistent plane CTAs of the
+ * affected stages to one full wave; fftb_plan_autotune also tries the
+ * levels. fftb_plan_info_t.prefetch says which stages prefetch.
+ * Errors: INVALID_ARG for a level outside 0..2. */
+fftb_status fftb_plan_set_prefetch(fftb_plan plan, int32_t level);
+
+/* Slab-plane buffers of the plane stage: 2 (default where it fits) lets a
+ * CTA start the next plane's y stage while slower warps finish the current
+ * plane's x stage, at twice the shared memory; 1 halves that memory (more
+ * resident CTAs per SM on large grids) for a second block barrier per plane.
+ * Resets the persistent plane CTAs to one full wave; fftb_plan_autotune also
+ * tries both. Errors: INVALID_ARG for a count other than 1 or 2;
+ * UNSUPPORTED when 2 do not fit or the plan keeps its slab planes in global
+ * memory (FP64 on the largest grids). */
+fftb_status fftb_plan_set_slab_buffers(fftb_plan plan, int32_t nbuf);
+
+/* Device status. Every wait of a plane kernel on an asynchronous copy gives
+ * up after one second; the CTA then lets its copies in flight land, leaves,
+ * and sets the plan's status word (mapped host memory), so the context stays
+ * usable but the result is invalid. fftb_plan_check synchronises the device,
+ * returns FFTB_ERR_DEVICE_TIMEOUT if the word is set since the previous check
+ * (and clears it), else FFTB_OK. fftb_execute_host checks it after its own
+ * synchronisation. */
+fftb_status fftb_plan_check(fftb_plan plan);
+
+/* Test hook for the bounded waits: with FFTB_INJECT_SKIP_FIRST_PREFETCH the
+ * first prefetch of CTA 0 (warp 0 in r->G) is not issued in each prefetching
+ * plane launch, so its wait runs out (about one second, twice: the wait, then
+ * the exit's wait for copies in flight) and the status word is set. 0 turns
+ * injection off. Unknown bits: FFTB_ERR_INVALID_ARG. */
+#define FFTB_INJECT_SKIP_FIRST_PREFETCH 1
+fftb_status fftb_plan_inject(fftb_plan plan, int32_t flags);
 
 /* Kernel launches this plan has issued so far (all executes). */
 int64_t fftb_plan_launches(fftb_plan plan);

@@ -86,6 +86,7 @@ struct fftb_plan_s {
   int32_t total_bands = 0;
   int64_t sphere_elems = 0, cube_elems = 0;
   int32_t smax = 0, xmax = 0, tiles = 0, chunk = 1;
+  int32_t tpitch = 2;  // stick-row pitch of T: smax rounded up to even
   int device = 0;
   int32_t plane_ctas[3] = {0, 0, 0};  // persistent CTAs: G->r, r->G, apply
   int32_t a_bufs = 2;                 // slab-plane buffers of the plane stage
@@ -115,6 +116,16 @@ struct fftb_plan_s {
   int sms = 0;
   int plane_occ[3] = {0, 0, 0};  // resident plane CTAs per SM: G->r, r->G, apply
   int stick_occ = 1;             // resident z-stage CTAs per SM
+  // bulk-copy prefetch in the plane stage (FP32), per mode: kernels exist and
+  // fit in shared memory (pf_fit), their resident CTAs per SM (pf_occ), and
+  // the level asked for (fftb_plan_set_prefetch: 0 off, 1 where no resident
+  // CTA is lost, 2 wherever it fits)
+  bool pf_fit[3] = {false, false, false};
+  int pf_occ[3] = {0, 0, 0};
+  int pf_level = 1;
+  int32_t inject = 0;              // fftb_plan_inject
+  int32_t* h_status = nullptr;     // status word in mapped pinned host memory
+  int32_t* d_status = nullptr;     // its device address
   // per-kernel timing (fftb_plan_set_timing)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -124,6 +135,46 @@ struct fftb_plan_s {
 };
 
 namespace {
+
+// the plane stage of mode index i (G->r, r->G, apply) prefetches
+bool pf_active(const fftb_plan_s* p, int i) {
+  if (!p->pf_fit[i] || p->pf_level == 0) return false;
+  return p->pf_level == 2 || p->pf_occ[i] >= p->plane_occ[i];
+}
+// resident plane CTAs per SM of the kernel mode index i uses
+int occ_in_use(const fftb_plan_s* p, int i) { return pf_active(p, i) ? p->pf_occ[i] : p->plane_occ[i]; }
+
+constexpr size_t kSmemLimit = 227 * 1024;
+
+// For the plan's slab-plane buffer count: kernel shared-memory limits,
+// resident CTAs per SM of every plane kernel (plain and prefetching), and
+// persistent plane CTAs of one full wave.
+fftb_status configure_planes(fftb_plan_s* p) {
+  cudaError_t e = prepare_kernels(p->prec_kernel, p->n[0], p->n[1], p->n[2], p->xmax, p->a_bufs, p->a_glob);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+  const int modes[3] = {M_G2R, M_R2G, M_APPLY};
+  for (int i = 0; i < 3; ++i) {
+    const int occ = plane_occupancy(p->prec_kernel, modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs, p->a_glob);
+    if (occ < 1) return fail(FFTB_ERR_UNSUPPORTED, "plane kernel cannot be resident on this device");
+    p->plane_occ[i] = occ;
+    p->pf_fit[i] = false;
+    p->pf_occ[i] = 0;
+  }
+  if (p->prec_kernel == P_F32 && !p->a_glob) {
+    // prefetching plane kernels where their staging fits in shared memory
+    for (int i = 0; i < 3; ++i) {
+      if (!plane_pf_supported(modes[i], p->n[0], p->n[1]) ||
+          plane_pf_smem(modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs, p->tpitch) > kSmemLimit)
+        continue;
+      e = prepare_plane_pf(modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs, p->tpitch);
+      if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+      p->pf_occ[i] = plane_pf_occupancy(modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs, p->tpitch);
+      p->pf_fit[i] = p->pf_occ[i] >= 1;
+    }
+  }
+  for (int i = 0; i < 3; ++i) p->plane_ctas[i] = p->sms * occ_in_use(p, i);
+  return FFTB_OK;
+}
 
 bool valid_direction(int d) { return d == FFTB_G_TO_R || d == FFTB_R_TO_G || d == FFTB_ROUNDTRIP || d == FFTB_APPLY_LOCAL; }
 
@@ -150,6 +201,7 @@ void release(fftb_plan_s* p) {
   if (p->d_stage_cube) cudaFree(p->d_stage_cube);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->h_status) cudaFreeHost(p->h_status);
   delete p;
 }
 
@@ -216,7 +268,7 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   }
   if (p->total_bands > 65535) { release(p); return fail(FFTB_ERR_UNSUPPORTED, "more than 65535 bands in one plan"); }
 
-  const size_t smem_limit = 227 * 1024;
+  const size_t smem_limit = kSmemLimit;
   if (plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, 2) > smem_limit) p->a_bufs = 1;
   if (plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, p->a_bufs) > smem_limit && p->prec_kernel == P_F64) {
     p->a_bufs = 2;  // slab planes in global memory, double buffered
@@ -229,7 +281,8 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   }
   const int ts = stick_tile(p->prec_kernel, p->n[2]);
   p->tiles = p->smax > 0 ? (p->smax + ts - 1) / ts : 1;
-  const int32_t smax_pitch = std::max<int32_t>(p->smax, 1);
+  const int32_t smax_pitch = (std::max<int32_t>(p->smax, 1) + 1) & ~1;
+  p->tpitch = smax_pitch;
 
   // band chunk: keep the stick buffer near 48 MB, or as requested
   const size_t t_band = (size_t)p->n[2] * smax_pitch * p->csize;
@@ -325,21 +378,31 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   p->T_bytes = (size_t)chunk * p->n[2] * smax_pitch * p->csize;
   e = cudaMalloc(&p->d_T, p->T_bytes);
   if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaMalloc stick scratch failed"); }
-  e = prepare_kernels(p->prec_kernel, p->n[0], p->n[1], p->n[2], p->xmax, p->a_bufs, p->a_glob);
-  if (e != cudaSuccess) { release(p); return cuda_fail(e, "kernel attributes"); }
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
   if (e != cudaSuccess) { release(p); return cuda_fail(e, "device attribute"); }
-  const int modes[3] = {M_G2R, M_R2G, M_APPLY};
   p->sms = sms;
+  fftb_status cst = configure_planes(p);
+  if (cst != FFTB_OK) { release(p); return cst; }
+  if (p->a_bufs == 2 && !p->a_glob) {
+    // one slab buffer when that makes more CTAs resident (large grids)
+    const int occ2 = occ_in_use(p, 0) + occ_in_use(p, 1) + occ_in_use(p, 2);
+    p->a_bufs = 1;
+    cst = configure_planes(p);
+    if (cst != FFTB_OK) { release(p); return cst; }
+    if (occ_in_use(p, 0) + occ_in_use(p, 1) + occ_in_use(p, 2) <= occ2) {
+      p->a_bufs = 2;
+      cst = configure_planes(p);
+      if (cst != FFTB_OK) { release(p); return cst; }
+    }
+  }
   p->stick_occ = std::max(1, stick_occupancy(p->prec_kernel, p->n[2]));
   p->tiles = sms * p->stick_occ;  // z stage: one wave of persistent CTAs (the autotuner may pick one warp per task pair)
-  for (int i = 0; i < 3; ++i) {
-    const int occ = plane_occupancy(p->prec_kernel, modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs, p->a_glob);
-    if (occ < 1) { release(p); return fail(FFTB_ERR_UNSUPPORTED, "plane kernel cannot be resident on this device"); }
-    p->plane_occ[i] = occ;
-    p->plane_ctas[i] = sms * occ;
-  }
+  e = cudaHostAlloc(reinterpret_cast<void**>(&p->h_status), sizeof(int32_t), cudaHostAllocMapped);
+  if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaHostAlloc status word failed"); }
+  *p->h_status = 0;
+  e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&p->d_status), p->h_status, 0);
+  if (e != cudaSuccess) { release(p); return cuda_fail(e, "status word device address"); }
   if (p->a_glob) {
     // one double-buffered slab-plane block per persistent CTA (the most any mode launches)
     const int ctas = std::max(p->plane_ctas[0], std::max(p->plane_ctas[1], p->plane_ctas[2]));
@@ -391,6 +454,10 @@ FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) 
   info->complex_bytes = p->csize;
   info->stick_ctas = p->tiles;
   info->plane_ctas = p->plane_ctas[p->dir == FFTB_R_TO_G ? 1 : p->dir == FFTB_APPLY_LOCAL ? 2 : 0];
+  info->prefetch = 0;
+  for (int i = 0; i < 3; ++i)
+    if (pf_active(p, i)) info->prefetch |= 1 << i;
+  info->slab_buffers = p->a_glob ? 0 : p->a_bufs;
   return FFTB_OK;
 }
 
@@ -431,20 +498,24 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
     case K_PLANE_G2R: {
       Launch Lp = L;
       Lp.plane_ctas = p->plane_ctas[0];
-      e = launch_plane(pk, M_G2R, Lp);
+      Lp.pf = pf_active(p, 0);
+      e = Lp.pf ? launch_plane_pf(M_G2R, Lp) : launch_plane(pk, M_G2R, Lp);
       break;
     }
     case K_PLANE_R2G: {
       Launch Lp = L;
       Lp.plane_ctas = p->plane_ctas[1];
-      e = launch_plane(pk, M_R2G, Lp);
+      // bulk copies read the cube from 16-byte aligned rows
+      Lp.pf = pf_active(p, 1) && (reinterpret_cast<uintptr_t>(L.cube_in) % 16) == 0;
+      e = Lp.pf ? launch_plane_pf(M_R2G, Lp) : launch_plane(pk, M_R2G, Lp);
       break;
     }
     case K_STICK_R2G: e = launch_stick(pk, M_R2G, L, p->tiles); break;
     default: {
       Launch Lp = L;
       Lp.plane_ctas = p->plane_ctas[2];
-      e = launch_plane(pk, M_APPLY, Lp);
+      Lp.pf = pf_active(p, 2);
+      e = Lp.pf ? launch_plane_pf(M_APPLY, Lp) : launch_plane(pk, M_APPLY, Lp);
       break;
     }
   }
@@ -466,6 +537,8 @@ static fftb_status enqueue(fftb_plan_s* p, int bands, const void* in, void* out,
   L.V = p->d_V;
   L.a_bufs = p->a_bufs;
   L.a_glob = p->d_A;
+  L.inject = p->inject;
+  L.status = p->d_status;
   L.stream = s;
   for (int b0 = 0; b0 < bands; b0 += p->chunk) {
     L.band0 = b0;
@@ -605,6 +678,74 @@ FFTB_EXPORT fftb_status fftb_execute_host(fftb_plan p, const void* in_host, void
   if (e != cudaSuccess) return cuda_fail(e, "copy out");
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
+  if (*reinterpret_cast<volatile int32_t*>(p->h_status)) {
+    *p->h_status = 0;
+    return fail(FFTB_ERR_DEVICE_TIMEOUT, "a plane-stage wait for an asynchronous copy ran out; the result is invalid");
+  }
+  return FFTB_OK;
+}
+
+FFTB_EXPORT fftb_status fftb_plan_check(fftb_plan p) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "device synchronise");
+  if (*reinterpret_cast<volatile int32_t*>(p->h_status)) {
+    *p->h_status = 0;
+    return fail(FFTB_ERR_DEVICE_TIMEOUT, "a plane-stage wait for an asynchronous copy ran out; results since the "
+                                         "previous check are invalid");
+  }
+  return FFTB_OK;
+}
+
+FFTB_EXPORT fftb_status fftb_plan_set_prefetch(fftb_plan p, int32_t level) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (level < 0 || level > 2) return fail(FFTB_ERR_INVALID_ARG, "prefetch level must be 0, 1 or 2");
+  for (int i = 0; i < 3; ++i) {
+    const bool was = pf_active(p, i);
+    const int old = p->pf_level;
+    p->pf_level = level;
+    const bool now = pf_active(p, i);
+    p->pf_level = old;
+    if (was != now) p->plane_ctas[i] = p->sms * (now ? p->pf_occ[i] : p->plane_occ[i]);
+  }
+  if (p->pf_level != level && p->gexec) {
+    cudaGraphExecDestroy(p->gexec);  // recorded with the other kernels
+    p->gexec = nullptr;
+  }
+  p->pf_level = level;
+  return FFTB_OK;
+}
+
+FFTB_EXPORT fftb_status fftb_plan_set_slab_buffers(fftb_plan p, int32_t nbuf) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (nbuf != 1 && nbuf != 2) return fail(FFTB_ERR_INVALID_ARG, "slab buffers must be 1 or 2");
+  if (p->a_glob) return fail(FFTB_ERR_UNSUPPORTED, "this plan keeps its slab planes in global memory");
+  if (plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, nbuf) > kSmemLimit)
+    return fail(FFTB_ERR_UNSUPPORTED, "two slab planes do not fit in shared memory for this plan");
+  if (nbuf == p->a_bufs) return FFTB_OK;
+  const int old = p->a_bufs;
+  p->a_bufs = nbuf;
+  fftb_status st = configure_planes(p);
+  if (st != FFTB_OK) {
+    p->a_bufs = old;
+    configure_planes(p);
+    return st;
+  }
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  return FFTB_OK;
+}
+
+FFTB_EXPORT fftb_status fftb_plan_inject(fftb_plan p, int32_t flags) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (flags & ~FFTB_INJECT_SKIP_FIRST_PREFETCH) return fail(FFTB_ERR_INVALID_ARG, "unknown injection flag");
+  if (p->inject != flags && p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  p->inject = flags;
   return FFTB_OK;
 }
 
@@ -707,7 +848,23 @@ std::string tune_key(const fftb_plan_s* p) {
   return out;
 }
 
-bool tune_cache_lookup(const std::string& key, int* chunk, int ctas[3], int* tiles) {
+// One autotuner candidate: everything it may change on a plan.
+struct TuneChoice {
+  int chunk = 1, tiles = 0, level = 1, a_bufs = 2;
+  int ctas[3] = {0, 0, 0};  // -1: one full wave of the kernel in use
+};
+
+TuneChoice current_choice(const fftb_plan_s* p) {
+  TuneChoice c;
+  c.chunk = p->chunk;
+  c.tiles = p->tiles;
+  c.level = p->pf_level;
+  c.a_bufs = p->a_bufs;
+  for (int i = 0; i < 3; ++i) c.ctas[i] = p->plane_ctas[i];
+  return c;
+}
+
+bool tune_cache_lookup(const std::string& key, TuneChoice* out) {
   const char* path = std::getenv("FFTB_TUNE_CACHE");
   if (!path || !*path) return false;
   std::ifstream f(path);
@@ -716,34 +873,54 @@ bool tune_cache_lookup(const std::string& key, int* chunk, int ctas[3], int* til
   while (std::getline(f, line)) {
     std::istringstream ls(line);
     std::string k;
-    int c, a, b, d, t;
-    if ((ls >> k >> c >> a >> b >> d >> t) && k == key) {
-      *chunk = c;
-      ctas[0] = a;
-      ctas[1] = b;
-      ctas[2] = d;
-      *tiles = t;
+    TuneChoice c;
+    if ((ls >> k >> c.chunk >> c.ctas[0] >> c.ctas[1] >> c.ctas[2] >> c.tiles >> c.level >> c.a_bufs) && k == key &&
+        c.chunk >= 1 && c.level >= 0 && c.level <= 2 && (c.a_bufs == 1 || c.a_bufs == 2)) {
+      *out = c;
       found = true;  // the last entry wins
     }
   }
   return found;
 }
 
-void tune_cache_store(const std::string& key, int chunk, const int ctas[3], int tiles) {
+void tune_cache_store(const std::string& key, const TuneChoice& c) {
   const char* path = std::getenv("FFTB_TUNE_CACHE");
   if (!path || !*path) return;
   std::ofstream f(path, std::ios::app);
-  f << key << " " << chunk << " " << ctas[0] << " " << ctas[1] << " " << ctas[2] << " " << tiles << "\n";
+  f << key << " " << c.chunk << " " << c.ctas[0] << " " << c.ctas[1] << " " << c.ctas[2] << " " << c.tiles << " "
+    << c.level << " " << c.a_bufs << "\n";
 }
 
 fftb_status resize_T(fftb_plan_s* p, int chunk) {
-  const size_t need = (size_t)chunk * p->n[2] * std::max<int32_t>(p->smax, 1) * p->csize;
+  const size_t need = (size_t)chunk * p->n[2] * p->tpitch * p->csize;
   if (need <= p->T_bytes) return FFTB_OK;
   if (p->d_T) cudaFree(p->d_T);
   p->d_T = nullptr;
   p->T_bytes = 0;
   if (cudaMalloc(&p->d_T, need) != cudaSuccess) return fail(FFTB_ERR_ALLOC, "cudaMalloc stick scratch failed");
   p->T_bytes = need;
+  return FFTB_OK;
+}
+
+// Puts a candidate on the plan (slab buffers first: they change the
+// resident CTAs per SM).
+fftb_status apply_choice(fftb_plan_s* p, const TuneChoice& c) {
+  if (c.a_bufs != p->a_bufs && !p->a_glob) {
+    const int old = p->a_bufs;
+    p->a_bufs = c.a_bufs;
+    fftb_status st = configure_planes(p);
+    if (st != FFTB_OK) {
+      p->a_bufs = old;
+      configure_planes(p);
+      return st;
+    }
+  }
+  fftb_status st = resize_T(p, c.chunk);
+  if (st != FFTB_OK) return st;
+  p->chunk = c.chunk;
+  p->tiles = c.tiles;
+  p->pf_level = c.level;
+  for (int i = 0; i < 3; ++i) p->plane_ctas[i] = c.ctas[i] >= 0 ? c.ctas[i] : p->sms * occ_in_use(p, i);
   return FFTB_OK;
 }
 
@@ -757,13 +934,10 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   cudaGetDevice(&dev);
   if (dev != p->device) return fail(FFTB_ERR_INVALID_ARG, "current device differs from the plan's device");
   const std::string key = tune_key(p);
-  int chunk = 0, ctas[3] = {0, 0, 0}, tiles = 0;
-  if (tune_cache_lookup(key, &chunk, ctas, &tiles)) {
-    fftb_status st = resize_T(p, chunk);
+  TuneChoice cached;
+  if (tune_cache_lookup(key, &cached)) {
+    fftb_status st = apply_choice(p, cached);
     if (st != FFTB_OK) return st;
-    p->chunk = chunk;
-    p->tiles = tiles;
-    for (int i = 0; i < 3; ++i) p->plane_ctas[i] = ctas[i];
     if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
     return FFTB_OK;
   }
@@ -775,10 +949,8 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   const size_t band_bytes = (size_t)p->csize * (2 * max_ngw + (cube_io ? vol : 0));
   const size_t budget = (size_t)4 << 30;
   const int bands = (int)std::max<int64_t>(1, std::min<int64_t>(p->total_bands, (int64_t)(budget / std::max<size_t>(band_bytes, 1))));
-  const size_t sph_b = (size_t)p->sphere_elems * p->csize;  // prefix offsets stay inside
+  const size_t sph_b = (size_t)p->sphere_elems * p->csize;
   const size_t cube_b = (size_t)bands * vol * p->csize;
-  const size_t in_b = p->dir == FFTB_R_TO_G ? cube_b : std::min(sph_b, (size_t)bands * max_ngw * p->csize + 256);
-  const size_t out_b = p->dir == FFTB_G_TO_R ? cube_b : std::min(sph_b, (size_t)bands * max_ngw * p->csize + 256);
   void *d_in = nullptr, *d_out = nullptr, *d_cube = nullptr, *d_v = nullptr;
   auto cleanup = [&]() {
     if (d_in) cudaFree(d_in);
@@ -789,8 +961,6 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   // a band prefix may still index the whole sphere batch: size for the real offsets
   const size_t in_full = p->dir == FFTB_R_TO_G ? cube_b : sph_b;
   const size_t out_full = p->dir == FFTB_G_TO_R ? cube_b : sph_b;
-  (void)in_b;
-  (void)out_b;
   if (cudaMalloc(&d_in, in_full) != cudaSuccess || cudaMalloc(&d_out, out_full) != cudaSuccess ||
       (p->dir == FFTB_ROUNDTRIP && cudaMalloc(&d_cube, cube_b) != cudaSuccess)) {
     cleanup();
@@ -806,28 +976,22 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
     cudaMemset(d_v, 0, (size_t)vol * p->csize / 2);
     p->d_V = d_v;
   }
-  // candidates
+  // chunk candidates
   std::vector<int> chunks;
-  const size_t t_band = (size_t)p->n[2] * std::max<int32_t>(p->smax, 1) * p->csize;
+  const size_t t_band = (size_t)p->n[2] * p->tpitch * p->csize;
   for (int c : {bands, (bands + 1) / 2, (bands + 3) / 4, (int)((24u << 20) / t_band), (int)((48u << 20) / t_band),
                 (int)((96u << 20) / t_band)}) {
     c = std::max(1, std::min(c, bands));
     if (std::find(chunks.begin(), chunks.end(), c) == chunks.end()) chunks.push_back(c);
   }
-  std::vector<int> mults;
-  const int mi = p->dir == FFTB_R_TO_G ? 1 : p->dir == FFTB_APPLY_LOCAL ? 2 : 0;
-  for (int m : {p->plane_occ[mi], p->plane_occ[mi] - 1, 0})
-    if ((m > 0 || (m == 0 && !p->a_glob)) && std::find(mults.begin(), mults.end(), m) == mults.end())
-      mults.push_back(m);
-  int max_chunk = *std::max_element(chunks.begin(), chunks.end());
+  const int max_chunk = *std::max_element(chunks.begin(), chunks.end());
   fftb_status st = resize_T(p, max_chunk);
   if (st != FFTB_OK) {
     p->d_V = saved_v;
     cleanup();
     return st;
   }
-  const int saved_chunk = p->chunk, saved_tiles = p->tiles;
-  int saved_ctas[3] = {p->plane_ctas[0], p->plane_ctas[1], p->plane_ctas[2]};
+  const TuneChoice saved = current_choice(p);
   const bool saved_timing = p->timing, saved_graph = p->use_graph;
   const int64_t saved_launches = p->launches;
   p->timing = false;
@@ -836,33 +1000,69 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int best_chunk = saved_chunk, best_ctas[3] = {saved_ctas[0], saved_ctas[1], saved_ctas[2]}, best_tiles = saved_tiles;
-  for (int c : chunks) {
-    for (int mm = 0; mm < 2 * (int)mults.size(); ++mm) {
-      const int m = mults[mm / 2];
-      p->tiles = (mm & 1) ? p->sms * p->stick_occ : 0;
-      p->chunk = c;
-      for (int i = 0; i < 3; ++i) p->plane_ctas[i] = m == 0 ? 0 : p->sms * std::min(m, p->plane_occ[i]);
-      st = enqueue(p, bands, d_in, d_out, d_cube, nullptr);
-      if (st != FFTB_OK) break;
-      cudaEventRecord(e0, nullptr);
-      for (int t = 0; t < trials && st == FFTB_OK; ++t) st = enqueue(p, bands, d_in, d_out, d_cube, nullptr);
-      cudaEventRecord(e1, nullptr);
-      cudaError_t ce = cudaEventSynchronize(e1);
-      if (st != FFTB_OK || ce != cudaSuccess) {
-        if (ce != cudaSuccess) st = cuda_fail(ce, "autotune run");
-        break;
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) {
-        best = ms;
-        best_chunk = c;
-        best_tiles = p->tiles;
-        for (int i = 0; i < 3; ++i) best_ctas[i] = p->plane_ctas[i];
-      }
+  TuneChoice best_c = saved;
+  // times one candidate; keeps it if it is the fastest so far
+  auto trial = [&](const TuneChoice& c) -> fftb_status {
+    fftb_status s2 = apply_choice(p, c);
+    if (s2 != FFTB_OK) return s2;
+    s2 = enqueue(p, bands, d_in, d_out, d_cube, nullptr);  // warm-up
+    if (s2 != FFTB_OK) return s2;
+    cudaEventRecord(e0, nullptr);
+    for (int t = 0; t < trials && s2 == FFTB_OK; ++t) s2 = enqueue(p, bands, d_in, d_out, d_cube, nullptr);
+    cudaEventRecord(e1, nullptr);
+    cudaError_t ce = cudaEventSynchronize(e1);
+    if (s2 != FFTB_OK) return s2;
+    if (ce != cudaSuccess) return cuda_fail(ce, "autotune run");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_c = current_choice(p);
     }
+    return FFTB_OK;
+  };
+  // stage 1: kernel variant (slab-plane buffers, prefetch level), each with a
+  // full wave of persistent plane CTAs and the plan's chunk
+  std::vector<int> nbufs = {saved.a_bufs};
+  if (!p->a_glob) {
+    const int other = 3 - saved.a_bufs;
+    if (plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, other) <= kSmemLimit) nbufs.push_back(other);
+  }
+  for (int nb : nbufs) {
     if (st != FFTB_OK) break;
+    std::vector<int> masks;
+    for (int lv : {saved.level, 0, 1, 2}) {
+      TuneChoice c = saved;
+      c.a_bufs = nb;
+      c.level = lv;
+      c.ctas[0] = c.ctas[1] = c.ctas[2] = -1;  // one full wave of the variant
+      st = apply_choice(p, c);
+      if (st != FFTB_OK) break;
+      int mask = 0;
+      for (int i = 0; i < 3; ++i)
+        if (pf_active(p, i)) mask |= 1 << i;
+      if (std::find(masks.begin(), masks.end(), mask) != masks.end()) continue;
+      masks.push_back(mask);
+      st = trial(c);
+      if (st != FFTB_OK) break;
+    }
+  }
+  // stage 2: chunk, persistent plane CTAs per SM (0: one CTA per plane) and
+  // z-stage CTAs for the chosen variant
+  const TuneChoice variant = best_c;
+  if (st == FFTB_OK) st = apply_choice(p, variant);
+  const int mi = p->dir == FFTB_R_TO_G ? 1 : p->dir == FFTB_APPLY_LOCAL ? 2 : 0;
+  std::vector<int> mults;
+  for (int m : {occ_in_use(p, mi), occ_in_use(p, mi) - 1, 0})
+    if ((m > 0 || (m == 0 && !p->a_glob)) && std::find(mults.begin(), mults.end(), m) == mults.end())
+      mults.push_back(m);
+  for (size_t k = 0; st == FFTB_OK && k < chunks.size() * mults.size() * 2; ++k) {
+    TuneChoice c = variant;
+    c.chunk = chunks[k / (2 * mults.size())];
+    const int m = mults[(k / 2) % mults.size()];
+    c.tiles = (k & 1) ? p->sms * p->stick_occ : 0;
+    for (int i = 0; i < 3; ++i) c.ctas[i] = m == 0 ? 0 : p->sms * std::min(m, occ_in_use(p, i));
+    st = trial(c);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -872,16 +1072,13 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   p->d_V = saved_v;
   cleanup();
   if (st != FFTB_OK) {
-    p->chunk = saved_chunk;
-    p->tiles = saved_tiles;
-    for (int i = 0; i < 3; ++i) p->plane_ctas[i] = saved_ctas[i];
+    apply_choice(p, saved);
     return st;
   }
   // a chunk tuned on a band prefix covers the whole batch too
-  p->chunk = best_chunk;
-  p->tiles = best_tiles;
-  for (int i = 0; i < 3; ++i) p->plane_ctas[i] = best_ctas[i];
+  st = apply_choice(p, best_c);
+  if (st != FFTB_OK) return st;
   if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
-  tune_cache_store(key, best_chunk, best_ctas, best_tiles);
+  tune_cache_store(key, best_c);
   return FFTB_OK;
 }

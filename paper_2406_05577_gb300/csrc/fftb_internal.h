@@ -49,7 +49,8 @@ struct Geo {
   const void* tw1;           // [N1]
   const void* tw2;           // [N2]
   int32_t n0, n1, n2;
-  int32_t smax;              // T pitch (max sticks over k)
+  int32_t smax;              // T pitch: max sticks over k, rounded up to even (rows start
+                             //   on 16-byte boundaries for bulk copies)
   int32_t xmax;              // max slabs over k
 };
 
@@ -66,10 +67,16 @@ struct Launch {
   int32_t plane_ctas;   // persistent plane-stage CTAs (0: one per plane)
   int32_t a_bufs;       // slab-plane buffers of the plane stage (1 or 2)
   void* a_glob;         // slab planes in global memory (per CTA), or NULL: shared memory
+  int32_t pf;           // plane stage: prefetch its inputs with bulk async copies
+  int32_t inject;       // INJECT_* bits (tests of the bounded waits)
+  int32_t* status;      // device-visible status word (STATUS_* bits), set on a failed wait
   cudaStream_t stream;
 };
 
 enum Prec { P_F64 = 0, P_F32 = 1, P_TC = 2 };
+// Launch::inject: the first prefetch of CTA 0 (warp 0) is not issued, so its
+// bounded wait runs out and the kernel reports STATUS_WAIT_TIMEOUT.
+constexpr int32_t INJECT_SKIP_FIRST_PREFETCH = 1;
 enum Mode { M_G2R = 1, M_R2G = -1, M_APPLY = 2 };
 
 bool grid_size_supported(int n);
@@ -89,6 +96,14 @@ int plane_occupancy(int prec, int mode, int n0, int n1, int xmax, int a_bufs, bo
 // ctas: persistent z-stage CTAs (0: one warp per task)
 cudaError_t launch_stick(int prec, int mode, const Launch& L, int ctas);
 cudaError_t launch_plane(int prec, int mode, const Launch& L);
+// FP32 plane kernels with bulk-copy prefetch of their inputs (mode M_*; tp =
+// the stick-row pitch Geo::smax). Unsupported combinations return false, 0
+// or cudaErrorInvalidValue.
+bool plane_pf_supported(int mode, int n0, int n1);
+size_t plane_pf_smem(int mode, int n0, int n1, int xmax, int a_bufs, int tp);
+cudaError_t prepare_plane_pf(int mode, int n0, int n1, int xmax, int a_bufs, int tp);
+int plane_pf_occupancy(int mode, int n0, int n1, int xmax, int a_bufs, int tp);
+cudaError_t launch_plane_pf(int mode, const Launch& L);
 // Sets the calling thread's message for fftb_last_error().
 void set_last_error(const std::string& msg);
 

@@ -1,0 +1,88 @@
+// k_f32_pf.cu -- float plane kernels whose inputs arrive by bulk asynchronous
+// copies (k_plane with PF), in a translation unit of their own.
+#include "kernels.cuh"
+
+namespace fftb {
+namespace {
+
+template <int N, int MODE> constexpr bool pf_has() { return MODE != M_R2G || rows_prefetchable<float, N, N>(); }
+
+template <int N, int MODE> auto pf_kernel() { return k_plane<float, N, N, MODE, false, false, pf_has<N, MODE>()>; }
+
+template <int N> cudaError_t go(int mode, const Launch& L) {
+  if (!plane_pf_supported(mode, N, N)) return cudaErrorInvalidValue;
+  const size_t smem = plane_smem_c<float, N, N>(L.g.xmax, L.a_bufs, false, mode, L.g.smax);
+  const int nplanes = L.nb * L.g.n2;
+  const dim3 grid(L.plane_ctas > 0 ? min(L.plane_ctas, nplanes) : nplanes);
+  constexpr int NT = PlaneCfg<float>::NW * 32;
+  if (mode == M_G2R) pf_kernel<N, M_G2R>()<<<grid, NT, smem, L.stream>>>(L);
+  else if (mode == M_R2G) pf_kernel<N, M_R2G>()<<<grid, NT, smem, L.stream>>>(L);
+  else pf_kernel<N, M_APPLY>()<<<grid, NT, smem, L.stream>>>(L);
+  return cudaGetLastError();
+}
+template <int N> cudaError_t prep(int mode, int xmax, int a_bufs, int tp) {
+  const int s = (int)plane_smem_c<float, N, N>(xmax, a_bufs, false, mode, tp);
+  if (mode == M_G2R) return raise_smem_limit((const void*)pf_kernel<N, M_G2R>(), s);
+  if (mode == M_R2G) return raise_smem_limit((const void*)pf_kernel<N, M_R2G>(), s);
+  return raise_smem_limit((const void*)pf_kernel<N, M_APPLY>(), s);
+}
+template <int N> int occ(int mode, int xmax, int a_bufs, int tp) {
+  constexpr int NT = PlaneCfg<float>::NW * 32;
+  const size_t s = plane_smem_c<float, N, N>(xmax, a_bufs, false, mode, tp);
+  int nb = 0;
+  cudaError_t e;
+  if (mode == M_G2R) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pf_kernel<N, M_G2R>(), NT, s);
+  else if (mode == M_R2G) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pf_kernel<N, M_R2G>(), NT, s);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pf_kernel<N, M_APPLY>(), NT, s);
+  return e == cudaSuccess ? nb : 0;
+}
+
+}  // namespace
+
+bool plane_pf_supported(int mode, int n0, int n1) {
+  if (n0 != n1) return false;
+  switch (n0) {
+#define C_(N) case N: return mode == M_G2R || mode == M_APPLY || (mode == M_R2G && rows_prefetchable<float, N, N>());
+    FFTB_SIZES(C_)
+#undef C_
+  }
+  return false;
+}
+size_t plane_pf_smem(int mode, int n0, int n1, int xmax, int a_bufs, int tp) {
+  if (n0 != n1) return 0;
+  switch (n0) {
+#define C_(N) case N: return plane_smem_c<float, N, N>(xmax, a_bufs, false, mode, tp);
+    FFTB_SIZES(C_)
+#undef C_
+  }
+  return 0;
+}
+cudaError_t prepare_plane_pf(int mode, int n0, int n1, int xmax, int a_bufs, int tp) {
+  if (!plane_pf_supported(mode, n0, n1)) return cudaErrorInvalidValue;
+  switch (n0) {
+#define C_(N) case N: return prep<N>(mode, xmax, a_bufs, tp);
+    FFTB_SIZES(C_)
+#undef C_
+  }
+  return cudaErrorInvalidValue;
+}
+int plane_pf_occupancy(int mode, int n0, int n1, int xmax, int a_bufs, int tp) {
+  if (!plane_pf_supported(mode, n0, n1)) return 0;
+  switch (n0) {
+#define C_(N) case N: return occ<N>(mode, xmax, a_bufs, tp);
+    FFTB_SIZES(C_)
+#undef C_
+  }
+  return 0;
+}
+cudaError_t launch_plane_pf(int mode, const Launch& L) {
+  if (L.g.n0 != L.g.n1) return cudaErrorInvalidValue;
+  switch (L.g.n0) {
+#define C_(N) case N: return go<N>(mode, L);
+    FFTB_SIZES(C_)
+#undef C_
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace fftb

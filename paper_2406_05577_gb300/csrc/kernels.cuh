@@ -21,6 +21,11 @@
 // shared-memory transposes inside k_plane.
 #pragma once
 
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "async_copy.cuh"
 #include "fft_core.cuh"
 #include "fftb_internal.h"
 #include "line_fft.cuh"
@@ -242,10 +247,33 @@ template <int N0, int N1> __host__ __device__ constexpr int plane_scratch() {
              : (32 / Line<N0>::G) * Line<N0>::PITCH;
 }
 
-template <typename T, int N0, int N1> size_t plane_smem_c(int xmax, int a_bufs, bool ag = false) {
+// Row pitch (elements) of cube rows staged in shared memory by the r -> G
+// prefetch: 64 bytes beyond a multiple of 128, so the rows a warp reads at
+// once fall on both halves of the banks; even, so every row starts on a
+// 16-byte boundary.
+template <typename C> __host__ __device__ constexpr int stage_pitch(int n) {
+  return n + ((int)(64 / sizeof(C)) - n % (int)(128 / sizeof(C)) + (int)(128 / sizeof(C))) % (int)(128 / sizeof(C));
+}
+// The r -> G prefetch hands every warp at least one x task per plane.
+template <typename T, int N0, int N1> __host__ __device__ constexpr bool rows_prefetchable() {
+  return (N1 + 32 / Line<N0>::G - 1) / (32 / Line<N0>::G) >= PlaneCfg<T>::NW;
+}
+// Shared memory the prefetch adds for `mode` (0: none): the next plane's
+// stick row (tp elements, G -> r and apply) or each warp's next x-task rows
+// (r -> G), plus their mbarriers.
+template <typename T, int N0, int N1> size_t plane_pf_bytes(int mode, int tp) {
+  using C = typename cplx<T>::type;
+  constexpr int NW = PlaneCfg<T>::NW, WX = 32 / Line<N0>::G;
+  if (mode == 0) return 0;
+  if (mode == M_R2G) return sizeof(C) * (size_t)NW * WX * stage_pitch<C>(N0) + 8 * NW;
+  return sizeof(C) * (size_t)tp + 16;
+}
+template <typename T, int N0, int N1> size_t plane_smem_c(int xmax, int a_bufs, bool ag = false, int pf_mode = 0,
+                                                          int tp = 0) {
   using C = typename cplx<T>::type;
   return sizeof(C) * ((ag ? 0 : (size_t)a_bufs * N1 * a_pitch(xmax)) + (size_t)PlaneCfg<T>::NW * plane_scratch<N0, N1>() +
-                      N0 + N1);
+                      N0 + N1) +
+         plane_pf_bytes<T, N0, N1>(pf_mode, tp);
 }
 
 // packed per-lane slab indices: byte q of w[q / 4] = xi of position q, 255 = empty
@@ -254,7 +282,13 @@ template <int E> struct XiPack {
   __device__ __forceinline__ int get(int q) const { return (int)((w[q >> 2] >> (8 * (q & 3))) & 0xFFu); }
 };
 
-template <typename T, int N0, int N1, int MODE, bool TC = false, bool AG = false>
+// PF: the plane's global inputs arrive by bulk asynchronous copies issued
+// one step ahead (G -> r, apply: the next plane's stick row, whole, by thread
+// 0 after the mid-plane barrier; r -> G: each warp's next x task's cube rows,
+// by the warp itself once it has read the current ones), completed on
+// mbarriers. A wait that runs out sets the plan's status word; the CTA then
+// leaves at the next block barrier, after its copies in flight have landed.
+template <typename T, int N0, int N1, int MODE, bool TC = false, bool AG = false, bool PF = false>
 __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k_plane(const Launch L) {
   using C = typename cplx<T>::type;
   using LY = Line<N1>;
@@ -277,11 +311,22 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   C* scr = sbase + warp * SCR;
   C* tw0 = sbase + NW * SCR;
   C* tw1 = tw0 + N0;
+  // prefetch staging (PF): a stick row, or NW blocks of WX cube rows at pitch RP
+  constexpr int RP = stage_pitch<C>(N0);
+  C* stg = tw1 + N1;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg + (MODE == M_R2G ? NW * WX * RP : L.g.smax));
+  C* wst = stg + warp * (WX * RP);
   {
     const C* t0 = static_cast<const C*>(L.g.tw0);
     const C* t1 = static_cast<const C*>(L.g.tw1);
     for (int m = threadIdx.x; m < N0; m += NT) tw0[m] = t0[m];
     for (int m = threadIdx.x; m < N1; m += NT) tw1[m] = t1[m];
+  }
+  if constexpr (PF) {
+    if (threadIdx.x < (MODE == M_R2G ? NW : 1)) {
+      mbar_init(bars + threadIdx.x, 1);
+      mbar_init_fence();
+    }
   }
   __syncthreads();
   C* rowy = scr + ly * LY::PITCH;
@@ -303,6 +348,61 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   auto ysigned = [](int y) { return y < N1 - N1 / 2 ? y : y - N1; };
 
   const int nplanes = L.nb * n2;
+  // ---- prefetch state (PF)
+  bool bad = false;          // a wait ran out
+  bool outstanding = false;  // a copy phase was issued (or withheld by injection) and not yet seen complete
+  uint32_t ph = 0;           // parity of the next phase to complete
+  // G -> r, apply (thread 0): the stick row of plane pp, rounded up to 16 bytes (within the even pitch)
+  auto issue_trow = [&](int pp) {
+    const int bl2 = pp / n2, z2 = pp - bl2 * n2;
+    const int S2 = L.g.band[L.band0 + bl2].ki.S;
+    const uint32_t bytes = (uint32_t)((S2 * (int)sizeof(C) + 15) & ~15);
+    fence_proxy_async_smem();
+    mbar_arrive_expect(bars, bytes);
+    if (bytes) bulk_g2s(stg, static_cast<const C*>(L.T) + ((size_t)bl2 * n2 + z2) * L.g.smax, bytes, bars);
+  };
+  // r -> G: this warp's first x task of plane pp (the x tasks follow the y tasks)
+  auto x_start = [&](int pp) {
+    const int Xn = L.g.band[L.band0 + pp / n2].ki.X;
+    return (warp - ((Xn + WY - 1) / WY) % NW + NW) % NW;
+  };
+  // r -> G (lane 0): the WX cube rows of x task t of plane pp
+  auto issue_rows = [&](int pp, int t) {
+    const int bl2 = pp / n2, z2 = pp - bl2 * n2;
+    const int r0 = t * WX, nr = min(WX, N1 - r0);
+    const C* src = static_cast<const C*>(L.cube_in) + ((size_t)(L.band0 + bl2) * n2 + z2) * (size_t)(N1 * N0) +
+                   (size_t)r0 * N0;
+    fence_proxy_async_smem();
+    mbar_arrive_expect(bars + warp, (uint32_t)(nr * N0 * sizeof(C)));
+    for (int r = 0; r < nr; ++r) bulk_g2s(wst + r * RP, src + (size_t)r * N0, (uint32_t)(N0 * sizeof(C)), bars + warp);
+  };
+  // waits for the outstanding phase of barrier b; false if the limit ran out
+  auto await = [&](uint64_t* b) {
+    if (outstanding && !bad) {
+      if (mbar_wait(b, ph, WAIT_LIMIT_NS)) {
+        outstanding = false;
+        ph ^= 1;
+      } else {
+        bad = true;
+      }
+    }
+  };
+  // leaving after a failed wait: let copies in flight land, report
+  auto abort_plane = [&]() {
+    if (outstanding) mbar_wait(bars + (MODE == M_R2G ? warp : 0), ph, WAIT_LIMIT_NS);
+    if (threadIdx.x == 0) *reinterpret_cast<volatile int32_t*>(L.status) = STATUS_WAIT_TIMEOUT;
+  };
+  if constexpr (PF) {
+    const bool withhold = (L.inject & INJECT_SKIP_FIRST_PREFETCH) && blockIdx.x == 0;
+    if ((int)blockIdx.x < nplanes) {
+      if constexpr (MODE == M_R2G) {
+        if (lane == 0 && !(withhold && warp == 0)) issue_rows(blockIdx.x, x_start(blockIdx.x));
+      } else {
+        if (threadIdx.x == 0 && !withhold) issue_trow(blockIdx.x);
+      }
+      outstanding = true;
+    }
+  }
   int cur_k = -1;
   XiPack<EX> xin, xout;  // slab index of this lane's first-pass / last-pass x positions
   int parity = 0;
@@ -346,6 +446,11 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
     if constexpr (MODE == M_G2R || MODE == M_APPLY) {
       // y-DFT (+) of the occupied x-slab columns: scatter the sticks of this
       // warp's columns into zeroed scratch rows, transform, write A columns
+      const C* Tr = Tz;
+      if constexpr (PF) {
+        await(bars);
+        Tr = stg;
+      }
 #pragma unroll 1
       for (int t = warp; t < ty; t += NW) {
         const int c0 = t * WY, nl = min(WY, X - c0);
@@ -360,7 +465,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
             for (int j = 0; j < LY::R0; ++j) {
               const int d = ysigned(LY::first_pos(gy, m, j)) - ylo;
-              v[m * LY::R0 + j] = (unsigned)d < (unsigned)len ? Tz[sa + d] : czero<C>();
+              v[m * LY::R0 + j] = (unsigned)d < (unsigned)len ? Tr[sa + d] : czero<C>();
             }
         } else {
           const int sbeg = __shfl_sync(0xffffffffu, ci.x, 0);
@@ -369,7 +474,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
           __syncwarp();
           for (int s = sbeg + lane; s < send; s += 32) {
             const int xy = sxy[s];
-            scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)] = Tz[s];
+            scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)] = Tr[s];
           }
           __syncwarp();
 #pragma unroll
@@ -387,7 +492,18 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
             for (int j = 0; j < LY::RL; ++j) A[LY::last_pos(gy, m, j) * XP + c0 + ly] = v[m * LY::RL + j];
         }
       }
-      __syncthreads();
+      if constexpr (PF) {
+        if (__syncthreads_or(bad)) {
+          abort_plane();
+          return;
+        }
+        // the stick row is consumed: fetch the next plane's during the x phase
+        const int pn = p + gridDim.x;
+        if (threadIdx.x == 0 && pn < nplanes) issue_trow(pn);
+        outstanding = pn < nplanes;
+      } else {
+        __syncthreads();
+      }
       // x-DFT (+) of every row, zero-extended from the X occupied columns
 #pragma unroll 1
       for (int t = (warp - x_first + NW) % NW; t < tx; t += NW) {
@@ -442,13 +558,42 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
       for (int t = (warp - x_first + NW) % NW; t < tx; t += NW) {
         const int y0 = t * WX, row = y0 + lx;
         const bool live = row < N1;
-        const C* in = static_cast<const C*>(L.cube_in) + plane + (size_t)(live ? row : 0) * N0;
         C v[EX];
+        if constexpr (PF) {
+          if (__any_sync(0xffffffffu, outstanding && !bad)) {
+            const bool ok = mbar_wait(bars + warp, ph, WAIT_LIMIT_NS);
+            if (__any_sync(0xffffffffu, ok)) {
+              outstanding = false;
+              ph ^= 1;
+            } else {
+              bad = true;
+            }
+          }
+          const C* in = wst + lx * RP;
 #pragma unroll
-        for (int m = 0; m < EX / LX::R0; ++m)
+          for (int m = 0; m < EX / LX::R0; ++m)
 #pragma unroll
-          for (int j = 0; j < LX::R0; ++j)
-            v[m * LX::R0 + j] = live ? in[LX::first_pos(gx, m, j)] : czero<C>();
+            for (int j = 0; j < LX::R0; ++j)
+              v[m * LX::R0 + j] = live ? in[LX::first_pos(gx, m, j)] : czero<C>();
+          __syncwarp();
+          // the rows are in registers: fetch this warp's next x task
+          int pn = p, tn = t + NW;
+          if (tn >= tx) {
+            pn = p + gridDim.x;
+            tn = pn < nplanes ? x_start(pn) : 0;
+          }
+          if (!bad && pn < nplanes) {
+            if (lane == 0) issue_rows(pn, tn);
+            outstanding = true;
+          }
+        } else {
+          const C* in = static_cast<const C*>(L.cube_in) + plane + (size_t)(live ? row : 0) * N0;
+#pragma unroll
+          for (int m = 0; m < EX / LX::R0; ++m)
+#pragma unroll
+            for (int j = 0; j < LX::R0; ++j)
+              v[m * LX::R0 + j] = live ? in[LX::first_pos(gx, m, j)] : czero<C>();
+        }
         if constexpr (TC) LX::template run_tc<-1>(v, gx, rowx, scr, tw0, tcx, wx_m);
         else LX::template run<-1>(v, gx, rowx, tw0, tcx);
         if (live) {
@@ -461,7 +606,14 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
       }
     }
     if constexpr (MODE == M_R2G || MODE == M_APPLY) {
-      __syncthreads();
+      if constexpr (PF && MODE == M_R2G) {
+        if (__syncthreads_or(bad)) {
+          abort_plane();
+          return;
+        }
+      } else {
+        __syncthreads();
+      }
       // y-DFT (-) of each occupied column; keep the occupied sticks
 #pragma unroll 1
       for (int t = warp; t < ty; t += NW) {
@@ -507,6 +659,24 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 }
 
 // ---------------------------------------------------------------- dispatch
+// Raises a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes`, never lowering it: plans of one grid size but different
+// spheres or buffers share the kernel, and a lower limit set by one plan
+// would make another plan's launches fail.
+inline cudaError_t raise_smem_limit(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> have;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  int& h = have[{dev, fn}];
+  if (bytes <= h) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) h = bytes;
+  return e;
+}
+
 #define FFTB_SIZES(X) X(12) X(16) X(20) X(24) X(32) X(40) X(48) X(64) X(96) X(128) X(160)
 
 template <typename T, bool TC> size_t stick_smem_t(int n2) {
@@ -569,30 +739,30 @@ template <typename T, bool TC, int N> cudaError_t go_plane(int mode, const Launc
 }
 template <typename T, bool TC, int N2> cudaError_t prep_stick() {
   const int s = (int)stick_smem_c<T, N2>();
-  cudaError_t e = cudaFuncSetAttribute(k_stick<T, N2, M_G2R, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaError_t e = raise_smem_limit((const void*)k_stick<T, N2, M_G2R, TC>, s);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_stick<T, N2, M_R2G, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+    e = raise_smem_limit((const void*)k_stick<T, N2, M_R2G, TC>, s);
   return e;
 }
 template <typename T, bool TC, int N> cudaError_t prep_plane(int xmax, int a_bufs, bool ag) {
   if constexpr (sizeof(T) == 8 && !TC) {
     if (ag) {
       const int s = (int)plane_smem_c<T, N, N>(xmax, a_bufs, true);
-      cudaError_t e = cudaFuncSetAttribute(k_plane<T, N, N, M_G2R, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+      cudaError_t e = raise_smem_limit((const void*)k_plane<T, N, N, M_G2R, false, true>, s);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_plane<T, N, N, M_R2G, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+        e = raise_smem_limit((const void*)k_plane<T, N, N, M_R2G, false, true>, s);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_plane<T, N, N, M_APPLY, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+        e = raise_smem_limit((const void*)k_plane<T, N, N, M_APPLY, false, true>, s);
       return e;
     }
   }
   if (ag) return cudaErrorInvalidValue;
   const int s = (int)plane_smem_c<T, N, N>(xmax, a_bufs);
-  cudaError_t e = cudaFuncSetAttribute(k_plane<T, N, N, M_G2R, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaError_t e = raise_smem_limit((const void*)k_plane<T, N, N, M_G2R, TC>, s);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_plane<T, N, N, M_R2G, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+    e = raise_smem_limit((const void*)k_plane<T, N, N, M_R2G, TC>, s);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_plane<T, N, N, M_APPLY, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+    e = raise_smem_limit((const void*)k_plane<T, N, N, M_APPLY, TC>, s);
   return e;
 }
 

@@ -20,6 +20,7 @@ FFTB_OK, FFTB_ERR_INVALID_ARG, FFTB_ERR_UNSUPPORTED, FFTB_ERR_ALLOC, FFTB_ERR_CU
     FFTB_ERR_DEVICE_TIMEOUT = range(6)
 FFTB_G_TO_R, FFTB_R_TO_G, FFTB_ROUNDTRIP, FFTB_APPLY_LOCAL = 1, -1, 0, 2
 FFTB_FP64, FFTB_FP32, FFTB_MIXED_TC = 0, 1, 2
+FFTB_INJECT_SKIP_FIRST_PREFETCH = 1
 
 DIRECTIONS = {"g2r": FFTB_G_TO_R, "r2g": FFTB_R_TO_G, "roundtrip": FFTB_ROUNDTRIP,
               "apply": FFTB_APPLY_LOCAL}
@@ -53,6 +54,8 @@ class fftb_plan_info_t(ctypes.Structure):
         ("complex_bytes", ctypes.c_int32),
         ("stick_ctas", ctypes.c_int32),
         ("plane_ctas", ctypes.c_int32),
+        ("prefetch", ctypes.c_int32),
+        ("slab_buffers", ctypes.c_int32),
     ]
 
 
@@ -78,6 +81,10 @@ EXPORTS = {
                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fftb_plan_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fftb_plan_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "fftb_plan_set_prefetch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "fftb_plan_check": (ctypes.c_int, [ctypes.c_void_p]),
+    "fftb_plan_set_slab_buffers": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "fftb_plan_inject": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fftb_sphere_enumerate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_double,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                              ctypes.POINTER(ctypes.c_int64)]),
@@ -218,6 +225,24 @@ def fftb_plan_autotune(plan, trials=3):
     _check(lib().fftb_plan_autotune(plan, int(trials)))
 
 
+def fftb_plan_set_prefetch(plan, level):
+    """level 0 off, 1 where no resident CTA is lost (default), 2 wherever it fits."""
+    _check(lib().fftb_plan_set_prefetch(plan, int(level)))
+
+
+def fftb_plan_set_slab_buffers(plan, nbuf):
+    _check(lib().fftb_plan_set_slab_buffers(plan, int(nbuf)))
+
+
+def fftb_plan_check(plan):
+    """Raises FFTBError (status FFTB_ERR_DEVICE_TIMEOUT) if a device wait ran out."""
+    _check(lib().fftb_plan_check(plan))
+
+
+def fftb_plan_inject(plan, flags):
+    _check(lib().fftb_plan_inject(plan, int(flags)))
+
+
 def fftb_plan_launches(plan):
     return int(lib().fftb_plan_launches(plan))
 
@@ -331,6 +356,20 @@ class Plan:
     def autotune(self, trials=3):
         fftb_plan_autotune(self.handle, trials)
         self.info = fftb_plan_get_info(self.handle)
+
+    def set_prefetch(self, level=1):
+        fftb_plan_set_prefetch(self.handle, int(level))
+        self.info = fftb_plan_get_info(self.handle)
+
+    def set_slab_buffers(self, nbuf):
+        fftb_plan_set_slab_buffers(self.handle, nbuf)
+        self.info = fftb_plan_get_info(self.handle)
+
+    def check(self):
+        fftb_plan_check(self.handle)
+
+    def inject(self, flags):
+        fftb_plan_inject(self.handle, flags)
 
     def close(self):
         if self.handle:
