@@ -101,6 +101,11 @@ typedef struct {
                               copies: bit 0 G->r, bit 1 r->G, bit 2 apply               */
   int32_t slab_buffers;    /* slab planes per plane-stage CTA in shared memory (1 or 2;
                               0: kept in global memory)                                 */
+  int32_t tensor_core_planes; /* MIXED_TC plane stages whose y and x DFTs run as dense
+                              split-FP16 products on the 5th-generation tensor cores
+                              (tcgen05, FP32 accumulators in tensor memory): bit 0 G->r,
+                              bit 1 r->G; grids 16, 32, 48, 64 with N0 == N1. Their
+                              z stage then runs in FP32.                                */
 } fftb_plan_info_t;
 
 /* Builds the spheres, stick/slab tables and twiddles on the host, uploads

@@ -123,6 +123,13 @@ struct fftb_plan_s {
   bool pf_fit[3] = {false, false, false};
   int pf_occ[3] = {0, 0, 0};
   int pf_level = 1;
+  // MIXED_TC plane stages on the 5th-generation tensor cores (grids up to
+  // 64): G->r and r->G use them, the z stage then runs in FP32
+  bool tc5 = false;
+  Tc5Geo tc5g[2] = {};  // G->r, r->G (each with its DFT-matrix image)
+  void* d_tc5w = nullptr;
+  int tc5_ctas = 0;
+  int stick_prec = P_F32;
   int32_t inject = 0;              // fftb_plan_inject
   int32_t* h_status = nullptr;     // status word in mapped pinned host memory
   int32_t* d_status = nullptr;     // its device address
@@ -202,6 +209,7 @@ void release(fftb_plan_s* p) {
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->h_status) cudaFreeHost(p->h_status);
+  if (p->d_tc5w) cudaFree(p->d_tc5w);
   delete p;
 }
 
@@ -396,7 +404,60 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
       if (cst != FFTB_OK) { release(p); return cst; }
     }
   }
-  p->stick_occ = std::max(1, stick_occupancy(p->prec_kernel, p->n[2]));
+  p->stick_prec = p->prec_kernel;
+  if (p->prec_kernel == P_TC && tc5_supported(p->n[0], p->n[1])) {
+    // union over k-points of the occupied x values and the stick y values
+    int xlo = 1 << 30, xhi = -(1 << 30), ylo = 1 << 30, yhi = -(1 << 30);
+    bool columns_ok = true;
+    for (int k = 0; k < p->nk; ++k) {
+      const KGeom& G = p->geo[k];
+      columns_ok = columns_ok && G.contiguous_columns;
+      std::vector<int32_t> rec;
+      slab_records(G, p->n, rec);
+      for (int x = 0; x < p->n[0]; ++x) {
+        const int xi = G.xmap[x];
+        if (xi < 0) continue;
+        const int xs = x < p->n[0] - p->n[0] / 2 ? x : x - p->n[0];
+        xlo = std::min(xlo, xs);
+        xhi = std::max(xhi, xs);
+        if (rec[4 * xi + 1] > 0) {
+          ylo = std::min(ylo, rec[4 * xi + 2]);
+          yhi = std::max(yhi, rec[4 * xi + 2] + rec[4 * xi + 1] - 1);
+        }
+      }
+    }
+    if (columns_ok && xhi >= xlo && yhi >= ylo) {
+      const Tc5Geo g0{xlo, xhi - xlo + 1, ylo, yhi - ylo + 1, nullptr};
+      int occ_a = 0, occ_b = 0;
+      bool fits = tc5_smem(M_G2R, p->n[0], g0, p->tpitch) <= kSmemLimit &&
+                  tc5_smem(M_R2G, p->n[0], g0, p->tpitch) <= kSmemLimit;
+      if (fits) {
+        e = tc5_prepare(M_G2R, p->n[0], g0, p->tpitch, &occ_a);
+        if (e == cudaSuccess) e = tc5_prepare(M_R2G, p->n[0], g0, p->tpitch, &occ_b);
+        if (e != cudaSuccess) { release(p); return cuda_fail(e, "tensor-core kernel attributes"); }
+        if (occ_a >= 1 && occ_b >= 1) {
+          // the DFT-matrix images of both directions, built once on the device
+          const size_t wa = align_up(tc5_weight_bytes(M_G2R, p->n[0], g0), 256);
+          const size_t wb = tc5_weight_bytes(M_R2G, p->n[0], g0);
+          e = cudaMalloc(&p->d_tc5w, wa + wb);
+          if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaMalloc tensor-core matrices failed"); }
+          p->tc5g[0] = g0;
+          p->tc5g[0].w = p->d_tc5w;
+          p->tc5g[1] = g0;
+          p->tc5g[1].w = static_cast<unsigned char*>(p->d_tc5w) + wa;
+          e = tc5_build_weights(M_G2R, p->n[0], p->tc5g[0], p->g.tw0, const_cast<void*>(p->tc5g[0].w));
+          if (e == cudaSuccess) e = tc5_build_weights(M_R2G, p->n[0], p->tc5g[1], p->g.tw0, const_cast<void*>(p->tc5g[1].w));
+          if (e != cudaSuccess) { release(p); return cuda_fail(e, "tensor-core matrices"); }
+          p->tc5 = true;
+          p->tc5_ctas = sms * std::min(occ_a, occ_b);
+          p->stick_prec = P_F32;
+          e = prepare_kernels(P_F32, p->n[0], p->n[1], p->n[2], p->xmax, p->a_bufs, false);
+          if (e != cudaSuccess) { release(p); return cuda_fail(e, "kernel attributes"); }
+        }
+      }
+    }
+  }
+  p->stick_occ = std::max(1, stick_occupancy(p->stick_prec, p->n[2]));
   p->tiles = sms * p->stick_occ;  // z stage: one wave of persistent CTAs (the autotuner may pick one warp per task pair)
   e = cudaHostAlloc(reinterpret_cast<void**>(&p->h_status), sizeof(int32_t), cudaHostAllocMapped);
   if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaHostAlloc status word failed"); }
@@ -458,6 +519,7 @@ FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) 
   for (int i = 0; i < 3; ++i)
     if (pf_active(p, i)) info->prefetch |= 1 << i;
   info->slab_buffers = p->a_glob ? 0 : p->a_bufs;
+  info->tensor_core_planes = p->tc5 ? 3 : 0;
   return FFTB_OK;
 }
 
@@ -493,24 +555,27 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
   }
   cudaError_t e;
   const int pk = p->prec_kernel;
+  // bulk copies read the cube from 16-byte aligned rows
+  const bool cube_in_16 = (reinterpret_cast<uintptr_t>(L.cube_in) % 16) == 0;
   switch (kind) {
-    case K_STICK_G2R: e = launch_stick(pk, M_G2R, L, p->tiles); break;
+    case K_STICK_G2R: e = launch_stick(p->stick_prec, M_G2R, L, p->tiles); break;
     case K_PLANE_G2R: {
       Launch Lp = L;
       Lp.plane_ctas = p->plane_ctas[0];
       Lp.pf = pf_active(p, 0);
-      e = Lp.pf ? launch_plane_pf(M_G2R, Lp) : launch_plane(pk, M_G2R, Lp);
+      if (p->tc5) e = tc5_launch(M_G2R, Lp, p->tc5g[0], p->tc5_ctas);
+      else e = Lp.pf ? launch_plane_pf(M_G2R, Lp) : launch_plane(pk, M_G2R, Lp);
       break;
     }
     case K_PLANE_R2G: {
       Launch Lp = L;
       Lp.plane_ctas = p->plane_ctas[1];
-      // bulk copies read the cube from 16-byte aligned rows
-      Lp.pf = pf_active(p, 1) && (reinterpret_cast<uintptr_t>(L.cube_in) % 16) == 0;
-      e = Lp.pf ? launch_plane_pf(M_R2G, Lp) : launch_plane(pk, M_R2G, Lp);
+      Lp.pf = pf_active(p, 1) && cube_in_16;
+      if (p->tc5 && cube_in_16) e = tc5_launch(M_R2G, Lp, p->tc5g[1], p->tc5_ctas);
+      else e = Lp.pf ? launch_plane_pf(M_R2G, Lp) : launch_plane(pk, M_R2G, Lp);
       break;
     }
-    case K_STICK_R2G: e = launch_stick(pk, M_R2G, L, p->tiles); break;
+    case K_STICK_R2G: e = launch_stick(p->stick_prec, M_R2G, L, p->tiles); break;
     default: {
       Launch Lp = L;
       Lp.plane_ctas = p->plane_ctas[2];

@@ -104,6 +104,24 @@ size_t plane_pf_smem(int mode, int n0, int n1, int xmax, int a_bufs, int tp);
 cudaError_t prepare_plane_pf(int mode, int n0, int n1, int xmax, int a_bufs, int tp);
 int plane_pf_occupancy(int mode, int n0, int n1, int xmax, int a_bufs, int tp);
 cudaError_t launch_plane_pf(int mode, const Launch& L);
+// MIXED_TC plane stage on the 5th-generation tensor cores (k_tc5.cu): the
+// union over k-points of the occupied x values [xlo, xlo + xu) and of the
+// stick y values [ylo, ylo + yu) (signed grid indices), and the device image
+// of the direction's DFT matrices (tc5_build_weights).
+struct Tc5Geo {
+  int32_t xlo, xu, ylo, yu;
+  const void* w;
+};
+bool tc5_supported(int n0, int n1);
+size_t tc5_weight_bytes(int mode, int n, const Tc5Geo& P);
+// writes the split-FP16 DFT matrices of `mode` into img (device), from the
+// plan's twiddle table tw (device, float2 e^{+2 pi i m / n}); asynchronous
+cudaError_t tc5_build_weights(int mode, int n, const Tc5Geo& P, const void* tw, void* img);
+size_t tc5_smem(int mode, int n, const Tc5Geo& P, int smax);
+// raises the shared-memory limit and reports resident CTAs per SM
+cudaError_t tc5_prepare(int mode, int n, const Tc5Geo& P, int smax, int* occupancy);
+// ctas: persistent CTAs (0: enough for every plane)
+cudaError_t tc5_launch(int mode, const Launch& L, const Tc5Geo& P, int ctas);
 // Sets the calling thread's message for fftb_last_error().
 void set_last_error(const std::string& msg);
 

@@ -56,6 +56,7 @@ class fftb_plan_info_t(ctypes.Structure):
         ("plane_ctas", ctypes.c_int32),
         ("prefetch", ctypes.c_int32),
         ("slab_buffers", ctypes.c_int32),
+        ("tensor_core_planes", ctypes.c_int32),
     ]
 
 
