@@ -147,10 +147,15 @@ fftb_status fftb_execute(fftb_plan plan, const void* in_dev, void* out_dev,
                          void* cube_dev, void* stream);
 
 /* As fftb_execute, but in_host / out_host are host buffers (pinned for
- * full-speed copies). Copies the input to plan-owned device staging, runs
- * the transform, copies the result back and synchronises `stream`. The
- * staging buffers are allocated on the first call and kept with the plan.
- * For ROUNDTRIP cube_dev is a device cube batch (may be NULL: plan-owned). */
+ * full-speed copies and for overlap). Copies the input to plan-owned device
+ * staging, runs the transform, copies the result back and synchronises
+ * `stream`. The bands go through in two pieces on three plan-owned
+ * streams, so the copy in of one piece, the transform of the previous one
+ * and the copy out of the one before that overlap; the call is ordered
+ * after earlier work on `stream` and returns when all of it is done. The
+ * staging buffers and streams are created on the first call and kept with
+ * the plan. For ROUNDTRIP cube_dev is a device cube batch (may be NULL:
+ * plan-owned). A device wait that ran out returns FFTB_ERR_DEVICE_TIMEOUT. */
 fftb_status fftb_execute_host(fftb_plan plan, const void* in_host, void* out_host,
                               void* cube_dev, void* stream);
 

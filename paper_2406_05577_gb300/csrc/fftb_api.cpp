@@ -100,6 +100,11 @@ struct fftb_plan_s {
   size_t T_bytes = 0;
   Geo g{};
   const void* d_V = nullptr;
+  // sphere offset of every band (complex elements; total_bands + 1 values)
+  std::vector<int64_t> band_sph;
+  // host-buffer path: copy-in, compute and copy-out streams and their events
+  cudaStream_t hs[3] = {nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> hev;
   // host-buffer path staging (allocated on first use)
   void* d_stage_in = nullptr;
   void* d_stage_out = nullptr;
@@ -207,6 +212,9 @@ void release(fftb_plan_s* p) {
   if (p->d_stage_out) cudaFree(p->d_stage_out);
   if (p->d_stage_cube) cudaFree(p->d_stage_cube);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->hev) cudaEventDestroy(e);
+  for (cudaStream_t st : p->hs)
+    if (st) cudaStreamDestroy(st);
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->h_status) cudaFreeHost(p->h_status);
   if (p->d_tc5w) cudaFree(p->d_tc5w);
@@ -331,6 +339,8 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
     ent_base += G.ngw;
   }
   if (ent_base >= (int64_t(1) << 31)) { release(p); return fail(FFTB_ERR_UNSUPPORTED, "total sphere entries above 2^31"); }
+  for (const BandInfo& bi : band) p->band_sph.push_back(bi.sph);
+  p->band_sph.push_back(sph);
   if (band.empty()) band.push_back(BandInfo{});
   if (ent_pos.empty()) { ent_pos.push_back(0); ent_zs.push_back(0); }
   if (stick_xy.empty()) stick_xy.push_back(0);
@@ -594,8 +604,9 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
 
 static bool aligned(const void* q, int a) { return (reinterpret_cast<uintptr_t>(q) % (uintptr_t)a) == 0; }
 
-// Enqueues every band chunk's stages for the first `bands` bands.
-static fftb_status enqueue(fftb_plan_s* p, int bands, const void* in, void* out, void* cube, cudaStream_t s) {
+// Enqueues every band chunk's stages for the bands [first, first + bands).
+static fftb_status enqueue(fftb_plan_s* p, int bands, const void* in, void* out, void* cube, cudaStream_t s,
+                           int first = 0) {
   Launch L{};
   L.g = p->g;
   L.T = p->d_T;
@@ -605,9 +616,9 @@ static fftb_status enqueue(fftb_plan_s* p, int bands, const void* in, void* out,
   L.inject = p->inject;
   L.status = p->d_status;
   L.stream = s;
-  for (int b0 = 0; b0 < bands; b0 += p->chunk) {
+  for (int b0 = first; b0 < first + bands; b0 += p->chunk) {
     L.band0 = b0;
-    L.nb = std::min(p->chunk, bands - b0);
+    L.nb = std::min(p->chunk, first + bands - b0);
     cudaError_t e = cudaSuccess;
     switch (p->dir) {
       case FFTB_G_TO_R:
@@ -723,25 +734,68 @@ FFTB_EXPORT fftb_status fftb_execute_host(fftb_plan p, const void* in_host, void
                                           void* stream) {
   if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
   if (!in_host || !out_host) return fail(FFTB_ERR_INVALID_ARG, "in_host and out_host must be given");
+  if (p->total_bands == 0) return FFTB_OK;
+  if (p->dir == FFTB_APPLY_LOCAL && !p->d_V) return fail(FFTB_ERR_INVALID_ARG, "APPLY_LOCAL needs fftb_set_potential");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != p->device) return fail(FFTB_ERR_INVALID_ARG, "current device differs from the plan's device");
   const size_t sph_b = (size_t)p->sphere_elems * p->csize, cube_b = (size_t)p->cube_elems * p->csize;
-  size_t in_b = sph_b, out_b = sph_b;
-  if (p->dir == FFTB_G_TO_R) out_b = cube_b;
-  if (p->dir == FFTB_R_TO_G) in_b = cube_b;
-  fftb_status st = ensure(&p->d_stage_in, &p->stage_in_bytes, in_b);
-  if (st == FFTB_OK) st = ensure(&p->d_stage_out, &p->stage_out_bytes, out_b);
+  const bool in_cube = p->dir == FFTB_R_TO_G, out_cube = p->dir == FFTB_G_TO_R;
+  fftb_status st = ensure(&p->d_stage_in, &p->stage_in_bytes, in_cube ? cube_b : sph_b);
+  if (st == FFTB_OK) st = ensure(&p->d_stage_out, &p->stage_out_bytes, out_cube ? cube_b : sph_b);
   if (st == FFTB_OK && p->dir == FFTB_ROUNDTRIP && !cube_dev) {
     st = ensure(&p->d_stage_cube, &p->stage_cube_bytes, cube_b);
     cube_dev = p->d_stage_cube;
   }
   if (st != FFTB_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(p->d_stage_in, in_host, in_b, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(e, "copy in");
-  st = fftb_execute(p, p->d_stage_in, p->d_stage_out, p->dir == FFTB_ROUNDTRIP ? cube_dev : nullptr, stream);
-  if (st != FFTB_OK) return st;
-  e = cudaMemcpyAsync(out_host, p->d_stage_out, out_b, cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return cuda_fail(e, "copy out");
-  e = cudaStreamSynchronize(s);
+  // Band pieces pipelined over three streams: the copy in of piece i + 1 and
+  // the copy out of piece i - 1 overlap the transform of piece i. Two pieces
+  // measured best on GB300 (more pieces cost more in smaller, less efficient
+  // launches than they hide; kernels reading or writing page-locked host
+  // memory directly over the CPU-GPU link measured slower than the copies).
+  const int pieces = std::min(2, p->total_bands);
+  if (!p->hs[0]) {
+    for (int i = 0; i < 3; ++i)
+      if (cudaStreamCreateWithFlags(&p->hs[i], cudaStreamNonBlocking) != cudaSuccess)
+        return fail(FFTB_ERR_CUDA, "stream creation failed");
+  }
+  while ((int)p->hev.size() < 2 * pieces + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(FFTB_ERR_CUDA, "event creation failed");
+    p->hev.push_back(e);
+  }
+  const int64_t vol = (int64_t)p->n[0] * p->n[1] * p->n[2];
+  auto bytes_of = [&](bool cube, int b) -> size_t {  // byte offset of band b in a batch
+    return (size_t)(cube ? (int64_t)b * vol : p->band_sph[b]) * p->csize;
+  };
+  cudaEvent_t ev_begin = p->hev[2 * pieces], ev_end = p->hev[2 * pieces + 1];
+  cudaError_t e = cudaEventRecord(ev_begin, s);
+  for (int i = 0; e == cudaSuccess && i < 3; ++i) e = cudaStreamWaitEvent(p->hs[i], ev_begin, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "stream ordering");
+  const unsigned char* hin = static_cast<const unsigned char*>(in_host);
+  unsigned char* hout = static_cast<unsigned char*>(out_host);
+  unsigned char* din = static_cast<unsigned char*>(p->d_stage_in);
+  unsigned char* dout = static_cast<unsigned char*>(p->d_stage_out);
+  for (int i = 0; i < pieces; ++i) {
+    const int b0 = (int)((int64_t)p->total_bands * i / pieces), b1 = (int)((int64_t)p->total_bands * (i + 1) / pieces);
+    if (b1 <= b0) continue;
+    const size_t i0 = bytes_of(in_cube, b0), i1 = bytes_of(in_cube, b1);
+    const size_t o0 = bytes_of(out_cube, b0), o1 = bytes_of(out_cube, b1);
+    e = cudaMemcpyAsync(din + i0, hin + i0, i1 - i0, cudaMemcpyHostToDevice, p->hs[0]);
+    if (e == cudaSuccess) e = cudaEventRecord(p->hev[2 * i], p->hs[0]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->hs[1], p->hev[2 * i], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "copy in");
+    st = enqueue(p, b1 - b0, din, dout, p->dir == FFTB_ROUNDTRIP ? cube_dev : nullptr, p->hs[1], b0);
+    if (st != FFTB_OK) return st;
+    e = cudaEventRecord(p->hev[2 * i + 1], p->hs[1]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->hs[2], p->hev[2 * i + 1], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hout + o0, dout + o0, o1 - o0, cudaMemcpyDeviceToHost, p->hs[2]);
+    if (e != cudaSuccess) return cuda_fail(e, "copy out");
+  }
+  e = cudaEventRecord(ev_end, p->hs[2]);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_end, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
   if (*reinterpret_cast<volatile int32_t*>(p->h_status)) {
     *p->h_status = 0;

@@ -46,8 +46,18 @@ template <typename T, int N2> constexpr size_t stick_smem_c() {
   return sizeof(C) * ((size_t)STICK_NW * (32 / Line<N2>::G) * Line<N2>::PITCH + N2);
 }
 
+// resident z-stage CTAs per SM the register allocation must allow (FP32: two,
+// measured best; the 128-point z-stage ran one CTA per SM without the cap)
+template <typename T> __host__ __device__ constexpr int stick_minb() {
+#ifdef FFTB_STICK_MINB
+  return FFTB_STICK_MINB;
+#else
+  return sizeof(T) == 8 ? 1 : 2;
+#endif
+}
+
 template <typename T, int N2, int MODE, bool TC = false>
-__global__ void __launch_bounds__(STICK_NW * 32) k_stick(const Launch L) {
+__global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(const Launch L) {
   using C = typename cplx<T>::type;
   using LZ = Line<N2>;
   constexpr int WZ = 32 / LZ::G, EZ = LZ::E, NT = STICK_NW * 32;

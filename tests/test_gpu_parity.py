@@ -193,7 +193,44 @@ def test_host_buffer_entry_point(F):
     xout = np.zeros_like(xin)
     F.fftb_execute_host(plan.handle, xin.ctypes.data, xout.ctypes.data, None, None)
     assert relerr(xout, np.prod(n) * xin) <= 1e-12
-    assert plan.launches() == plan.info["kernels_per_execute"]
+    # two pieces (one and two bands), four kernels each
+    assert plan.launches() == 2 * plan.info["kernels_per_execute"]
+
+
+@pytest.mark.parametrize("direction", ["g2r", "r2g", "roundtrip", "apply"])
+def test_host_pipeline_matches_device_execute(F, direction):
+    """The host-buffer entry point splits the bands into pieces (here across a
+    k-point boundary and band chunks) and overlaps copies with transforms: its
+    results are those of the device entry point, bit for bit."""
+    import torch
+    n, r = (32, 32, 32), 7.5
+    ks = np.array([(0.1, 0.2, -0.3), (-0.4, 0.0, 0.25), (0.3, -0.45, 0.0)])
+    bands = [3, 1, 6]
+    plan = F.Plan(n, direction, "fp32", radius=r, kshift=ks, bands=bands, max_chunk_bands=2)
+    info = plan.info
+    if direction == "apply":
+        v = fi.gaussian_potential(n, 8, 3.0, seed=81).astype(np.float32)
+        plan.set_potential(torch.from_numpy(v).cuda())
+    nin = info["cube_elems"] if direction == "r2g" else info["sphere_elems"]
+    nout = info["cube_elems"] if direction == "g2r" else info["sphere_elems"]
+    xin = fi.complex_gaussian((nin,), 82).astype(np.complex64)
+    xd = torch.from_numpy(xin).cuda()
+    od = torch.empty(nout, dtype=torch.complex64, device="cuda")
+    cd = torch.empty(info["cube_elems"], dtype=torch.complex64, device="cuda") if direction == "roundtrip" else None
+    plan.execute(xd, od, cd)
+    torch.cuda.synchronize()
+    want = od.cpu().numpy()
+    pin_in = torch.from_numpy(xin).pin_memory()
+    pin_out = torch.empty(nout, dtype=torch.complex64).pin_memory()
+    cube_ptr = None
+    if direction == "roundtrip":
+        cube2 = torch.empty(info["cube_elems"], dtype=torch.complex64, device="cuda")
+        cube_ptr = cube2.data_ptr()
+    s = torch.cuda.Stream()
+    F.fftb_execute_host(plan.handle, pin_in.data_ptr(), pin_out.data_ptr(), cube_ptr, s.cuda_stream)
+    assert np.array_equal(pin_out.numpy(), want)
+    if direction == "roundtrip":
+        assert torch.equal(cube2, cd)
 
 
 def test_graph_replay_and_update(F):
