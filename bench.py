@@ -6,7 +6,8 @@ round trip G -> r -> G with the real-space cube written to HBM and read back.
 A step is one fftb_execute of the whole batch. Other workloads
 (``--workload``): 96^3 with 8 k-points and uneven band counts in one graph-
 replayed, autotuned launch sequence; 128^3 local-potential apply
-V(r) psi(r) with 256 bands; 160^3 with 512 bands streamed in band chunks.
+V(r) psi(r) with 256 bands; 160^3 with 512 bands streamed in band chunks; 256^3
+(sphere diameter 128) with 256 bands, the paper's own single-GPU shape.
 
 Under torchrun each rank runs its own copy of the workload on its own GPU
 (bands are independent: weak scaling, no collective on the data path).
@@ -68,6 +69,12 @@ class Workload:
             self.desc = ("160^3 grid, |G|<=40 (267761 G), 512 bands, G->r->G with the 16.8 GB cube set "
                          "kept in HBM, processed in band chunks")
             self.envelope, self.seed, self.graph, self.tune = None, 5, False, True
+        elif name == "sphere256_e2":
+            self.n, self.radius, self.kshift, self.bands = (256, 256, 256), 64.0, None, [256]
+            self.direction = "roundtrip"
+            self.desc = ("256^3 grid, |G|<=64 (sphere diameter 128, 1097917 G), 256 bands, G->r->G with the "
+                         "34 GB cube set kept in HBM, processed in band chunks (the paper's E2 shape on one GPU)")
+            self.envelope, self.seed, self.graph, self.tune = None, 6, False, True
         else:
             raise SystemExit(f"unknown workload {name}")
         self.total_bands = sum(self.bands)
@@ -497,7 +504,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sphere64_rt",
-                    choices=["sphere64_rt", "sphere96_multik", "sphere128_apply", "sphere160_large"])
+                    choices=["sphere64_rt", "sphere96_multik", "sphere128_apply", "sphere160_large", "sphere256_e2"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

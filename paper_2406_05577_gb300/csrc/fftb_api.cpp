@@ -33,7 +33,7 @@ template <typename T, bool TC> int stick_occupancy_t(int);
 #define FFTB_BY_PREC(prec, call)                                                           \
   ((prec) == P_F64 ? call<double, false> : (prec) == P_TC ? call<float, true> : call<float, false>)
 
-static const int kSizes[] = {12, 16, 20, 24, 32, 40, 48, 64, 96, 128, 160};
+static const int kSizes[] = {12, 16, 20, 24, 32, 40, 48, 64, 96, 128, 160, 256};
 
 bool grid_size_supported(int n) {
   for (int s : kSizes)
@@ -240,7 +240,7 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   if (!grid_size_supported(d->n[0]) || !grid_size_supported(d->n[1]) || !grid_size_supported(d->n[2]) ||
       !plane_size_supported(d->n[0], d->n[1]))
     return fail(FFTB_ERR_UNSUPPORTED,
-                "grid extents must be one of 12,16,20,24,32,40,48,64,96,128,160 with N0 == N1");
+                "grid extents must be one of 12,16,20,24,32,40,48,64,96,128,160,256 with N0 == N1");
 
   fftb_plan_s* p = new (std::nothrow) fftb_plan_s();
   if (!p) return fail(FFTB_ERR_ALLOC, "host allocation failed");
@@ -286,7 +286,7 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
 
   const size_t smem_limit = kSmemLimit;
   if (plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, 2) > smem_limit) p->a_bufs = 1;
-  if (plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, p->a_bufs) > smem_limit && p->prec_kernel == P_F64) {
+  if (plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, p->a_bufs) > smem_limit && p->n[0] >= 128) {
     p->a_bufs = 2;  // slab planes in global memory, double buffered
     p->a_glob = true;
   }

@@ -4,6 +4,8 @@
 
 namespace fftb {
 namespace {
+// the prefetch staging fits shared memory beside the slab planes up to 160
+#define FFTB_PF_SIZES(X) X(12) X(16) X(20) X(24) X(32) X(40) X(48) X(64) X(96) X(128) X(160)
 
 template <int N, int MODE> constexpr bool pf_has() { return MODE != M_R2G || rows_prefetchable<float, N, N>(); }
 
@@ -43,7 +45,7 @@ bool plane_pf_supported(int mode, int n0, int n1) {
   if (n0 != n1) return false;
   switch (n0) {
 #define C_(N) case N: return mode == M_G2R || mode == M_APPLY || (mode == M_R2G && rows_prefetchable<float, N, N>());
-    FFTB_SIZES(C_)
+    FFTB_PF_SIZES(C_)
 #undef C_
   }
   return false;
@@ -52,7 +54,7 @@ size_t plane_pf_smem(int mode, int n0, int n1, int xmax, int a_bufs, int tp) {
   if (n0 != n1) return 0;
   switch (n0) {
 #define C_(N) case N: return plane_smem_c<float, N, N>(xmax, a_bufs, false, mode, tp);
-    FFTB_SIZES(C_)
+    FFTB_PF_SIZES(C_)
 #undef C_
   }
   return 0;
@@ -61,7 +63,7 @@ cudaError_t prepare_plane_pf(int mode, int n0, int n1, int xmax, int a_bufs, int
   if (!plane_pf_supported(mode, n0, n1)) return cudaErrorInvalidValue;
   switch (n0) {
 #define C_(N) case N: return prep<N>(mode, xmax, a_bufs, tp);
-    FFTB_SIZES(C_)
+    FFTB_PF_SIZES(C_)
 #undef C_
   }
   return cudaErrorInvalidValue;
@@ -70,7 +72,7 @@ int plane_pf_occupancy(int mode, int n0, int n1, int xmax, int a_bufs, int tp) {
   if (!plane_pf_supported(mode, n0, n1)) return 0;
   switch (n0) {
 #define C_(N) case N: return occ<N>(mode, xmax, a_bufs, tp);
-    FFTB_SIZES(C_)
+    FFTB_PF_SIZES(C_)
 #undef C_
   }
   return 0;
@@ -79,7 +81,7 @@ cudaError_t launch_plane_pf(int mode, const Launch& L) {
   if (L.g.n0 != L.g.n1) return cudaErrorInvalidValue;
   switch (L.g.n0) {
 #define C_(N) case N: return go<N>(mode, L);
-    FFTB_SIZES(C_)
+    FFTB_PF_SIZES(C_)
 #undef C_
   }
   return cudaErrorInvalidValue;

@@ -687,7 +687,7 @@ inline cudaError_t raise_smem_limit(const void* fn, int bytes) {
   return e;
 }
 
-#define FFTB_SIZES(X) X(12) X(16) X(20) X(24) X(32) X(40) X(48) X(64) X(96) X(128) X(160)
+#define FFTB_SIZES(X) X(12) X(16) X(20) X(24) X(32) X(40) X(48) X(64) X(96) X(128) X(160) X(256)
 
 template <typename T, bool TC> size_t stick_smem_t(int n2) {
   switch (n2) {
@@ -725,15 +725,15 @@ template <typename T, bool TC, int N2> cudaError_t go_stick(int mode, const Laun
   return cudaGetLastError();
 }
 template <typename T, bool TC, int N> cudaError_t go_plane(int mode, const Launch& L) {
-  if constexpr (sizeof(T) == 8 && !TC) {
-    if (L.a_glob) {  // double-precision slab planes too large for shared memory
+  if constexpr (N >= 128) {
+    if (L.a_glob) {  // slab planes too large for shared memory: per-CTA blocks of a global buffer
       const size_t smem = plane_smem_c<T, N, N>(L.g.xmax, L.a_bufs, true);
       const int nplanes = L.nb * L.g.n2;
       const dim3 grid(min(L.plane_ctas, nplanes));
       constexpr int NT = PlaneCfg<T>::NW * 32;
-      if (mode == M_G2R) k_plane<T, N, N, M_G2R, false, true><<<grid, NT, smem, L.stream>>>(L);
-      else if (mode == M_R2G) k_plane<T, N, N, M_R2G, false, true><<<grid, NT, smem, L.stream>>>(L);
-      else k_plane<T, N, N, M_APPLY, false, true><<<grid, NT, smem, L.stream>>>(L);
+      if (mode == M_G2R) k_plane<T, N, N, M_G2R, TC, true><<<grid, NT, smem, L.stream>>>(L);
+      else if (mode == M_R2G) k_plane<T, N, N, M_R2G, TC, true><<<grid, NT, smem, L.stream>>>(L);
+      else k_plane<T, N, N, M_APPLY, TC, true><<<grid, NT, smem, L.stream>>>(L);
       return cudaGetLastError();
     }
   }
@@ -755,14 +755,14 @@ template <typename T, bool TC, int N2> cudaError_t prep_stick() {
   return e;
 }
 template <typename T, bool TC, int N> cudaError_t prep_plane(int xmax, int a_bufs, bool ag) {
-  if constexpr (sizeof(T) == 8 && !TC) {
+  if constexpr (N >= 128) {
     if (ag) {
       const int s = (int)plane_smem_c<T, N, N>(xmax, a_bufs, true);
-      cudaError_t e = raise_smem_limit((const void*)k_plane<T, N, N, M_G2R, false, true>, s);
+      cudaError_t e = raise_smem_limit((const void*)k_plane<T, N, N, M_G2R, TC, true>, s);
       if (e == cudaSuccess)
-        e = raise_smem_limit((const void*)k_plane<T, N, N, M_R2G, false, true>, s);
+        e = raise_smem_limit((const void*)k_plane<T, N, N, M_R2G, TC, true>, s);
       if (e == cudaSuccess)
-        e = raise_smem_limit((const void*)k_plane<T, N, N, M_APPLY, false, true>, s);
+        e = raise_smem_limit((const void*)k_plane<T, N, N, M_APPLY, TC, true>, s);
       return e;
     }
   }
@@ -780,12 +780,12 @@ template <typename T, bool TC, int N> int occ_plane(int mode, int xmax, int a_bu
   constexpr int NT = PlaneCfg<T>::NW * 32;
   int nb = 0;
   cudaError_t e;
-  if constexpr (sizeof(T) == 8 && !TC) {
+  if constexpr (N >= 128) {
     if (ag) {
       const size_t sm = plane_smem_c<T, N, N>(xmax, a_bufs, true);
-      if (mode == M_G2R) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_G2R, false, true>, NT, sm);
-      else if (mode == M_R2G) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_R2G, false, true>, NT, sm);
-      else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_APPLY, false, true>, NT, sm);
+      if (mode == M_G2R) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_G2R, TC, true>, NT, sm);
+      else if (mode == M_R2G) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_R2G, TC, true>, NT, sm);
+      else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_APPLY, TC, true>, NT, sm);
       return e == cudaSuccess ? nb : 0;
     }
   }

@@ -35,6 +35,7 @@ FFTB_LP(64, 8, 8, 8, 0, 0);  // measured best of 8x8, 16x4 (E=16) and 4x16 (E=16
 FFTB_LP(96, 12, 6, 4, 4, 0);
 FFTB_LP(128, 16, 16, 8, 0, 0);
 FFTB_LP(160, 20, 4, 4, 2, 5);
+FFTB_LP(256, 16, 16, 16, 0, 0);
 #undef FFTB_LP
 
 // ----------------------------------------------------------- tensor cores

@@ -88,7 +88,7 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
   if (bands < 0) return err(FFTB_ERR_INVALID_ARG, "bands must be >= 0");
   if (!grid_size_supported(n[0]) || !grid_size_supported(n[1]) || !grid_size_supported(n[2]) ||
       !plane_size_supported(n[0], n[1]))
-    return err(FFTB_ERR_UNSUPPORTED, "grid extents must be one of 12,16,20,24,32,40,48,64,96,128,160 with N0 == N1");
+    return err(FFTB_ERR_UNSUPPORTED, "grid extents must be one of 12,16,20,24,32,40,48,64,96,128,160,256 with N0 == N1");
   if (bands == 0) return FFTB_OK;
   if (!in_dev || !out_dev) return err(FFTB_ERR_INVALID_ARG, "in_dev and out_dev must be device pointers");
   if ((reinterpret_cast<uintptr_t>(in_dev) | reinterpret_cast<uintptr_t>(out_dev)) % 8 != 0)

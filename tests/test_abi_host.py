@@ -58,7 +58,8 @@ def test_kshift_spheres_match_oracle(fftb):
 
 @pytest.mark.parametrize("n,r,sticks,slabs", [((24, 24, 24), 6.0, 113, 13), ((64, 64, 64), 16.0, 797, 33),
                                               ((128, 128, 128), 32.0, 3209, 65),
-                                              ((160, 160, 160), 40.0, 5025, 81)])
+                                              ((160, 160, 160), 40.0, 5025, 81),
+                                              ((256, 256, 256), 64.0, 12853, 129)])
 def test_stick_and_slab_counts(fftb, n, r, sticks, slabs):
     g = sphere_gvectors(n, r)
     # independent count from the oracle's list

@@ -163,3 +163,27 @@ def test_160_fp64_roundtrip_sampled(F):
     pts = sample_points(n, 12, 21)
     want = oracle.g2r_points(g, c, n, pts)
     assert relerr(R[:, pts[:, 2], pts[:, 1], pts[:, 0]], want) <= 1e-12
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp64", 1e-12), ("mixed", 1e-5)])
+def test_256_roundtrip_paper_shape(F, prec, tol):
+    """256^3 with sphere diameter 128 (|G| <= 64, 1 097 917 G): the paper's
+    single-GPU shape; slab planes of 256 x 129 live in global memory. One band
+    against the full oracle, the round trip on two bands."""
+    import torch
+    n, r, bands = (256, 256, 256), 64.0, 2
+    plan = F.Plan(n, "roundtrip", prec, radius=r, bands=[bands])
+    assert plan.info["slab_buffers"] == 0
+    g = plan.sphere(0)
+    assert len(g) == 1097917
+    cd = np.complex128 if prec == "fp64" else np.complex64
+    c = fi.complex_gaussian((bands, len(g)), 7).astype(cd)
+    x = torch.from_numpy(c.reshape(-1)).cuda()
+    out = torch.empty_like(x)
+    cube = torch.empty(plan.info["cube_elems"], dtype=x.dtype, device="cuda")
+    plan.execute(x, out, cube)
+    torch.cuda.synchronize()
+    c64 = c.astype(np.complex128)
+    assert relerr(out.cpu().numpy(), 256 ** 3 * c64.reshape(-1)) <= tol
+    R0 = cube[: 256 ** 3].view(256, 256, 256).cpu().numpy().astype(np.complex128)
+    assert relerr(R0, oracle.g2r(g, c64[0], n)) <= tol
