@@ -99,13 +99,15 @@ typedef struct {
   int32_t plane_ctas;      /* persistent plane-stage CTAs of this direction (0: one per plane) */
   int32_t prefetch;        /* plane stages that prefetch their inputs with bulk asynchronous
                               copies: bit 0 G->r, bit 1 r->G, bit 2 apply               */
-  int32_t slab_buffers;    /* slab planes per plane-stage CTA in shared memory (1 or 2;
-                              0: kept in global memory)                                 */
+  int32_t slab_buffers;    /* slab planes per plane-stage CTA (1 or 2)                  */
   int32_t tensor_core_planes; /* MIXED_TC plane stages whose y and x DFTs run as dense
                               split-FP16 products on the 5th-generation tensor cores
                               (tcgen05, FP32 accumulators in tensor memory): bit 0 G->r,
                               bit 1 r->G; grids 16, 32, 48, 64 with N0 == N1. Their
                               z stage then runs in FP32.                                */
+  int32_t slab_planes_global; /* 1: the slab planes live in a per-CTA block of global
+                              memory (planes too large for shared memory: FP64 from
+                              160, any precision at 256), 0: in shared memory          */
 } fftb_plan_info_t;
 
 /* Builds the spheres, stick/slab tables and twiddles on the host, uploads
@@ -208,12 +210,12 @@ fftb_status fftb_plan_set_prefetch(fftb_plan plan, int32_t level);
 
 /* Slab-plane buffers of the plane stage: 2 (default where it fits) lets a
  * CTA start the next plane's y stage while slower warps finish the current
- * plane's x stage, at twice the shared memory; 1 halves that memory (more
- * resident CTAs per SM on large grids) for a second block barrier per plane.
- * Resets the persistent plane CTAs to one full wave; fftb_plan_autotune also
- * tries both. Errors: INVALID_ARG for a count other than 1 or 2;
- * UNSUPPORTED when 2 do not fit or the plan keeps its slab planes in global
- * memory (FP64 on the largest grids). */
+ * plane's x stage, at twice the memory; 1 halves that memory (more resident
+ * CTAs per SM on large grids, or slab planes that stay in L2 when they live
+ * in global memory) for a second block barrier per plane. Resets the
+ * persistent plane CTAs to one full wave; fftb_plan_autotune also tries
+ * both. Errors: INVALID_ARG for a count other than 1 or 2; UNSUPPORTED when
+ * 2 do not fit in shared memory. */
 fftb_status fftb_plan_set_slab_buffers(fftb_plan plan, int32_t nbuf);
 
 /* Device status. Every wait of a plane kernel on an asynchronous copy gives

@@ -300,9 +300,13 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   const int32_t smax_pitch = (std::max<int32_t>(p->smax, 1) + 1) & ~1;
   p->tpitch = smax_pitch;
 
-  // band chunk: keep the stick buffer near 48 MB, or as requested
+  // band chunk: keep the stick buffer near 48 MB (it then stays in L2), but
+  // give every launch at least about 2048 (band, z) planes so the persistent
+  // plane CTAs have several planes each; or as requested
   const size_t t_band = (size_t)p->n[2] * smax_pitch * p->csize;
-  int chunk = d->max_chunk_bands > 0 ? d->max_chunk_bands : (int)std::max<size_t>(1, (48u << 20) / t_band);
+  int chunk = d->max_chunk_bands > 0
+                  ? d->max_chunk_bands
+                  : (int)std::max<size_t>({(size_t)1, (48u << 20) / t_band, (size_t)((2048 + p->n[2] - 1) / p->n[2])});
   chunk = std::max(1, std::min(chunk, std::max(1, p->total_bands)));
   p->chunk = chunk;
 
@@ -528,7 +532,8 @@ FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) 
   info->prefetch = 0;
   for (int i = 0; i < 3; ++i)
     if (pf_active(p, i)) info->prefetch |= 1 << i;
-  info->slab_buffers = p->a_glob ? 0 : p->a_bufs;
+  info->slab_buffers = p->a_bufs;
+  info->slab_planes_global = p->a_glob ? 1 : 0;
   info->tensor_core_planes = p->tc5 ? 3 : 0;
   return FFTB_OK;
 }
@@ -838,8 +843,7 @@ FFTB_EXPORT fftb_status fftb_plan_set_prefetch(fftb_plan p, int32_t level) {
 FFTB_EXPORT fftb_status fftb_plan_set_slab_buffers(fftb_plan p, int32_t nbuf) {
   if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
   if (nbuf != 1 && nbuf != 2) return fail(FFTB_ERR_INVALID_ARG, "slab buffers must be 1 or 2");
-  if (p->a_glob) return fail(FFTB_ERR_UNSUPPORTED, "this plan keeps its slab planes in global memory");
-  if (plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, nbuf) > kSmemLimit)
+  if (!p->a_glob && plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, nbuf) > kSmemLimit)
     return fail(FFTB_ERR_UNSUPPORTED, "two slab planes do not fit in shared memory for this plan");
   if (nbuf == p->a_bufs) return FFTB_OK;
   const int old = p->a_bufs;
@@ -1024,7 +1028,7 @@ fftb_status resize_T(fftb_plan_s* p, int chunk) {
 // Puts a candidate on the plan (slab buffers first: they change the
 // resident CTAs per SM).
 fftb_status apply_choice(fftb_plan_s* p, const TuneChoice& c) {
-  if (c.a_bufs != p->a_bufs && !p->a_glob) {
+  if (c.a_bufs != p->a_bufs) {
     const int old = p->a_bufs;
     p->a_bufs = c.a_bufs;
     fftb_status st = configure_planes(p);
@@ -1143,9 +1147,10 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   // stage 1: kernel variant (slab-plane buffers, prefetch level), each with a
   // full wave of persistent plane CTAs and the plan's chunk
   std::vector<int> nbufs = {saved.a_bufs};
-  if (!p->a_glob) {
+  {
     const int other = 3 - saved.a_bufs;
-    if (plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, other) <= kSmemLimit) nbufs.push_back(other);
+    if (p->a_glob || plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, other) <= kSmemLimit)
+      nbufs.push_back(other);
   }
   for (int nb : nbufs) {
     if (st != FFTB_OK) break;

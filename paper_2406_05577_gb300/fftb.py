@@ -57,6 +57,7 @@ class fftb_plan_info_t(ctypes.Structure):
         ("prefetch", ctypes.c_int32),
         ("slab_buffers", ctypes.c_int32),
         ("tensor_core_planes", ctypes.c_int32),
+        ("slab_planes_global", ctypes.c_int32),
     ]
 
 

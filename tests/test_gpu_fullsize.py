@@ -173,7 +173,7 @@ def test_256_roundtrip_paper_shape(F, prec, tol):
     import torch
     n, r, bands = (256, 256, 256), 64.0, 2
     plan = F.Plan(n, "roundtrip", prec, radius=r, bands=[bands])
-    assert plan.info["slab_buffers"] == 0
+    assert plan.info["slab_planes_global"] == 1
     g = plan.sphere(0)
     assert len(g) == 1097917
     cd = np.complex128 if prec == "fp64" else np.complex64
