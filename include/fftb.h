@@ -108,6 +108,10 @@ typedef struct {
   int32_t slab_planes_global; /* 1: the slab planes live in a per-CTA block of global
                               memory (planes too large for shared memory: FP64 from
                               160, any precision at 256), 0: in shared memory          */
+  int32_t radix_schedule_plane; /* plane stages whose y/x lines use the alternative
+                              radix schedule (fftb_plan_set_radix_schedule, or the
+                              autotuner per stage): bit 0 G->r, bit 1 r->G, bit 2 apply */
+  int32_t radix_schedule_stick; /* the same for the z lines                            */
 } fftb_plan_info_t;
 
 /* Builds the spheres, stick/slab tables and twiddles on the host, uploads
@@ -185,7 +189,8 @@ fftb_status fftb_plan_stage_times(fftb_plan plan, double* ms, int64_t* launches)
 fftb_status fftb_plan_set_graph(fftb_plan plan, int32_t enable);
 
 /* Autotuner: times the candidate schedules of this plan -- first the kernel
- * variant (slab-plane buffers, prefetch level), then bands per launch chunk,
+ * variant (slab-plane buffers, prefetch level, radix schedules of the plane
+ * and z lines), then bands per launch chunk,
  * persistent CTAs of the plane stage and z-stage CTAs -- with `trials` timed
  * executes each on device buffers it allocates and frees (at most 4 GiB;
  * larger batches are tuned on a prefix of the bands), keeps the fastest and
@@ -217,6 +222,17 @@ fftb_status fftb_plan_set_prefetch(fftb_plan plan, int32_t level);
  * both. Errors: INVALID_ARG for a count other than 1 or 2; UNSUPPORTED when
  * 2 do not fit in shared memory. */
 fftb_status fftb_plan_set_slab_buffers(fftb_plan plan, int32_t nbuf);
+
+/* Radix schedule of the FP32 line FFTs: 0 the default, 1 the alternative for
+ * the lengths that have one (64 = 16x4, 96 = 12x8, 128 = 8x16, 160 = 10x4x4;
+ * the defaults are 8x8, 6x4x4, 16x8, 4x4x2x5), separately for the y/x lines of
+ * the plane stages (here all three at once; the autotuner chooses per stage)
+ * and the z lines. The alternative plane schedule excludes the bulk-copy
+ * prefetch. Resets the persistent CTAs to one full wave; fftb_plan_autotune
+ * also tries the schedules. Errors: INVALID_ARG for
+ * values other than 0/1; UNSUPPORTED where no alternative exists (other
+ * lengths, FP64, MIXED_TC plane stages, slab planes in global memory). */
+fftb_status fftb_plan_set_radix_schedule(fftb_plan plan, int32_t plane, int32_t stick);
 
 /* Device status. Every wait of a plane kernel on an asynchronous copy gives
  * up after one second; the CTA then lets its copies in flight land, leaves,

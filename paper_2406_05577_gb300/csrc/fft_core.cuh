@@ -155,6 +155,56 @@ template <int S, typename C> __device__ __forceinline__ void dft16(C* v) {
   }
 }
 
+// radix 10 = 2 x 5 (Cooley-Tukey): DFT5 of the even and of the odd inputs,
+// twiddle the odd outputs by W10^k, then radix-2 butterflies (W10^(k+5) = -W10^k).
+template <int S, typename C> __device__ __forceinline__ void dft10(C* v) {
+  using T = decltype(C::x);
+  const T c1 = T(0.80901699437494742410229342), s1 = T(0.58778525229247312916870595);  // 36 degrees
+  const T c2 = T(0.30901699437494742410229342), s2 = T(0.95105651629515357211643933);  // 72 degrees
+  C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], e4 = v[8];
+  C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7], o4 = v[9];
+  dft5<S>(e0, e1, e2, e3, e4);
+  dft5<S>(o0, o1, o2, o3, o4);
+  // W10^k = cos + S j sin of 2 pi k / 10
+  auto w = [&](C a, T cr, T si) { return mk(a.x * cr - a.y * (T(S) * si), a.x * (T(S) * si) + a.y * cr); };
+  o1 = w(o1, c1, s1);
+  o2 = w(o2, c2, s2);
+  o3 = w(o3, -c2, s2);
+  o4 = w(o4, -c1, s1);
+  v[0] = e0 + o0; v[5] = e0 - o0;
+  v[1] = e1 + o1; v[6] = e1 - o1;
+  v[2] = e2 + o2; v[7] = e2 - o2;
+  v[3] = e3 + o3; v[8] = e3 - o3;
+  v[4] = e4 + o4; v[9] = e4 - o4;
+}
+
+// radix 12 = 4 x 3: DFT4 over n1 for each n2 (inputs 3 n1 + n2), twiddle by
+// W12^(n2 k1), DFT3 over n2, outputs k1 + 4 k2.
+template <int S, typename C> __device__ __forceinline__ void dft12(C* v) {
+  using T = decltype(C::x);
+  const T r3 = T(0.86602540378443864676372317), h = T(0.5);
+  C y[3][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 3; ++n2) {
+    C a = v[n2], b = v[3 + n2], c = v[6 + n2], d = v[9 + n2];
+    dft4<S>(a, b, c, d);
+    y[n2][0] = a; y[n2][1] = b; y[n2][2] = c; y[n2][3] = d;
+  }
+  auto w = [&](C a, T cr, T si) { return mk(a.x * cr - a.y * (T(S) * si), a.x * (T(S) * si) + a.y * cr); };
+  y[1][1] = w(y[1][1], r3, h);    // W12^1
+  y[1][2] = w(y[1][2], h, r3);    // W12^2
+  y[1][3] = mulj<S>(y[1][3]);     // W12^3
+  y[2][1] = w(y[2][1], h, r3);    // W12^2
+  y[2][2] = w(y[2][2], -h, r3);   // W12^4
+  y[2][3] = mk(-y[2][3].x, -y[2][3].y);  // W12^6
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C a = y[0][k1], b = y[1][k1], c = y[2][k1];
+    dft3<S>(a, b, c);
+    v[k1] = a; v[k1 + 4] = b; v[k1 + 8] = c;
+  }
+}
+
 template <int R, int S, typename C> __device__ __forceinline__ void dft(C* v) {
   if constexpr (R == 2) dft2<S>(v[0], v[1]);
   else if constexpr (R == 3) dft3<S>(v[0], v[1], v[2]);
@@ -162,6 +212,8 @@ template <int R, int S, typename C> __device__ __forceinline__ void dft(C* v) {
   else if constexpr (R == 5) dft5<S>(v[0], v[1], v[2], v[3], v[4]);
   else if constexpr (R == 6) dft6<S>(v);
   else if constexpr (R == 8) dft8<S>(v);
+  else if constexpr (R == 10) dft10<S>(v);
+  else if constexpr (R == 12) dft12<S>(v);
   else if constexpr (R == 16) dft16<S>(v);
   else static_assert(R == 2, "unsupported radix");
 }

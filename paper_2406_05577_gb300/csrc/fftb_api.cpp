@@ -128,6 +128,11 @@ struct fftb_plan_s {
   bool pf_fit[3] = {false, false, false};
   int pf_occ[3] = {0, 0, 0};
   int pf_level = 1;
+  // alternative radix schedules (FP32): available, resident CTAs, in use
+  bool alt_plane_ok = false, alt_stick_ok = false;
+  int alt_plane_occ[3] = {0, 0, 0};
+  int alt_stick_occ = 0;
+  int sched_plane = 0, sched_stick = 0;  // plane: bit i for mode index i (G->r, r->G, apply)
   // MIXED_TC plane stages on the 5th-generation tensor cores (grids up to
   // 64): G->r and r->G use them, the z stage then runs in FP32
   bool tc5 = false;
@@ -150,11 +155,16 @@ namespace {
 
 // the plane stage of mode index i (G->r, r->G, apply) prefetches
 bool pf_active(const fftb_plan_s* p, int i) {
-  if (!p->pf_fit[i] || p->pf_level == 0) return false;
+  if (!p->pf_fit[i] || p->pf_level == 0 || ((p->sched_plane >> i) & 1)) return false;
   return p->pf_level == 2 || p->pf_occ[i] >= p->plane_occ[i];
 }
 // resident plane CTAs per SM of the kernel mode index i uses
-int occ_in_use(const fftb_plan_s* p, int i) { return pf_active(p, i) ? p->pf_occ[i] : p->plane_occ[i]; }
+int occ_in_use(const fftb_plan_s* p, int i) {
+  if ((p->sched_plane >> i) & 1) return p->alt_plane_occ[i];
+  return pf_active(p, i) ? p->pf_occ[i] : p->plane_occ[i];
+}
+// persistent z-stage CTAs of one full wave for the schedule in use
+int stick_wave(const fftb_plan_s* p) { return p->sms * (p->sched_stick ? p->alt_stick_occ : p->stick_occ); }
 
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -184,6 +194,20 @@ fftb_status configure_planes(fftb_plan_s* p) {
       p->pf_fit[i] = p->pf_occ[i] >= 1;
     }
   }
+  // the alternative radix schedule of the plane length (FP32, slab planes in shared memory)
+  p->alt_plane_ok = false;
+  if (p->prec_kernel == P_F32 && !p->a_glob && alt_schedule(p->n[0]) &&
+      plane_alt_smem(p->n[0], p->xmax, p->a_bufs) <= kSmemLimit) {
+    e = prepare_alt(p->n[0], 0, p->xmax, p->a_bufs);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    bool ok = true;
+    for (int i = 0; i < 3; ++i) {
+      p->alt_plane_occ[i] = plane_alt_occupancy(modes[i], p->n[0], p->xmax, p->a_bufs);
+      ok = ok && p->alt_plane_occ[i] >= 1;
+    }
+    p->alt_plane_ok = ok;
+  }
+  if (!p->alt_plane_ok) p->sched_plane = 0;
   for (int i = 0; i < 3; ++i) p->plane_ctas[i] = p->sms * occ_in_use(p, i);
   return FFTB_OK;
 }
@@ -472,6 +496,12 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
     }
   }
   p->stick_occ = std::max(1, stick_occupancy(p->stick_prec, p->n[2]));
+  if (p->stick_prec == P_F32 && alt_schedule(p->n[2])) {
+    e = prepare_alt(0, p->n[2], 0, 1);
+    if (e != cudaSuccess) { release(p); return cuda_fail(e, "kernel attributes"); }
+    p->alt_stick_occ = stick_alt_occupancy(p->n[2]);
+    p->alt_stick_ok = p->alt_stick_occ >= 1;
+  }
   p->tiles = sms * p->stick_occ;  // z stage: one wave of persistent CTAs (the autotuner may pick one warp per task pair)
   e = cudaHostAlloc(reinterpret_cast<void**>(&p->h_status), sizeof(int32_t), cudaHostAllocMapped);
   if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaHostAlloc status word failed"); }
@@ -535,6 +565,8 @@ FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) 
   info->slab_buffers = p->a_bufs;
   info->slab_planes_global = p->a_glob ? 1 : 0;
   info->tensor_core_planes = p->tc5 ? 3 : 0;
+  info->radix_schedule_plane = p->sched_plane;
+  info->radix_schedule_stick = p->sched_stick;
   return FFTB_OK;
 }
 
@@ -573,12 +605,15 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
   // bulk copies read the cube from 16-byte aligned rows
   const bool cube_in_16 = (reinterpret_cast<uintptr_t>(L.cube_in) % 16) == 0;
   switch (kind) {
-    case K_STICK_G2R: e = launch_stick(p->stick_prec, M_G2R, L, p->tiles); break;
+    case K_STICK_G2R:
+      e = p->sched_stick ? launch_stick_alt(M_G2R, L, p->tiles) : launch_stick(p->stick_prec, M_G2R, L, p->tiles);
+      break;
     case K_PLANE_G2R: {
       Launch Lp = L;
       Lp.plane_ctas = p->plane_ctas[0];
       Lp.pf = pf_active(p, 0);
       if (p->tc5) e = tc5_launch(M_G2R, Lp, p->tc5g[0], p->tc5_ctas);
+      else if (p->sched_plane & 1) e = launch_plane_alt(M_G2R, Lp);
       else e = Lp.pf ? launch_plane_pf(M_G2R, Lp) : launch_plane(pk, M_G2R, Lp);
       break;
     }
@@ -587,15 +622,19 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
       Lp.plane_ctas = p->plane_ctas[1];
       Lp.pf = pf_active(p, 1) && cube_in_16;
       if (p->tc5 && cube_in_16) e = tc5_launch(M_R2G, Lp, p->tc5g[1], p->tc5_ctas);
+      else if (p->sched_plane & 2) e = launch_plane_alt(M_R2G, Lp);
       else e = Lp.pf ? launch_plane_pf(M_R2G, Lp) : launch_plane(pk, M_R2G, Lp);
       break;
     }
-    case K_STICK_R2G: e = launch_stick(p->stick_prec, M_R2G, L, p->tiles); break;
+    case K_STICK_R2G:
+      e = p->sched_stick ? launch_stick_alt(M_R2G, L, p->tiles) : launch_stick(p->stick_prec, M_R2G, L, p->tiles);
+      break;
     default: {
       Launch Lp = L;
       Lp.plane_ctas = p->plane_ctas[2];
       Lp.pf = pf_active(p, 2);
-      e = Lp.pf ? launch_plane_pf(M_APPLY, Lp) : launch_plane(pk, M_APPLY, Lp);
+      if (p->sched_plane & 4) e = launch_plane_alt(M_APPLY, Lp);
+      else e = Lp.pf ? launch_plane_pf(M_APPLY, Lp) : launch_plane(pk, M_APPLY, Lp);
       break;
     }
   }
@@ -861,6 +900,23 @@ FFTB_EXPORT fftb_status fftb_plan_set_slab_buffers(fftb_plan p, int32_t nbuf) {
   return FFTB_OK;
 }
 
+FFTB_EXPORT fftb_status fftb_plan_set_radix_schedule(fftb_plan p, int32_t plane, int32_t stick) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (plane < 0 || plane > 1 || stick < 0 || stick > 1) return fail(FFTB_ERR_INVALID_ARG, "schedule must be 0 or 1");
+  if (plane && !p->alt_plane_ok) return fail(FFTB_ERR_UNSUPPORTED, "no alternative radix schedule for this plane stage");
+  if (stick && !p->alt_stick_ok) return fail(FFTB_ERR_UNSUPPORTED, "no alternative radix schedule for this z stage");
+  const bool stick_wave_before = p->tiles == stick_wave(p);
+  p->sched_plane = plane ? 7 : 0;
+  p->sched_stick = stick;
+  if (stick_wave_before) p->tiles = stick_wave(p);
+  for (int i = 0; i < 3; ++i) p->plane_ctas[i] = p->sms * occ_in_use(p, i);
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  return FFTB_OK;
+}
+
 FFTB_EXPORT fftb_status fftb_plan_inject(fftb_plan p, int32_t flags) {
   if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
   if (flags & ~FFTB_INJECT_SKIP_FIRST_PREFETCH) return fail(FFTB_ERR_INVALID_ARG, "unknown injection flag");
@@ -975,6 +1031,7 @@ std::string tune_key(const fftb_plan_s* p) {
 struct TuneChoice {
   int chunk = 1, tiles = 0, level = 1, a_bufs = 2;
   int ctas[3] = {0, 0, 0};  // -1: one full wave of the kernel in use
+  int sched_plane = 0, sched_stick = 0;  // radix schedule variants
 };
 
 TuneChoice current_choice(const fftb_plan_s* p) {
@@ -983,6 +1040,8 @@ TuneChoice current_choice(const fftb_plan_s* p) {
   c.tiles = p->tiles;
   c.level = p->pf_level;
   c.a_bufs = p->a_bufs;
+  c.sched_plane = p->sched_plane;
+  c.sched_stick = p->sched_stick;
   for (int i = 0; i < 3; ++i) c.ctas[i] = p->plane_ctas[i];
   return c;
 }
@@ -997,8 +1056,10 @@ bool tune_cache_lookup(const std::string& key, TuneChoice* out) {
     std::istringstream ls(line);
     std::string k;
     TuneChoice c;
-    if ((ls >> k >> c.chunk >> c.ctas[0] >> c.ctas[1] >> c.ctas[2] >> c.tiles >> c.level >> c.a_bufs) && k == key &&
-        c.chunk >= 1 && c.level >= 0 && c.level <= 2 && (c.a_bufs == 1 || c.a_bufs == 2)) {
+    if ((ls >> k >> c.chunk >> c.ctas[0] >> c.ctas[1] >> c.ctas[2] >> c.tiles >> c.level >> c.a_bufs >>
+         c.sched_plane >> c.sched_stick) &&
+        k == key && c.chunk >= 1 && c.level >= 0 && c.level <= 2 && (c.a_bufs == 1 || c.a_bufs == 2) &&
+        c.sched_plane >= 0 && c.sched_plane <= 7 && (c.sched_stick == 0 || c.sched_stick == 1)) {
       *out = c;
       found = true;  // the last entry wins
     }
@@ -1011,7 +1072,7 @@ void tune_cache_store(const std::string& key, const TuneChoice& c) {
   if (!path || !*path) return;
   std::ofstream f(path, std::ios::app);
   f << key << " " << c.chunk << " " << c.ctas[0] << " " << c.ctas[1] << " " << c.ctas[2] << " " << c.tiles << " "
-    << c.level << " " << c.a_bufs << "\n";
+    << c.level << " " << c.a_bufs << " " << c.sched_plane << " " << c.sched_stick << "\n";
 }
 
 fftb_status resize_T(fftb_plan_s* p, int chunk) {
@@ -1041,8 +1102,10 @@ fftb_status apply_choice(fftb_plan_s* p, const TuneChoice& c) {
   fftb_status st = resize_T(p, c.chunk);
   if (st != FFTB_OK) return st;
   p->chunk = c.chunk;
-  p->tiles = c.tiles;
   p->pf_level = c.level;
+  p->sched_plane = p->alt_plane_ok ? c.sched_plane : 0;
+  p->sched_stick = (c.sched_stick && p->alt_stick_ok) ? 1 : 0;
+  p->tiles = c.tiles < 0 ? stick_wave(p) : c.tiles;
   for (int i = 0; i < 3; ++i) p->plane_ctas[i] = c.ctas[i] >= 0 ? c.ctas[i] : p->sms * occ_in_use(p, i);
   return FFTB_OK;
 }
@@ -1152,22 +1215,38 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
     if (p->a_glob || plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, other) <= kSmemLimit)
       nbufs.push_back(other);
   }
+  std::vector<int> plane_scheds = {0}, stick_scheds = {0};
+  if (p->alt_stick_ok) stick_scheds.push_back(1);
   for (int nb : nbufs) {
     if (st != FFTB_OK) break;
-    std::vector<int> masks;
-    for (int lv : {saved.level, 0, 1, 2}) {
-      TuneChoice c = saved;
-      c.a_bufs = nb;
-      c.level = lv;
-      c.ctas[0] = c.ctas[1] = c.ctas[2] = -1;  // one full wave of the variant
-      st = apply_choice(p, c);
-      if (st != FFTB_OK) break;
-      int mask = 0;
-      for (int i = 0; i < 3; ++i)
-        if (pf_active(p, i)) mask |= 1 << i;
-      if (std::find(masks.begin(), masks.end(), mask) != masks.end()) continue;
-      masks.push_back(mask);
-      st = trial(c);
+    for (int ss : stick_scheds) {
+      std::vector<int> masks;  // kernel choices already timed for this slab-buffer count
+      // plane schedule per stage the direction uses (bits: G->r 1, r->G 2, apply 4)
+      const int used = p->dir == FFTB_G_TO_R ? 1 : p->dir == FFTB_R_TO_G ? 2 : p->dir == FFTB_APPLY_LOCAL ? 4 : 3;
+      std::vector<int> sps;
+      for (int m = 0; m <= 7; ++m)
+        if ((m & ~used) == 0 && (m == 0 || p->alt_plane_ok)) sps.push_back(m);
+      for (int sp : sps) {
+        for (int lv : {saved.level, 0, 1, 2}) {
+          TuneChoice c = saved;
+          c.a_bufs = nb;
+          c.level = lv;
+          c.sched_plane = sp;
+          c.sched_stick = ss;
+          c.tiles = c.tiles ? -1 : 0;              // z-stage: the same kind, one full wave of its schedule
+          c.ctas[0] = c.ctas[1] = c.ctas[2] = -1;  // one full wave of the variant
+          st = apply_choice(p, c);
+          if (st != FFTB_OK) break;
+          int mask = p->sched_plane << 3;
+          for (int i = 0; i < 3; ++i)
+            if (pf_active(p, i)) mask |= 1 << i;
+          if (std::find(masks.begin(), masks.end(), mask) != masks.end()) continue;
+          masks.push_back(mask);
+          st = trial(current_choice(p));
+          if (st != FFTB_OK) break;
+        }
+        if (st != FFTB_OK) break;
+      }
       if (st != FFTB_OK) break;
     }
   }
@@ -1184,7 +1263,7 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
     TuneChoice c = variant;
     c.chunk = chunks[k / (2 * mults.size())];
     const int m = mults[(k / 2) % mults.size()];
-    c.tiles = (k & 1) ? p->sms * p->stick_occ : 0;
+    c.tiles = (k & 1) ? stick_wave(p) : 0;
     for (int i = 0; i < 3; ++i) c.ctas[i] = m == 0 ? 0 : p->sms * std::min(m, occ_in_use(p, i));
     st = trial(c);
   }

@@ -104,6 +104,16 @@ size_t plane_pf_smem(int mode, int n0, int n1, int xmax, int a_bufs, int tp);
 cudaError_t prepare_plane_pf(int mode, int n0, int n1, int xmax, int a_bufs, int tp);
 int plane_pf_occupancy(int mode, int n0, int n1, int xmax, int a_bufs, int tp);
 cudaError_t launch_plane_pf(int mode, const Launch& L);
+// FP32 kernels with the alternative radix schedule of a length (k_f32_alt.cu;
+// lengths 64, 96, 128, 160): whether n has one, shared memory, kernel
+// attributes, resident CTAs per SM, launches.
+bool alt_schedule(int n);
+size_t plane_alt_smem(int n, int xmax, int a_bufs);
+cudaError_t prepare_alt(int n0, int n2, int xmax, int a_bufs);
+int plane_alt_occupancy(int mode, int n, int xmax, int a_bufs);
+int stick_alt_occupancy(int n);
+cudaError_t launch_plane_alt(int mode, const Launch& L);
+cudaError_t launch_stick_alt(int mode, const Launch& L, int ctas);
 // MIXED_TC plane stage on the 5th-generation tensor cores (k_tc5.cu): the
 // union over k-points of the occupied x values [xlo, xlo + xu) and of the
 // stick y values [ylo, ylo + yu) (signed grid indices), and the device image

@@ -40,10 +40,12 @@ namespace fftb {
 // lanes index the coefficient list directly; otherwise the warp scatters
 // (gathers) its sticks' entries through zeroed scratch rows.
 constexpr int STICK_NW = 8;
-template <int N2> __host__ __device__ constexpr int stick_tile_c2() { return STICK_NW * (32 / Line<N2>::G); }
-template <typename T, int N2> constexpr size_t stick_smem_c() {
+template <int N2, int V = 0> __host__ __device__ constexpr int stick_tile_c2() {
+  return STICK_NW * (32 / Line<N2, V>::G);
+}
+template <typename T, int N2, int V = 0> constexpr size_t stick_smem_c() {
   using C = typename cplx<T>::type;
-  return sizeof(C) * ((size_t)STICK_NW * (32 / Line<N2>::G) * Line<N2>::PITCH + N2);
+  return sizeof(C) * ((size_t)STICK_NW * (32 / Line<N2, V>::G) * Line<N2, V>::PITCH + N2);
 }
 
 // resident z-stage CTAs per SM the register allocation must allow (FP32: two,
@@ -56,10 +58,10 @@ template <typename T> __host__ __device__ constexpr int stick_minb() {
 #endif
 }
 
-template <typename T, int N2, int MODE, bool TC = false>
+template <typename T, int N2, int MODE, bool TC = false, int V = 0>
 __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(const Launch L) {
   using C = typename cplx<T>::type;
-  using LZ = Line<N2>;
+  using LZ = Line<N2, V>;
   constexpr int WZ = 32 / LZ::G, EZ = LZ::E, NT = STICK_NW * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
@@ -251,10 +253,10 @@ template <typename T, int N0> __host__ __device__ constexpr int plane_minb() {
 }
 
 __host__ __device__ constexpr int a_pitch(int x) { return x + ((2 - x % 16) + 16) % 16; }
-template <int N0, int N1> __host__ __device__ constexpr int plane_scratch() {
-  return (32 / Line<N1>::G) * Line<N1>::PITCH > (32 / Line<N0>::G) * Line<N0>::PITCH
-             ? (32 / Line<N1>::G) * Line<N1>::PITCH
-             : (32 / Line<N0>::G) * Line<N0>::PITCH;
+template <int N0, int N1, int V = 0> __host__ __device__ constexpr int plane_scratch() {
+  return (32 / Line<N1, V>::G) * Line<N1, V>::PITCH > (32 / Line<N0, V>::G) * Line<N0, V>::PITCH
+             ? (32 / Line<N1, V>::G) * Line<N1, V>::PITCH
+             : (32 / Line<N0, V>::G) * Line<N0, V>::PITCH;
 }
 
 // Row pitch (elements) of cube rows staged in shared memory by the r -> G
@@ -278,11 +280,11 @@ template <typename T, int N0, int N1> size_t plane_pf_bytes(int mode, int tp) {
   if (mode == M_R2G) return sizeof(C) * (size_t)NW * WX * stage_pitch<C>(N0) + 8 * NW;
   return sizeof(C) * (size_t)tp + 16;
 }
-template <typename T, int N0, int N1> size_t plane_smem_c(int xmax, int a_bufs, bool ag = false, int pf_mode = 0,
-                                                          int tp = 0) {
+template <typename T, int N0, int N1, int V = 0>
+size_t plane_smem_c(int xmax, int a_bufs, bool ag = false, int pf_mode = 0, int tp = 0) {
   using C = typename cplx<T>::type;
-  return sizeof(C) * ((ag ? 0 : (size_t)a_bufs * N1 * a_pitch(xmax)) + (size_t)PlaneCfg<T>::NW * plane_scratch<N0, N1>() +
-                      N0 + N1) +
+  return sizeof(C) * ((ag ? 0 : (size_t)a_bufs * N1 * a_pitch(xmax)) +
+                      (size_t)PlaneCfg<T>::NW * plane_scratch<N0, N1, V>() + N0 + N1) +
          plane_pf_bytes<T, N0, N1>(pf_mode, tp);
 }
 
@@ -298,15 +300,15 @@ template <int E> struct XiPack {
 // by the warp itself once it has read the current ones), completed on
 // mbarriers. A wait that runs out sets the plan's status word; the CTA then
 // leaves at the next block barrier, after its copies in flight have landed.
-template <typename T, int N0, int N1, int MODE, bool TC = false, bool AG = false, bool PF = false>
+template <typename T, int N0, int N1, int MODE, bool TC = false, bool AG = false, bool PF = false, int V = 0>
 __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k_plane(const Launch L) {
   using C = typename cplx<T>::type;
-  using LY = Line<N1>;
-  using LX = Line<N0>;
+  using LY = Line<N1, V>;
+  using LX = Line<N0, V>;
   constexpr int NW = PlaneCfg<T>::NW, NT = NW * 32;
   constexpr int WY = 32 / LY::G, WX = 32 / LX::G;   // lines per warp
   constexpr int EY = LY::E, EX = LX::E;
-  constexpr int SCR = plane_scratch<N0, N1>();
+  constexpr int SCR = plane_scratch<N0, N1, V>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
 
   const int n2 = L.g.n2;

@@ -38,6 +38,22 @@ FFTB_LP(160, 20, 4, 4, 2, 5);
 FFTB_LP(256, 16, 16, 16, 0, 0);
 #undef FFTB_LP
 
+// Schedule variants the autotuner may pick instead (V = 1): a different
+// radix order or element count per lane for the same length.
+template <int N, int V> struct LPV : LP<N> {};
+template <int N> struct has_alt_schedule { static constexpr bool value = false; };
+#define FFTB_LPV(N_, E_, R0, R1, R2, R3)                                      \
+  template <> struct LPV<N_, 1> {                                           \
+    static constexpr int E = E_;                                            \
+    static constexpr int R[4] = {R0, R1, R2, R3};                           \
+  };                                                                        \
+  template <> struct has_alt_schedule<N_> { static constexpr bool value = true; }
+FFTB_LPV(64, 16, 16, 4, 0, 0);
+FFTB_LPV(96, 24, 12, 8, 0, 0);
+FFTB_LPV(128, 16, 8, 16, 0, 0);
+FFTB_LPV(160, 20, 10, 4, 4, 0);
+#undef FFTB_LPV
+
 // ----------------------------------------------------------- tensor cores
 // A radix-8 pass as a dense product on the tensor cores (split precision):
 // 16 butterflies (rows) x 8 complex inputs = a 16 x 16 real matrix A, the
@@ -71,25 +87,26 @@ __device__ __forceinline__ void row_scale(float m, float& s, float& inv) {
   inv = __int_as_float((254 - es) << 23);         // 2^-(es - 127)
 }
 
-template <int N> struct Line {
-  static constexpr int E = LP<N>::E;
+template <int N, int V = 0> struct Line {
+  using LPN = LPV<N, V>;
+  static constexpr int E = LPN::E;
   static constexpr int G = N / E;
-  static constexpr int NP = LP<N>::R[1] == 0 ? 1 : LP<N>::R[2] == 0 ? 2 : LP<N>::R[3] == 0 ? 3 : 4;
-  static constexpr int R0 = LP<N>::R[0];
-  static constexpr int RL = LP<N>::R[NP - 1];
+  static constexpr int NP = LPN::R[1] == 0 ? 1 : LPN::R[2] == 0 ? 2 : LPN::R[3] == 0 ? 3 : 4;
+  static constexpr int R0 = LPN::R[0];
+  static constexpr int RL = LPN::R[NP - 1];
   static constexpr int PITCH = wpitch(N);
   static_assert(32 % G == 0, "lanes per line must divide the warp");
-  static_assert(R0 * (NP > 1 ? LP<N>::R[1] : 1) * (NP > 2 ? LP<N>::R[2] : 1) * (NP > 3 ? LP<N>::R[3] : 1) == N,
+  static_assert(R0 * (NP > 1 ? LPN::R[1] : 1) * (NP > 2 ? LPN::R[2] : 1) * (NP > 3 ? LPN::R[3] : 1) == N,
                 "radix schedule must multiply to N");
 
   // position of v[m * R0 + j] before run(), and of v[m * RL + j] after it
   __device__ __forceinline__ static int first_pos(int g, int m, int j) { return g + m * G + j * (N / R0); }
   __device__ __forceinline__ static int last_pos(int g, int m, int j) { return g + m * G + j * (N / RL); }
 
-  template <int p> __host__ __device__ static constexpr int radix() { return LP<N>::R[p]; }
+  template <int p> __host__ __device__ static constexpr int radix() { return LPN::R[p]; }
   template <int p> __host__ __device__ static constexpr int span() {  // product of radices before p
     int s = 1;
-    for (int q = 0; q < p; ++q) s *= LP<N>::R[q];
+    for (int q = 0; q < p; ++q) s *= LPN::R[q];
     return s;
   }
 
@@ -98,7 +115,7 @@ template <int N> struct Line {
   // R - 1 values in registers for the whole kernel.
   static constexpr bool CACHE1 = NP > 1 && (G % span<1>() == 0);
   template <typename C> struct TwCache {
-    C w[CACHE1 ? LP<N>::R[1] - 1 : 1];
+    C w[CACHE1 ? LPN::R[1] - 1 : 1];
     __device__ __forceinline__ void load(int g, const C* __restrict__ tw) {
       if constexpr (CACHE1) {
         constexpr int R = radix<1>(), P = span<1>(), STEP = N / (P * R);

@@ -1,0 +1,101 @@
+"""Alternative radix schedules (64 = 16x4, 96 = 12x8, 128 = 8x16, 160 =
+10x4x4; radix-10 and radix-12 codelets) against the FP64 oracle, and the
+autotuner's choice among them."""
+import numpy as np
+import pytest
+
+import fftb_inputs as fi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    from paper_2406_05577_gb300 import build
+    build.build()
+    from paper_2406_05577_gb300 import fftb
+    assert torch.cuda.is_available()
+    return fftb
+
+
+def relerr(a, b):
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n,r", [((64, 64, 64), 16.0), ((96, 96, 96), 24.0), ((128, 128, 128), 32.0),
+                                 ((160, 160, 160), 40.0), ((64, 64, 96), 15.0)])
+def test_alternative_schedules_roundtrip(F, n, r):
+    import torch
+    bands = 2
+    plan = F.Plan(n, "roundtrip", "fp32", radius=r, bands=[bands])
+    plan.set_radix_schedule(1, 1)
+    assert plan.info["radix_schedule_plane"] == 7 and plan.info["radix_schedule_stick"] == 1
+    g = plan.sphere(0)
+    c = fi.complex_gaussian((bands, len(g)), 91).astype(np.complex64)
+    x = torch.from_numpy(c.reshape(-1)).cuda()
+    out = torch.empty_like(x)
+    cube = torch.empty(plan.info["cube_elems"], dtype=torch.complex64, device="cuda")
+    plan.execute(x, out, cube)
+    torch.cuda.synchronize()
+    vol = n[0] * n[1] * n[2]
+    c64 = c.astype(np.complex128)
+    assert relerr(out.cpu().numpy(), vol * c64.reshape(-1)) <= 2e-6
+    R = cube[:vol].view(n[2], n[1], n[0]).cpu().numpy().astype(np.complex128)
+    assert relerr(R, oracle.g2r(g, c64[0], n)) <= 2e-6
+
+
+def test_alternative_schedule_apply_and_r2g(F):
+    import torch
+    n, r = (96, 96, 96), 24.0
+    g = oracle.sphere_gvectors(n, r)
+    v = fi.gaussian_potential(n, 16, 4.0, seed=92).astype(np.float32)
+    c = fi.complex_gaussian((3, len(g)), 93).astype(np.complex64)
+    ap = F.Plan(n, "apply", "fp32", radius=r, bands=[3])
+    ap.set_radix_schedule(1, 1)
+    ap.set_potential(torch.from_numpy(v).cuda())
+    out = torch.empty(c.size, dtype=torch.complex64, device="cuda")
+    ap.execute(torch.from_numpy(c.reshape(-1)).cuda(), out)
+    torch.cuda.synchronize()
+    want = oracle.apply_potential(g, c.astype(np.complex128), v.astype(np.float64), n)
+    assert relerr(out.cpu().numpy(), want) <= 2e-6
+    R = fi.complex_gaussian((2, 96, 96, 96), 94).astype(np.complex64)
+    p2 = F.Plan(n, "r2g", "fp32", radius=r, bands=[2])
+    p2.set_radix_schedule(1, 1)
+    o2 = torch.empty(p2.info["sphere_elems"], dtype=torch.complex64, device="cuda")
+    p2.execute(torch.from_numpy(R.reshape(-1)).cuda(), o2)
+    torch.cuda.synchronize()
+    assert relerr(o2.cpu().numpy(), oracle.r2g(g, R.astype(np.complex128), n).reshape(-1)) <= 2e-6
+
+
+def test_schedule_errors_and_autotune(F, tmp_path, monkeypatch):
+    import torch
+    monkeypatch.setenv("FFTB_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    p48 = F.Plan((48, 48, 48), "roundtrip", "fp32", radius=11.0, bands=[1])
+    with pytest.raises(F.FFTBError) as ei:
+        p48.set_radix_schedule(1, 0)
+    assert ei.value.status == F.FFTB_ERR_UNSUPPORTED
+    p64d = F.Plan((64, 64, 64), "roundtrip", "fp64", radius=16.0, bands=[1])
+    with pytest.raises(F.FFTBError):
+        p64d.set_radix_schedule(1, 0)
+    with pytest.raises(F.FFTBError) as ei:
+        p64d.set_radix_schedule(2, 0)
+    assert ei.value.status == F.FFTB_ERR_INVALID_ARG
+    # the autotuner may pick either schedule; the result stays correct and is cached
+    n, r, bands = (128, 128, 128), 32.0, 6
+    plan = F.Plan(n, "roundtrip", "fp32", radius=r, bands=[bands])
+    plan.autotune(2)
+    g = plan.sphere(0)
+    c = fi.complex_gaussian((bands, len(g)), 95).astype(np.complex64)
+    x = torch.from_numpy(c.reshape(-1)).cuda()
+    out = torch.empty_like(x)
+    cube = torch.empty(plan.info["cube_elems"], dtype=torch.complex64, device="cuda")
+    plan.execute(x, out, cube)
+    torch.cuda.synchronize()
+    assert relerr(out.cpu().numpy(), 128 ** 3 * c.reshape(-1).astype(np.complex128)) <= 2e-6
+    line = (tmp_path / "tune.txt").read_text().strip().split()
+    assert 0 <= int(line[-2]) <= 3 and line[-1] in ("0", "1")
+    assert int(line[-2]) == plan.info["radix_schedule_plane"] and int(line[-1]) == plan.info["radix_schedule_stick"]
