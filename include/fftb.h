@@ -112,6 +112,8 @@ typedef struct {
                               radix schedule (fftb_plan_set_radix_schedule, or the
                               autotuner per stage): bit 0 G->r, bit 1 r->G, bit 2 apply */
   int32_t radix_schedule_stick; /* the same for the z lines                            */
+  int32_t dependent_launch;   /* 1: stage kernels use programmatic dependent launch
+                              (fftb_plan_set_pdl, or the autotuner's choice)          */
 } fftb_plan_info_t;
 
 /* Builds the spheres, stick/slab tables and twiddles on the host, uploads
@@ -233,6 +235,13 @@ fftb_status fftb_plan_set_slab_buffers(fftb_plan plan, int32_t nbuf);
  * values other than 0/1; UNSUPPORTED where no alternative exists (other
  * lengths, FP64, MIXED_TC plane stages, slab planes in global memory). */
 fftb_status fftb_plan_set_radix_schedule(fftb_plan plan, int32_t plane, int32_t stick);
+
+/* Programmatic dependent launch between the stage kernels of an execute (on
+ * by default; fftb_plan_autotune measures both and keeps the faster): each kernel may launch while its predecessor drains, runs its
+ * prologue (twiddle tables, barriers, tensor memory) and waits for the
+ * predecessor to complete before touching stage data, so launch latency and
+ * prologues overlap the previous kernel's tail. 0 launches them plainly. */
+fftb_status fftb_plan_set_pdl(fftb_plan plan, int32_t enable);
 
 /* Device status. Every wait of a plane kernel on an asynchronous copy gives
  * up after one second; the CTA then lets its copies in flight land, leaves,

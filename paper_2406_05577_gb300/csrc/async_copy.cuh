@@ -77,6 +77,13 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Programmatic dependent launch: the next kernel in the stream may launch
+// (its CTAs take SMs as this grid's CTAs leave and run their prologue) ...
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// ... and waits here until the previous grid has completed and its memory
+// is visible, before it reads or writes anything a neighbour kernel touches.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Device status value (plan status word): a bounded wait ran out.
 constexpr int STATUS_WAIT_TIMEOUT = 1;
 

@@ -133,6 +133,7 @@ struct fftb_plan_s {
   int alt_plane_occ[3] = {0, 0, 0};
   int alt_stick_occ = 0;
   int sched_plane = 0, sched_stick = 0;  // plane: bit i for mode index i (G->r, r->G, apply)
+  bool pdl = true;                       // programmatic dependent launch between stage kernels
   // MIXED_TC plane stages on the 5th-generation tensor cores (grids up to
   // 64): G->r and r->G use them, the z stage then runs in FP32
   bool tc5 = false;
@@ -567,6 +568,7 @@ FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) 
   info->tensor_core_planes = p->tc5 ? 3 : 0;
   info->radix_schedule_plane = p->sched_plane;
   info->radix_schedule_stick = p->sched_stick;
+  info->dependent_launch = p->pdl ? 1 : 0;
   return FFTB_OK;
 }
 
@@ -659,6 +661,7 @@ static fftb_status enqueue(fftb_plan_s* p, int bands, const void* in, void* out,
   L.a_glob = p->d_A;
   L.inject = p->inject;
   L.status = p->d_status;
+  L.pdl = p->pdl ? 1 : 0;
   L.stream = s;
   for (int b0 = first; b0 < first + bands; b0 += p->chunk) {
     L.band0 = b0;
@@ -917,6 +920,16 @@ FFTB_EXPORT fftb_status fftb_plan_set_radix_schedule(fftb_plan p, int32_t plane,
   return FFTB_OK;
 }
 
+FFTB_EXPORT fftb_status fftb_plan_set_pdl(fftb_plan p, int32_t enable) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (p->pdl != (enable != 0) && p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  p->pdl = enable != 0;
+  return FFTB_OK;
+}
+
 FFTB_EXPORT fftb_status fftb_plan_inject(fftb_plan p, int32_t flags) {
   if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
   if (flags & ~FFTB_INJECT_SKIP_FIRST_PREFETCH) return fail(FFTB_ERR_INVALID_ARG, "unknown injection flag");
@@ -1032,6 +1045,7 @@ struct TuneChoice {
   int chunk = 1, tiles = 0, level = 1, a_bufs = 2;
   int ctas[3] = {0, 0, 0};  // -1: one full wave of the kernel in use
   int sched_plane = 0, sched_stick = 0;  // radix schedule variants
+  int pdl = 1;                           // programmatic dependent launch
 };
 
 TuneChoice current_choice(const fftb_plan_s* p) {
@@ -1042,6 +1056,7 @@ TuneChoice current_choice(const fftb_plan_s* p) {
   c.a_bufs = p->a_bufs;
   c.sched_plane = p->sched_plane;
   c.sched_stick = p->sched_stick;
+  c.pdl = p->pdl ? 1 : 0;
   for (int i = 0; i < 3; ++i) c.ctas[i] = p->plane_ctas[i];
   return c;
 }
@@ -1057,9 +1072,10 @@ bool tune_cache_lookup(const std::string& key, TuneChoice* out) {
     std::string k;
     TuneChoice c;
     if ((ls >> k >> c.chunk >> c.ctas[0] >> c.ctas[1] >> c.ctas[2] >> c.tiles >> c.level >> c.a_bufs >>
-         c.sched_plane >> c.sched_stick) &&
+         c.sched_plane >> c.sched_stick >> c.pdl) &&
         k == key && c.chunk >= 1 && c.level >= 0 && c.level <= 2 && (c.a_bufs == 1 || c.a_bufs == 2) &&
-        c.sched_plane >= 0 && c.sched_plane <= 7 && (c.sched_stick == 0 || c.sched_stick == 1)) {
+        c.sched_plane >= 0 && c.sched_plane <= 7 && (c.sched_stick == 0 || c.sched_stick == 1) &&
+        (c.pdl == 0 || c.pdl == 1)) {
       *out = c;
       found = true;  // the last entry wins
     }
@@ -1072,7 +1088,7 @@ void tune_cache_store(const std::string& key, const TuneChoice& c) {
   if (!path || !*path) return;
   std::ofstream f(path, std::ios::app);
   f << key << " " << c.chunk << " " << c.ctas[0] << " " << c.ctas[1] << " " << c.ctas[2] << " " << c.tiles << " "
-    << c.level << " " << c.a_bufs << " " << c.sched_plane << " " << c.sched_stick << "\n";
+    << c.level << " " << c.a_bufs << " " << c.sched_plane << " " << c.sched_stick << " " << c.pdl << "\n";
 }
 
 fftb_status resize_T(fftb_plan_s* p, int chunk) {
@@ -1105,6 +1121,7 @@ fftb_status apply_choice(fftb_plan_s* p, const TuneChoice& c) {
   p->pf_level = c.level;
   p->sched_plane = p->alt_plane_ok ? c.sched_plane : 0;
   p->sched_stick = (c.sched_stick && p->alt_stick_ok) ? 1 : 0;
+  p->pdl = c.pdl != 0;
   p->tiles = c.tiles < 0 ? stick_wave(p) : c.tiles;
   for (int i = 0; i < 3; ++i) p->plane_ctas[i] = c.ctas[i] >= 0 ? c.ctas[i] : p->sms * occ_in_use(p, i);
   return FFTB_OK;
@@ -1265,6 +1282,14 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
     const int m = mults[(k / 2) % mults.size()];
     c.tiles = (k & 1) ? stick_wave(p) : 0;
     for (int i = 0; i < 3; ++i) c.ctas[i] = m == 0 ? 0 : p->sms * std::min(m, occ_in_use(p, i));
+    st = trial(c);
+  }
+  // stage 3: the best schedule with and without programmatic dependent launch
+  // (early launch helps short stages; on long ones the waiting CTAs can cost
+  // more than the hidden launch latency)
+  if (st == FFTB_OK) {
+    TuneChoice c = best_c;
+    c.pdl = 1 - c.pdl;
     st = trial(c);
   }
   cudaEventDestroy(e0);

@@ -70,6 +70,7 @@ struct Launch {
   int32_t pf;           // plane stage: prefetch its inputs with bulk async copies
   int32_t inject;       // INJECT_* bits (tests of the bounded waits)
   int32_t* status;      // device-visible status word (STATUS_* bits), set on a failed wait
+  int32_t pdl;          // launch with programmatic dependent launch (overlaps launch and prologue)
   cudaStream_t stream;
 };
 

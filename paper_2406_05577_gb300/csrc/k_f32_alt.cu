@@ -18,10 +18,9 @@ template <int N> cudaError_t go_plane_v(int mode, const Launch& L) {
   const int nplanes = L.nb * L.g.n2;
   const dim3 grid(L.plane_ctas > 0 ? min(L.plane_ctas, nplanes) : nplanes);
   constexpr int NT = PlaneCfg<float>::NW * 32;
-  if (mode == M_G2R) k_plane<float, N, N, M_G2R, false, false, false, 1><<<grid, NT, smem, L.stream>>>(L);
-  else if (mode == M_R2G) k_plane<float, N, N, M_R2G, false, false, false, 1><<<grid, NT, smem, L.stream>>>(L);
-  else k_plane<float, N, N, M_APPLY, false, false, false, 1><<<grid, NT, smem, L.stream>>>(L);
-  return cudaGetLastError();
+  if (mode == M_G2R) return launch_k(k_plane<float, N, N, M_G2R, false, false, false, 1>, grid, NT, smem, L, L);
+  if (mode == M_R2G) return launch_k(k_plane<float, N, N, M_R2G, false, false, false, 1>, grid, NT, smem, L, L);
+  return launch_k(k_plane<float, N, N, M_APPLY, false, false, false, 1>, grid, NT, smem, L, L);
 }
 template <int N> cudaError_t go_stick_v(int mode, const Launch& L, int ctas) {
   constexpr int WZ = 32 / Line<N, 1>::G;
@@ -29,9 +28,8 @@ template <int N> cudaError_t go_stick_v(int mode, const Launch& L, int ctas) {
   const int gpb = (L.g.smax + WZ - 1) / WZ;
   const int need = (L.nb * gpb + STICK_NW - 1) / STICK_NW;  // one task per warp
   const dim3 grid(ctas > 0 ? min(ctas, need) : need);
-  if (mode == M_G2R) k_stick<float, N, M_G2R, false, 1><<<grid, STICK_NW * 32, smem, L.stream>>>(L);
-  else k_stick<float, N, M_R2G, false, 1><<<grid, STICK_NW * 32, smem, L.stream>>>(L);
-  return cudaGetLastError();
+  if (mode == M_G2R) return launch_k(k_stick<float, N, M_G2R, false, 1>, grid, STICK_NW * 32, smem, L, L);
+  return launch_k(k_stick<float, N, M_R2G, false, 1>, grid, STICK_NW * 32, smem, L, L);
 }
 template <int N> cudaError_t prep_plane_v(int xmax, int a_bufs) {
   const int s = (int)plane_smem_c<float, N, N, 1>(xmax, a_bufs);

@@ -17,10 +17,9 @@ template <int N> cudaError_t go(int mode, const Launch& L) {
   const int nplanes = L.nb * L.g.n2;
   const dim3 grid(L.plane_ctas > 0 ? min(L.plane_ctas, nplanes) : nplanes);
   constexpr int NT = PlaneCfg<float>::NW * 32;
-  if (mode == M_G2R) pf_kernel<N, M_G2R>()<<<grid, NT, smem, L.stream>>>(L);
-  else if (mode == M_R2G) pf_kernel<N, M_R2G>()<<<grid, NT, smem, L.stream>>>(L);
-  else pf_kernel<N, M_APPLY>()<<<grid, NT, smem, L.stream>>>(L);
-  return cudaGetLastError();
+  if (mode == M_G2R) return launch_k(pf_kernel<N, M_G2R>(), grid, NT, smem, L, L);
+  if (mode == M_R2G) return launch_k(pf_kernel<N, M_R2G>(), grid, NT, smem, L, L);
+  return launch_k(pf_kernel<N, M_APPLY>(), grid, NT, smem, L, L);
 }
 template <int N> cudaError_t prep(int mode, int xmax, int a_bufs, int tp) {
   const int s = (int)plane_smem_c<float, N, N>(xmax, a_bufs, false, mode, tp);

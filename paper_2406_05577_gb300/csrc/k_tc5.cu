@@ -263,8 +263,10 @@ __global__ void __launch_bounds__(TC5_NT, 1) k_plane_tc5(const Launch L, const T
   }
   fence_proxy_async_smem();
   umma::fence_before_sync();
+  pdl_launch_dependents();
   __syncthreads();
   umma::fence_after_sync();
+  pdl_wait();
   const bool w_bad = __syncthreads_or(!mbar_wait(bar_w, 0, WAIT_LIMIT_NS)) != 0;
   const uint32_t tmem = *slot + 256 * pl;
   const uint32_t t_d1 = tmem;  // first product; second products alternate at +64 and +128
@@ -673,9 +675,8 @@ cudaError_t tc5_launch(int mode, const Launch& L, const Tc5Geo& P, int ctas) {
   switch (n) {
 #define C_(N)                                                                                  \
   case N:                                                                                      \
-    if (mode == M_G2R) k_plane_tc5<N, M_G2R><<<grid, TC5_NT, s, L.stream>>>(L, P);              \
-    else k_plane_tc5<N, M_R2G><<<grid, TC5_NT, s, L.stream>>>(L, P);                             \
-    return cudaGetLastError();
+    if (mode == M_G2R) return launch_k(k_plane_tc5<N, M_G2R>, grid, TC5_NT, s, L, L, P);    \
+    return launch_k(k_plane_tc5<N, M_R2G>, grid, TC5_NT, s, L, L, P);
     TC5_SIZES(C_)
 #undef C_
   }

@@ -73,7 +73,9 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
     const C* tw_g = static_cast<const C*>(L.g.tw2);
     for (int m = threadIdx.x; m < N2; m += NT) tw[m] = tw_g[m];
   }
+  pdl_launch_dependents();
   __syncthreads();
+  pdl_wait();
   typename LZ::template TwCache<C> tc;
   tc.load(g, tw);
   typename LZ::template TcW<MODE == M_G2R ? +1 : -1> tcw;
@@ -340,7 +342,9 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
       mbar_init_fence();
     }
   }
+  pdl_launch_dependents();
   __syncthreads();
+  pdl_wait();
   C* rowy = scr + ly * LY::PITCH;
   C* rowx = scr + lx * LX::PITCH;
   typename LY::template TwCache<C> tcy;
@@ -671,6 +675,25 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 }
 
 // ---------------------------------------------------------------- dispatch
+// Launches a stage kernel; with L.pdl the launch allows programmatic
+// dependent launch (every stage kernel starts with pdl_launch_dependents and
+// calls pdl_wait before touching stage data, so neighbours only overlap their
+// launch latency and prologues).
+template <typename... A, typename... B>
+cudaError_t launch_k(void (*kernel)(A...), dim3 grid, dim3 block, size_t smem, const Launch& L, B&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = L.stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = L.pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<B>(args)...);
+}
+
 // Raises a kernel's dynamic shared-memory limit on the current device to at
 // least `bytes`, never lowering it: plans of one grid size but different
 // spheres or buffers share the kernel, and a lower limit set by one plan
@@ -722,9 +745,8 @@ template <typename T, bool TC, int N2> cudaError_t go_stick(int mode, const Laun
   const int gpb = (L.g.smax + (32 / Line<N2>::G) - 1) / (32 / Line<N2>::G);
   const int need = (L.nb * gpb + STICK_NW - 1) / STICK_NW;  // one task per warp
   const dim3 grid(ctas > 0 ? min(ctas, need) : need);
-  if (mode == M_G2R) k_stick<T, N2, M_G2R, TC><<<grid, STICK_NW * 32, smem, L.stream>>>(L);
-  else k_stick<T, N2, M_R2G, TC><<<grid, STICK_NW * 32, smem, L.stream>>>(L);
-  return cudaGetLastError();
+  if (mode == M_G2R) return launch_k(k_stick<T, N2, M_G2R, TC>, grid, STICK_NW * 32, smem, L, L);
+  return launch_k(k_stick<T, N2, M_R2G, TC>, grid, STICK_NW * 32, smem, L, L);
 }
 template <typename T, bool TC, int N> cudaError_t go_plane(int mode, const Launch& L) {
   if constexpr (N >= 128) {
@@ -733,10 +755,9 @@ template <typename T, bool TC, int N> cudaError_t go_plane(int mode, const Launc
       const int nplanes = L.nb * L.g.n2;
       const dim3 grid(min(L.plane_ctas, nplanes));
       constexpr int NT = PlaneCfg<T>::NW * 32;
-      if (mode == M_G2R) k_plane<T, N, N, M_G2R, TC, true><<<grid, NT, smem, L.stream>>>(L);
-      else if (mode == M_R2G) k_plane<T, N, N, M_R2G, TC, true><<<grid, NT, smem, L.stream>>>(L);
-      else k_plane<T, N, N, M_APPLY, TC, true><<<grid, NT, smem, L.stream>>>(L);
-      return cudaGetLastError();
+      if (mode == M_G2R) return launch_k(k_plane<T, N, N, M_G2R, TC, true>, grid, NT, smem, L, L);
+      if (mode == M_R2G) return launch_k(k_plane<T, N, N, M_R2G, TC, true>, grid, NT, smem, L, L);
+      return launch_k(k_plane<T, N, N, M_APPLY, TC, true>, grid, NT, smem, L, L);
     }
   }
   if (L.a_glob) return cudaErrorInvalidValue;
@@ -744,10 +765,9 @@ template <typename T, bool TC, int N> cudaError_t go_plane(int mode, const Launc
   const int nplanes = L.nb * L.g.n2;
   const dim3 grid(L.plane_ctas > 0 ? min(L.plane_ctas, nplanes) : nplanes);
   constexpr int NT = PlaneCfg<T>::NW * 32;
-  if (mode == M_G2R) k_plane<T, N, N, M_G2R, TC><<<grid, NT, smem, L.stream>>>(L);
-  else if (mode == M_R2G) k_plane<T, N, N, M_R2G, TC><<<grid, NT, smem, L.stream>>>(L);
-  else k_plane<T, N, N, M_APPLY, TC><<<grid, NT, smem, L.stream>>>(L);
-  return cudaGetLastError();
+  if (mode == M_G2R) return launch_k(k_plane<T, N, N, M_G2R, TC>, grid, NT, smem, L, L);
+  if (mode == M_R2G) return launch_k(k_plane<T, N, N, M_R2G, TC>, grid, NT, smem, L, L);
+  return launch_k(k_plane<T, N, N, M_APPLY, TC>, grid, NT, smem, L, L);
 }
 template <typename T, bool TC, int N2> cudaError_t prep_stick() {
   const int s = (int)stick_smem_c<T, N2>();

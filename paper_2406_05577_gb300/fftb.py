@@ -60,6 +60,7 @@ class fftb_plan_info_t(ctypes.Structure):
         ("slab_planes_global", ctypes.c_int32),
         ("radix_schedule_plane", ctypes.c_int32),
         ("radix_schedule_stick", ctypes.c_int32),
+        ("dependent_launch", ctypes.c_int32),
     ]
 
 
@@ -89,6 +90,7 @@ EXPORTS = {
     "fftb_plan_check": (ctypes.c_int, [ctypes.c_void_p]),
     "fftb_plan_set_slab_buffers": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fftb_plan_set_radix_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
+    "fftb_plan_set_pdl": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fftb_plan_inject": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fftb_sphere_enumerate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_double,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -243,6 +245,10 @@ def fftb_plan_set_radix_schedule(plan, plane, stick):
     _check(lib().fftb_plan_set_radix_schedule(plan, int(plane), int(stick)))
 
 
+def fftb_plan_set_pdl(plan, enable):
+    _check(lib().fftb_plan_set_pdl(plan, 1 if enable else 0))
+
+
 def fftb_plan_check(plan):
     """Raises FFTBError (status FFTB_ERR_DEVICE_TIMEOUT) if a device wait ran out."""
     _check(lib().fftb_plan_check(plan))
@@ -376,6 +382,10 @@ class Plan:
 
     def set_radix_schedule(self, plane=0, stick=0):
         fftb_plan_set_radix_schedule(self.handle, plane, stick)
+        self.info = fftb_plan_get_info(self.handle)
+
+    def set_pdl(self, enable=True):
+        fftb_plan_set_pdl(self.handle, enable)
         self.info = fftb_plan_get_info(self.handle)
 
     def check(self):
