@@ -20,11 +20,19 @@
  * reverse direction prunes its outputs the same way.
  *
  * Data layout (all complex data interleaved re,im; float for FP32 and
- * MIXED_TC plans, double for FP64 plans):
- *   sphere batch : concatenation over k-points of [B_k][ngw_k]   (band-major)
+ * MIXED_TC plans, double for FP64 plans), fftb_desc.layout = 0 (band-major):
+ *   sphere batch : concatenation over k-points of [B_k][ngw_k]
  *   cube batch   : concatenation over k-points of [B_k][N2][N1][N0] (x fastest,
  *                  Sec. 2.1: n0 is the fastest dimension in memory)
  *   potential V  : real, [N2][N1][N0]
+ * fftb_desc.layout = 1 (batch-fastest: the batch dimension declared first is
+ * the fastest in memory, Sec. 3.3), per k-point:
+ *   sphere batch : concatenation over k-points of [ngw_k][B_k]
+ *   cube batch   : concatenation over k-points of [N2][N1][N0][B_k]
+ * The arithmetic is the same in both layouts (results are bit-identical up to
+ * the permutation); batch-fastest cube rows are read and written point by
+ * point B_k elements apart, so its r -> G stage does not use bulk copies and
+ * MIXED_TC plans run their plane stages on the mma.sync path.
  * Within one k-point the sphere order is the user's list order, or for a
  * cutoff sphere the canonical order: sorted by gy, then gx, then gz, each
  * ascending over signed values (the offset array over the xy projection of
@@ -80,7 +88,7 @@ typedef struct {
                               triples of every k-point, in the order the data uses;
                               copied at plan creation                                */
   const int64_t* g_count;  /* host, n_kpoints sizes of g_list's parts (with g_list)  */
-  int32_t layout;          /* 0 = band-major sphere and cube (the only layout now)   */
+  int32_t layout;          /* 0 = band-major sphere and cube, 1 = batch-fastest      */
   int32_t max_chunk_bands; /* bands per launch chunk; 0 = chosen by the plan         */
 } fftb_desc;
 
@@ -121,8 +129,9 @@ typedef struct {
  * call that allocates device memory or synchronises the device.
  * Errors: INVALID_ARG for a bad description (grid extent outside the
  * supported list, sphere that does not fit the grid and would alias, G
- * outside [-N/2, N/2), duplicate G, negative bands); UNSUPPORTED for a valid
- * request without a kernel; ALLOC; CUDA. *out is NULL on error. */
+ * outside [-N/2, N/2), duplicate G, negative bands, layout other than 0 or
+ * 1); UNSUPPORTED for a valid request without a kernel; ALLOC; CUDA. *out is
+ * NULL on error. */
 fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* desc,
                              fftb_direction direction, fftb_precision precision);
 
@@ -159,7 +168,9 @@ fftb_status fftb_execute(fftb_plan plan, const void* in_dev, void* out_dev,
  * staging, runs the transform, copies the result back and synchronises
  * `stream`. The bands go through in two pieces on three plan-owned
  * streams, so the copy in of one piece, the transform of the previous one
- * and the copy out of the one before that overlap; the call is ordered
+ * and the copy out of the one before that overlap (batch-fastest plans split
+ * only at a k-point boundary, and a single k-point goes in one piece); the
+ * call is ordered
  * after earlier work on `stream` and returns when all of it is done. The
  * staging buffers and streams are created on the first call and kept with
  * the plan. For ROUNDTRIP cube_dev is a device cube batch (may be NULL:
@@ -237,10 +248,11 @@ fftb_status fftb_plan_set_slab_buffers(fftb_plan plan, int32_t nbuf);
 fftb_status fftb_plan_set_radix_schedule(fftb_plan plan, int32_t plane, int32_t stick);
 
 /* Programmatic dependent launch between the stage kernels of an execute (on
- * by default; fftb_plan_autotune measures both and keeps the faster): each kernel may launch while its predecessor drains, runs its
- * prologue (twiddle tables, barriers, tensor memory) and waits for the
- * predecessor to complete before touching stage data, so launch latency and
- * prologues overlap the previous kernel's tail. 0 launches them plainly. */
+ * by default; fftb_plan_autotune measures both and keeps the faster): each
+ * kernel may launch while its predecessor drains, runs its prologue (twiddle
+ * tables, barriers, tensor memory) and waits for the predecessor to complete
+ * before touching stage data, so launch latency and prologues overlap the
+ * previous kernel's tail. 0 launches them plainly. */
 fftb_status fftb_plan_set_pdl(fftb_plan plan, int32_t enable);
 
 /* Device status. Every wait of a plane kernel on an asynchronous copy gives

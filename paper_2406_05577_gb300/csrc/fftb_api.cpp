@@ -87,6 +87,7 @@ struct fftb_plan_s {
   int64_t sphere_elems = 0, cube_elems = 0;
   int32_t smax = 0, xmax = 0, tiles = 0, chunk = 1;
   int32_t tpitch = 2;  // stick-row pitch of T: smax rounded up to even
+  int32_t layout = 0;  // 0 band-major, 1 batch-fastest (band index fastest)
   int device = 0;
   int32_t plane_ctas[3] = {0, 0, 0};  // persistent CTAs: G->r, r->G, apply
   int32_t a_bufs = 2;                 // slab-plane buffers of the plane stage
@@ -157,6 +158,7 @@ namespace {
 // the plane stage of mode index i (G->r, r->G, apply) prefetches
 bool pf_active(const fftb_plan_s* p, int i) {
   if (!p->pf_fit[i] || p->pf_level == 0 || ((p->sched_plane >> i) & 1)) return false;
+  if (i == 1 && p->layout != 0) return false;  // bulk copies take whole band-major cube rows
   return p->pf_level == 2 || p->pf_occ[i] >= p->plane_occ[i];
 }
 // resident plane CTAs per SM of the kernel mode index i uses
@@ -259,7 +261,7 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   for (int i = 0; i < 3; ++i)
     if (d->n[i] < 1) return fail(FFTB_ERR_INVALID_ARG, "grid extents must be >= 1");
   if (d->n_kpoints < 1) return fail(FFTB_ERR_INVALID_ARG, "n_kpoints must be >= 1");
-  if (d->layout != 0) return fail(FFTB_ERR_UNSUPPORTED, "only the band-major layout (0) is implemented");
+  if (d->layout != 0 && d->layout != 1) return fail(FFTB_ERR_INVALID_ARG, "layout must be 0 (band-major) or 1 (batch-fastest)");
   if (d->max_chunk_bands < 0) return fail(FFTB_ERR_INVALID_ARG, "max_chunk_bands must be >= 0");
   if (d->g_list && !d->g_count) return fail(FFTB_ERR_INVALID_ARG, "g_list given without g_count");
   if (!grid_size_supported(d->n[0]) || !grid_size_supported(d->n[1]) || !grid_size_supported(d->n[2]) ||
@@ -271,6 +273,7 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   if (!p) return fail(FFTB_ERR_ALLOC, "host allocation failed");
   std::memcpy(p->n, d->n, sizeof(p->n));
   p->nk = d->n_kpoints;
+  p->layout = d->layout;
   p->dir = dir;
   p->prec = prec;
   p->prec_kernel = (prec == FFTB_FP64) ? P_F64 : (prec == FFTB_MIXED_TC) ? P_TC : P_F32;
@@ -345,11 +348,16 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   for (int k = 0; k < p->nk; ++k) {
     const KGeom& G = p->geo[k];
     const size_t first_band = band.size();
+    // band-major: [B_k][ngw_k] and [B_k][N2][N1][N0]; batch-fastest (Sec. 3.3,
+    // the batch dimension declared first): [ngw_k][B_k] and [N2][N1][N0][B_k]
+    const bool bf = p->layout == 1;
     for (int b = 0; b < p->bands[k]; ++b) {
       BandInfo bi{};
-      bi.sph = sph + (int64_t)b * G.ngw;
+      bi.sph = sph + (bf ? (int64_t)b : (int64_t)b * G.ngw);
+      bi.cube = (int64_t)first_band * vol + (bf ? (int64_t)b : (int64_t)b * vol);
       band.push_back(bi);
     }
+    kinfo[k].bstride = bf ? std::max(p->bands[k], 1) : 1;
     sph += (int64_t)p->bands[k] * G.ngw;
     kinfo[k].S = G.S;
     kinfo[k].X = G.X;
@@ -444,7 +452,8 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
     }
   }
   p->stick_prec = p->prec_kernel;
-  if (p->prec_kernel == P_TC && tc5_supported(p->n[0], p->n[1])) {
+  // the tcgen05 plane kernels read and write band-major cube planes
+  if (p->prec_kernel == P_TC && p->layout == 0 && tc5_supported(p->n[0], p->n[1])) {
     // union over k-points of the occupied x values and the stick y values
     int xlo = 1 << 30, xhi = -(1 << 30), ylo = 1 << 30, yhi = -(1 << 30);
     bool columns_ok = true;
@@ -801,7 +810,23 @@ FFTB_EXPORT fftb_status fftb_execute_host(fftb_plan p, const void* in_host, void
   // measured best on GB300 (more pieces cost more in smaller, less efficient
   // launches than they hide; kernels reading or writing page-locked host
   // memory directly over the CPU-GPU link measured slower than the copies).
-  const int pieces = std::min(2, p->total_bands);
+  // A batch-fastest piece must be whole k-points (a band range of one
+  // k-point is not contiguous there): split at the k-point start nearest the
+  // middle, or not at all.
+  int bounds[3] = {0, p->total_bands / 2, p->total_bands};
+  int pieces = std::min(2, p->total_bands);
+  if (p->layout == 1 && pieces == 2) {
+    int best = 0, b = 0;
+    for (int k = 0; k + 1 < p->nk; ++k) {
+      b += p->bands[k];
+      if (b > 0 && b < p->total_bands &&
+          (best == 0 || std::abs(2 * b - p->total_bands) < std::abs(2 * best - p->total_bands)))
+        best = b;
+    }
+    if (best > 0) bounds[1] = best;
+    else pieces = 1;
+  }
+  if (pieces == 1) bounds[1] = p->total_bands;
   if (!p->hs[0]) {
     for (int i = 0; i < 3; ++i)
       if (cudaStreamCreateWithFlags(&p->hs[i], cudaStreamNonBlocking) != cudaSuccess)
@@ -825,7 +850,7 @@ FFTB_EXPORT fftb_status fftb_execute_host(fftb_plan p, const void* in_host, void
   unsigned char* din = static_cast<unsigned char*>(p->d_stage_in);
   unsigned char* dout = static_cast<unsigned char*>(p->d_stage_out);
   for (int i = 0; i < pieces; ++i) {
-    const int b0 = (int)((int64_t)p->total_bands * i / pieces), b1 = (int)((int64_t)p->total_bands * (i + 1) / pieces);
+    const int b0 = bounds[i], b1 = bounds[i + 1];
     if (b1 <= b0) continue;
     const size_t i0 = bytes_of(in_cube, b0), i1 = bytes_of(in_cube, b1);
     const size_t o0 = bytes_of(out_cube, b0), o1 = bytes_of(out_cube, b1);

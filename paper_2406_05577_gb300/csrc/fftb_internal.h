@@ -18,6 +18,9 @@ struct KInfo {
   int32_t xmap_base;   // first entry of this k in xmap (k * N0)
   int32_t col_base;    // first entry of this k in col_info (sum of X over earlier k)
   int32_t flags;       // KF_* bits
+  int32_t bstride;     // elements between consecutive sphere entries and between
+                       //   consecutive cube points of one band: 1 band-major, B_k
+                       //   batch-fastest (the band index is then the fastest)
 };
 // Every slab column's sticks have consecutive gy (always true for a cutoff
 // sphere); the plane stage then indexes stick rows directly.
@@ -27,11 +30,12 @@ constexpr int32_t KF_CONTIGUOUS_COLUMNS = 1;
 // indexes the coefficient list directly.
 constexpr int32_t KF_CANONICAL_STICKS = 2;
 
-// Per band: its k-point's geometry and the offset of its sphere (complex
-// elements), read by the kernels in one 32-byte load.
+// Per band: its k-point's geometry and the offsets (complex elements) of
+// its first sphere entry and first cube point, read in one 48-byte load.
 struct __align__(16) BandInfo {
   KInfo ki;
   int64_t sph;
+  int64_t cube;
 };
 
 // Device tables for all k-points (concatenated) plus twiddles.

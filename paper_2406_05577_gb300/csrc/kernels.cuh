@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
   const int nwarps = gridDim.x * STICK_NW;
   const int t0 = blockIdx.x * STICK_NW + warp;
   const int t1 = ntask;
-  int cur_bl = -1, S = 0, stick_base = 0;
+  int cur_bl = -1, S = 0, stick_base = 0, bst = 1;
   bool canon = false;
   int64_t sph = 0;
   auto band_of = [&](int bl) {
@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
       S = bi.ki.S;
       stick_base = bi.ki.stick_base;
       canon = bi.ki.flags & KF_CANONICAL_STICKS;
+      bst = bi.ki.bstride;
       sph = bi.sph;
     }
   };
@@ -108,6 +109,7 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
     int bl, s0, nl;
     int4 si;  // first entry, end entry, list position, signed gz of this lane's stick
     int64_t sph;
+    int st;  // sphere entry stride (1 band-major, B_k batch-fastest)
     bool live, canon;
   };
   auto meta = [&](int t) {
@@ -119,6 +121,7 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
     k.live = k.s0 < S;
     k.canon = canon;
     k.sph = sph;
+    k.st = bst;
     k.nl = k.live ? min(WZ, S - k.s0) : 0;
     const int s = k.s0 + (l < k.nl ? l : 0);
     k.si = k.live ? L.g.stick_info[stick_base + s] : make_int4(0, 0, 0, 0);
@@ -134,7 +137,7 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
 #pragma unroll
         for (int j = 0; j < LZ::R0; ++j) {
           const int d = zsigned(LZ::first_pos(g, m, j)) - k.si.w;
-          v[m * LZ::R0 + j] = (unsigned)d < (unsigned)len ? in[k.si.z + d] : czero<C>();
+          v[m * LZ::R0 + j] = (unsigned)d < (unsigned)len ? in[(int64_t)(k.si.z + d) * k.st] : czero<C>();
         }
     } else {
       const C* Tb = static_cast<const C*>(L.T) + (size_t)k.bl * N2 * smax + k.s0 + (l < k.nl ? l : 0);
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
 #pragma unroll
             for (int j = 0; j < LZ::RL; ++j) {
               const int d = zsigned(LZ::last_pos(g, m, j)) - k.si.w;
-              if ((unsigned)d < (unsigned)len) out[k.si.z + d] = v[m * LZ::RL + j];
+              if ((unsigned)d < (unsigned)len) out[(int64_t)(k.si.z + d) * k.st] = v[m * LZ::RL + j];
             }
         }
       } else {
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
         __syncwarp();
         for (int e = ea + lane; e < eb; e += 32) {
           const uint32_t zs = (uint32_t)L.g.ent_zs[e];
-          out[L.g.ent_pos[e]] = scr[((int)(zs & 0xFFFFFFu) - k.s0) * LZ::PITCH + wpad((int)(zs >> 24))];
+          out[(int64_t)L.g.ent_pos[e] * k.st] = scr[((int)(zs & 0xFFFFFFu) - k.s0) * LZ::PITCH + wpad((int)(zs >> 24))];
         }
         __syncwarp();
       }
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
     __syncwarp();
     for (int e = ea + lane; e < eb; e += 32) {
       const uint32_t zs = (uint32_t)L.g.ent_zs[e];
-      scr[((int)(zs & 0xFFFFFFu) - k.s0) * LZ::PITCH + wpad((int)(zs >> 24))] = in[L.g.ent_pos[e]];
+      scr[((int)(zs & 0xFFFFFFu) - k.s0) * LZ::PITCH + wpad((int)(zs >> 24))] = in[(int64_t)L.g.ent_pos[e] * k.st];
     }
     __syncwarp();
 #pragma unroll
@@ -427,8 +430,10 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
     const int bl = p / n2;
     const int z = p - bl * n2;
     const int gb = L.band0 + bl;
-    const KInfo ki = L.g.band[gb].ki;
+    const BandInfo bi = L.g.band[gb];
+    const KInfo ki = bi.ki;
     const int X = ki.X;
+    const int cst = ki.bstride;  // cube point stride: 1 band-major, B_k batch-fastest
     const int XP = a_pitch(X);
     if (ki.xmap_base != cur_k) {  // a new k-point (uniform across the CTA)
       cur_k = ki.xmap_base;
@@ -454,7 +459,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
     const int4* __restrict__ cinfo = L.g.col_info + ki.col_base;
     const int32_t* sxy = L.g.stick_xy + ki.stick_base;
     C* Tz = static_cast<C*>(L.T) + ((size_t)bl * n2 + z) * L.g.smax;
-    const size_t plane = ((size_t)gb * n2 + z) * (size_t)(N1 * N0);
+    const size_t plane = (size_t)bi.cube + (size_t)z * (size_t)(N1 * N0) * (size_t)cst;
     const int ty = (X + WY - 1) / WY;       // y tasks of this plane
     const int tx = (N1 + WX - 1) / WX;      // x tasks
     const int x_first = ty % NW;            // x tasks start after the y tasks
@@ -534,12 +539,18 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
         if constexpr (TC) LX::template run_tc<+1>(v, gx, rowx, scr, tw0, tcx, wx_p);
         else LX::template run<+1>(v, gx, rowx, tw0, tcx);
         if constexpr (MODE == M_G2R) {
-          if (live) {
+          if (live && cst == 1) {
             C* out = static_cast<C*>(L.cube_out) + plane + (size_t)row * N0;
 #pragma unroll
             for (int m = 0; m < EX / LX::RL; ++m)
 #pragma unroll
               for (int j = 0; j < LX::RL; ++j) out[LX::last_pos(gx, m, j)] = v[m * LX::RL + j];
+          } else if (live) {  // batch-fastest cube: points B_k apart
+            C* out = static_cast<C*>(L.cube_out) + plane + (size_t)row * N0 * cst;
+#pragma unroll
+            for (int m = 0; m < EX / LX::RL; ++m)
+#pragma unroll
+              for (int j = 0; j < LX::RL; ++j) out[(size_t)LX::last_pos(gx, m, j) * cst] = v[m * LX::RL + j];
           }
         } else {
           // V(r) * psi(r), then back to first-pass order and x-DFT (-)
@@ -602,13 +613,20 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
             if (lane == 0) issue_rows(pn, tn);
             outstanding = true;
           }
-        } else {
+        } else if (cst == 1) {
           const C* in = static_cast<const C*>(L.cube_in) + plane + (size_t)(live ? row : 0) * N0;
 #pragma unroll
           for (int m = 0; m < EX / LX::R0; ++m)
 #pragma unroll
             for (int j = 0; j < LX::R0; ++j)
               v[m * LX::R0 + j] = live ? in[LX::first_pos(gx, m, j)] : czero<C>();
+        } else {  // batch-fastest cube: points B_k apart
+          const C* in = static_cast<const C*>(L.cube_in) + plane + (size_t)(live ? row : 0) * N0 * cst;
+#pragma unroll
+          for (int m = 0; m < EX / LX::R0; ++m)
+#pragma unroll
+            for (int j = 0; j < LX::R0; ++j)
+              v[m * LX::R0 + j] = live ? in[(size_t)LX::first_pos(gx, m, j) * cst] : czero<C>();
         }
         if constexpr (TC) LX::template run_tc<-1>(v, gx, rowx, scr, tw0, tcx, wx_m);
         else LX::template run<-1>(v, gx, rowx, tw0, tcx);

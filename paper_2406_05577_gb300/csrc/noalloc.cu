@@ -115,11 +115,13 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
 
   // tables, packed like a one-k-point plan
   KInfo ki{G.S, G.X, 0, 0, 0,
-           (G.contiguous_columns ? KF_CONTIGUOUS_COLUMNS : 0) | (G.canonical_sticks ? KF_CANONICAL_STICKS : 0)};
+           (G.contiguous_columns ? KF_CONTIGUOUS_COLUMNS : 0) | (G.canonical_sticks ? KF_CANONICAL_STICKS : 0), 1};
+  const int64_t vol = (int64_t)n[0] * n[1] * n[2];
   std::vector<BandInfo> band((size_t)bands);
   for (int b = 0; b < bands; ++b) {
     band[b].ki = ki;
     band[b].sph = (int64_t)b * G.ngw;
+    band[b].cube = (int64_t)b * vol;
   }
   std::vector<float> tw[3];
   for (int d = 0; d < 3; ++d) {

@@ -93,8 +93,8 @@ def test_plan_errors_before_device(fftb):
         fftb.fftb_plan_create((24, 24, 24), "roundtrip", "fp32", radius=6.0, bands=[-1])
     assert e.value.status == fftb.FFTB_ERR_INVALID_ARG
     with pytest.raises(E) as e:
-        fftb.fftb_plan_create((24, 24, 24), "roundtrip", "fp32", radius=6.0, layout=1)
-    assert e.value.status == fftb.FFTB_ERR_UNSUPPORTED
+        fftb.fftb_plan_create((24, 24, 24), "roundtrip", "fp32", radius=6.0, layout=2)
+    assert e.value.status == fftb.FFTB_ERR_INVALID_ARG
     with pytest.raises(E) as e:
         fftb.fftb_plan_create((24, 24, 24), 7, "fp32", radius=6.0)
     assert e.value.status == fftb.FFTB_ERR_INVALID_ARG
