@@ -331,6 +331,30 @@ fftb_status fftb_sphere_enumerate(const int32_t n[3], double radius, const doubl
 fftb_status fftb_sphere_sticks(const int32_t n[3], const int32_t* g, int64_t ngw,
                                int32_t* n_sticks, int32_t* n_slabs);
 
+/* The whole frequency box of an N0 x N1 x N2 grid, every G with components
+ * in [-N/2, N/2), in canonical order (gy, then gx, then gz ascending): as a
+ * g_list it makes a plan the unpruned 3D transform of the full cube (the
+ * classical cuboid transform of Sec. 3.2 / Fig. 5, and the fully padded
+ * baseline of Sec. 2.3 that staged padding prunes). Writes N0 N1 N2 triples
+ * to g_out (host, capacity checked: INVALID_ARG if capacity is smaller). */
+fftb_status fftb_box_enumerate(const int32_t n[3], int32_t* g_out, int64_t capacity);
+
+/* The sphere of an offset array over a bounding domain (Sec. 3.3, Fig. 6 and
+ * the domain of Fig. 7), as a g_list in the order of the data. The domain has
+ * the inclusive corners lo[3] and hi[3] (any lower corner, e.g. 0..N-1 or a
+ * box around the sphere); its xy projection is dense and its z dimension is
+ * compressed like CSR rows: column c = (y - lo[1]) * (hi[0] - lo[0] + 1) +
+ * (x - lo[0]) (x fastest) holds the entries offsets[c] .. offsets[c+1] - 1,
+ * and entry e lies at z = z_index[e] (a domain coordinate in [lo[2], hi[2]]).
+ * A domain coordinate v is the frequency v mod N, written to g_out as the
+ * signed component in [-N/2, N/2) (N - 1 is -1). offsets has one entry per
+ * column plus one, from 0 up to nnz, non-decreasing; g_out (host) takes nnz
+ * triples. INVALID_ARG for a domain wider than the grid, a malformed offset
+ * array or a z outside the domain; duplicates are caught at plan creation. */
+fftb_status fftb_glist_from_offsets(const int32_t n[3], const int32_t lo[3], const int32_t hi[3],
+                                    const int64_t* offsets, const int32_t* z_index, int64_t nnz,
+                                    int32_t* g_out);
+
 /* Library version string. */
 const char* fftb_version(void);
 

@@ -1006,6 +1006,57 @@ FFTB_EXPORT fftb_status fftb_sphere_enumerate(const int32_t n[3], double radius,
   return FFTB_OK;
 }
 
+FFTB_EXPORT fftb_status fftb_box_enumerate(const int32_t n[3], int32_t* g_out, int64_t capacity) {
+  if (!n || !g_out) return fail(FFTB_ERR_INVALID_ARG, "NULL argument");
+  for (int i = 0; i < 3; ++i)
+    if (n[i] < 1) return fail(FFTB_ERR_INVALID_ARG, "grid extents must be >= 1");
+  const int64_t vol = (int64_t)n[0] * n[1] * n[2];
+  if (capacity < vol) return fail(FFTB_ERR_INVALID_ARG, "g_out holds fewer than N0 N1 N2 triples");
+  const int32_t h0 = n[0] / 2, h1 = n[1] / 2, h2 = n[2] / 2;
+  int32_t* o = g_out;
+  for (int32_t gy = -h1; gy < n[1] - h1; ++gy)
+    for (int32_t gx = -h0; gx < n[0] - h0; ++gx)
+      for (int32_t gz = -h2; gz < n[2] - h2; ++gz) {
+        *o++ = gx;
+        *o++ = gy;
+        *o++ = gz;
+      }
+  return FFTB_OK;
+}
+
+FFTB_EXPORT fftb_status fftb_glist_from_offsets(const int32_t n[3], const int32_t lo[3], const int32_t hi[3],
+                                                const int64_t* offsets, const int32_t* z_index, int64_t nnz,
+                                                int32_t* g_out) {
+  if (!n || !lo || !hi || !offsets || (nnz > 0 && (!z_index || !g_out))) return fail(FFTB_ERR_INVALID_ARG, "NULL argument");
+  if (nnz < 0) return fail(FFTB_ERR_INVALID_ARG, "nnz must be >= 0");
+  for (int i = 0; i < 3; ++i) {
+    if (n[i] < 1) return fail(FFTB_ERR_INVALID_ARG, "grid extents must be >= 1");
+    if (hi[i] < lo[i]) return fail(FFTB_ERR_INVALID_ARG, "domain upper corner below its lower corner");
+    if ((int64_t)hi[i] - lo[i] + 1 > n[i]) return fail(FFTB_ERR_INVALID_ARG, "domain wider than the grid (would alias)");
+  }
+  const int64_t nx = (int64_t)hi[0] - lo[0] + 1, ny = (int64_t)hi[1] - lo[1] + 1;
+  const int64_t cols = nx * ny;
+  if (offsets[0] != 0 || offsets[cols] != nnz) return fail(FFTB_ERR_INVALID_ARG, "offsets must run from 0 to nnz");
+  // a domain coordinate v is the frequency v mod N, as a signed component
+  auto freq = [](int64_t v, int32_t N) {
+    int64_t m = v % N;
+    if (m < 0) m += N;
+    return (int32_t)(m >= N - N / 2 ? m - N : m);
+  };
+  for (int64_t c = 0; c < cols; ++c) {
+    if (offsets[c + 1] < offsets[c]) return fail(FFTB_ERR_INVALID_ARG, "offsets must be non-decreasing");
+    const int32_t gx = freq(lo[0] + c % nx, n[0]), gy = freq(lo[1] + c / nx, n[1]);
+    for (int64_t e = offsets[c]; e < offsets[c + 1]; ++e) {
+      const int32_t z = z_index[e];
+      if (z < lo[2] || z > hi[2]) return fail(FFTB_ERR_INVALID_ARG, "z index outside the domain");
+      g_out[3 * e] = gx;
+      g_out[3 * e + 1] = gy;
+      g_out[3 * e + 2] = freq(z, n[2]);
+    }
+  }
+  return FFTB_OK;
+}
+
 FFTB_EXPORT fftb_status fftb_sphere_sticks(const int32_t n[3], const int32_t* g, int64_t ngw,
                                            int32_t* n_sticks, int32_t* n_slabs) {
   if (!n || (!g && ngw > 0) || !n_sticks || !n_slabs) return fail(FFTB_ERR_INVALID_ARG, "NULL argument");

@@ -98,6 +98,10 @@ EXPORTS = {
     "fftb_sphere_sticks": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p,
                                           ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int32)]),
+    "fftb_box_enumerate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_int64]),
+    "fftb_glist_from_offsets": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                               ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_int64, ctypes.c_void_p]),
 }
 
 _lib = None
@@ -289,6 +293,30 @@ def fftb_sphere_sticks(n, g):
     _check(L.fftb_sphere_sticks(nn, gg.ctypes.data if gg.size else None, len(gg),
                                 ctypes.byref(s), ctypes.byref(x)))
     return s.value, x.value
+
+
+def fftb_box_enumerate(n):
+    """Every G of the grid's frequency box in canonical order, (N0 N1 N2, 3)
+    int32 (host only): the g_list of the unpruned full-cube transform."""
+    nn = (ctypes.c_int32 * 3)(*[int(v) for v in n])
+    vol = int(n[0]) * int(n[1]) * int(n[2])
+    out = np.zeros((vol, 3), np.int32)
+    _check(lib().fftb_box_enumerate(nn, out.ctypes.data, vol))
+    return out
+
+
+def fftb_glist_from_offsets(n, lo, hi, offsets, z_index):
+    """(nnz, 3) int32 G list of an offset array over the bounding domain
+    [lo, hi] (inclusive corners; x-fastest columns, per-entry z), host only."""
+    nn = (ctypes.c_int32 * 3)(*[int(v) for v in n])
+    l3 = (ctypes.c_int32 * 3)(*[int(v) for v in lo])
+    h3 = (ctypes.c_int32 * 3)(*[int(v) for v in hi])
+    off = np.ascontiguousarray(np.asarray(offsets, np.int64).reshape(-1))
+    zi = np.ascontiguousarray(np.asarray(z_index, np.int32).reshape(-1))
+    out = np.zeros((max(len(zi), 1), 3), np.int32)
+    _check(lib().fftb_glist_from_offsets(nn, l3, h3, off.ctypes.data, zi.ctypes.data if zi.size else None,
+                                         len(zi), out.ctypes.data))
+    return out[:len(zi)]
 
 
 def fftb_g2r_noalloc(n, radius, kshift, bands, in_ptr, out_ptr, stream=None):

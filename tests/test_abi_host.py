@@ -110,3 +110,70 @@ def test_sphere_enumerate_rejects_alias(fftb):
     with pytest.raises(fftb.FFTBError):
         fftb.fftb_sphere_enumerate((24, 24, 16), 8.5)
     assert len(fftb.fftb_sphere_enumerate((25, 25, 25), 12.0)) == len(sphere_gvectors((25, 25, 25), 12.0))
+
+
+def test_box_enumerate(fftb):
+    """The whole frequency box: every component in [-N/2, N/2), each G once,
+    sorted by gy, then gx, then gz (signed)."""
+    for n in [(4, 6, 5), (12, 12, 16), (32, 32, 32)]:
+        g = fftb.fftb_box_enumerate(n)
+        assert g.shape == (n[0] * n[1] * n[2], 3)
+        for d in range(3):
+            h = n[d] // 2
+            assert g[:, d].min() == -h and g[:, d].max() == n[d] - h - 1
+        assert len({tuple(v) for v in g}) == len(g)
+        assert np.array_equal(np.lexsort((g[:, 2], g[:, 0], g[:, 1])), np.arange(len(g)))
+    small = np.zeros((63, 3), np.int32)  # one triple short
+    st = fftb.lib().fftb_box_enumerate((fftb.ctypes.c_int32 * 3)(4, 4, 4), small.ctypes.data, 63)
+    assert st == fftb.FFTB_ERR_INVALID_ARG and not small.any()
+
+
+def _csr_of(g, n, lo, hi):
+    """an offset array over the domain [lo, hi] for the G list g: domain
+    coordinates are the frequencies shifted into [lo, hi] by multiples of N"""
+    g = np.asarray(g, np.int64)
+    lo, hi = np.asarray(lo), np.asarray(hi)
+    v = lo + np.mod(g - lo, np.asarray(n))
+    assert np.all(v <= hi)
+    nx, ny = hi[0] - lo[0] + 1, hi[1] - lo[1] + 1
+    col = (v[:, 1] - lo[1]) * nx + (v[:, 0] - lo[0])
+    order = np.lexsort((v[:, 2], col))
+    offsets = np.zeros(nx * ny + 1, np.int64)
+    np.add.at(offsets, col + 1, 1)
+    return np.cumsum(offsets), v[order, 2].astype(np.int32), g[order]
+
+
+@pytest.mark.parametrize("n,r,lo,hi", [((24, 24, 24), 6.0, (0, 0, 0), (23, 23, 23)),
+                                       ((24, 24, 24), 6.0, (-6, -6, -6), (6, 6, 6)),
+                                       ((32, 32, 48), 9.5, (-16, 0, -24), (15, 31, 23)),
+                                       ((20, 20, 40), 6.5, (-7, -7, 0), (7, 7, 39))])
+def test_glist_from_offsets(fftb, n, r, lo, hi):
+    """The paper's offset array over a bounding domain (z compressed per xy
+    column, any lower corner): the G list comes back in the data's order."""
+    g = sphere_gvectors(n, r)
+    offsets, zi, want = _csr_of(g, n, lo, hi)
+    got = fftb.fftb_glist_from_offsets(n, lo, hi, offsets, zi)
+    assert got.dtype == np.int32 and np.array_equal(got, want)
+    # the list holds the sphere once: as many sticks as the offset array has runs
+    assert fftb.fftb_sphere_sticks(n, got)[0] == int(np.count_nonzero(np.diff(offsets)))
+
+
+def test_glist_from_offsets_errors(fftb):
+    n = (8, 8, 8)
+    E = fftb.FFTBError
+    ok_off = np.zeros(8 * 8 + 1, np.int64)
+    ok_off[1:] = 1
+    zi = np.zeros(1, np.int32)
+    assert np.array_equal(fftb.fftb_glist_from_offsets(n, (0, 0, 0), (7, 7, 7), ok_off, zi), [[0, 0, 0]])
+    assert np.array_equal(fftb.fftb_glist_from_offsets(n, (4, 0, 0), (11, 7, 7), ok_off, zi), [[-4, 0, 0]])
+    with pytest.raises(E) as e:  # nine x values on an 8-point grid alias
+        fftb.fftb_glist_from_offsets(n, (0, 0, 0), (8, 7, 7), np.zeros(9 * 8 + 1, np.int64), zi[:0])
+    assert e.value.status == fftb.FFTB_ERR_INVALID_ARG
+    bad = ok_off.copy()
+    bad[5] = 2  # not non-decreasing
+    with pytest.raises(E):
+        fftb.fftb_glist_from_offsets(n, (0, 0, 0), (7, 7, 7), bad, np.zeros(2, np.int32))
+    with pytest.raises(E):  # last offset != nnz
+        fftb.fftb_glist_from_offsets(n, (0, 0, 0), (7, 7, 7), ok_off, np.zeros(2, np.int32))
+    with pytest.raises(E):  # z outside the domain
+        fftb.fftb_glist_from_offsets(n, (0, 0, 0), (7, 7, 3), ok_off, np.array([5], np.int32))
