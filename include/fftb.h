@@ -122,6 +122,10 @@ typedef struct {
   int32_t radix_schedule_stick; /* the same for the z lines                            */
   int32_t dependent_launch;   /* 1: stage kernels use programmatic dependent launch
                               (fftb_plan_set_pdl, or the autotuner's choice)          */
+  int32_t plane_band_group;   /* batch-fastest FP32 plans: bands of one k-point whose
+                              G->r / r->G plane stages one CTA runs together, so cube
+                              rows move band-contiguous (4 up to 96 points, 2 at 128);
+                              0: one band per plane (every other plan)                */
 } fftb_plan_info_t;
 
 /* Builds the spheres, stick/slab tables and twiddles on the host, uploads
@@ -254,6 +258,12 @@ fftb_status fftb_plan_set_radix_schedule(fftb_plan plan, int32_t plane, int32_t 
  * before touching stage data, so launch latency and prologues overlap the
  * previous kernel's tail. 0 launches them plainly. */
 fftb_status fftb_plan_set_pdl(fftb_plan plan, int32_t enable);
+
+/* Batch-fastest FP32 plans with N0 == N1 up to 128 run their G->r and r->G
+ * plane stages over groups of bands of one k-point (on by default;
+ * fftb_plan_autotune measures both): UNSUPPORTED to enable where the plan has
+ * no grouped kernels. Results are identical either way. */
+fftb_status fftb_plan_set_band_groups(fftb_plan plan, int32_t enable);
 
 /* Device status. Every wait of a plane kernel on an asynchronous copy gives
  * up after one second; the CTA then lets its copies in flight land, leaves,

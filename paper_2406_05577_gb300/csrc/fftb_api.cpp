@@ -88,6 +88,13 @@ struct fftb_plan_s {
   int32_t smax = 0, xmax = 0, tiles = 0, chunk = 1;
   int32_t tpitch = 2;  // stick-row pitch of T: smax rounded up to even
   int32_t layout = 0;  // 0 band-major, 1 batch-fastest (band index fastest)
+  // batch-fastest FP32 plans: plane stages over groups of bands of one k-point
+  int bg = 0;                      // group size in use (0: one band per plane)
+  int bg_size = 0;                 // the grid's group size where the grouped kernels fit, else 0
+  int bg_occ[2] = {0, 0};          // their resident CTAs per SM: G->r, r->G
+  std::vector<int2> groups;        // (first band, bands) of every group, k-point by k-point
+  std::vector<int32_t> band_grp;   // group of a band that starts one, else -1
+  void* d_groups = nullptr;
   int device = 0;
   int32_t plane_ctas[3] = {0, 0, 0};  // persistent CTAs: G->r, r->G, apply
   int32_t a_bufs = 2;                 // slab-plane buffers of the plane stage
@@ -157,12 +164,14 @@ namespace {
 
 // the plane stage of mode index i (G->r, r->G, apply) prefetches
 bool pf_active(const fftb_plan_s* p, int i) {
+  if (p->bg && i < 2) return false;  // the grouped kernels do not prefetch
   if (!p->pf_fit[i] || p->pf_level == 0 || ((p->sched_plane >> i) & 1)) return false;
   if (i == 1 && p->layout != 0) return false;  // bulk copies take whole band-major cube rows
   return p->pf_level == 2 || p->pf_occ[i] >= p->plane_occ[i];
 }
 // resident plane CTAs per SM of the kernel mode index i uses
 int occ_in_use(const fftb_plan_s* p, int i) {
+  if (p->bg && i < 2) return p->bg_occ[i];
   if ((p->sched_plane >> i) & 1) return p->alt_plane_occ[i];
   return pf_active(p, i) ? p->pf_occ[i] : p->plane_occ[i];
 }
@@ -245,6 +254,7 @@ void release(fftb_plan_s* p) {
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->h_status) cudaFreeHost(p->h_status);
   if (p->d_tc5w) cudaFree(p->d_tc5w);
+  if (p->d_groups) cudaFree(p->d_groups);
   delete p;
 }
 
@@ -518,6 +528,43 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   *p->h_status = 0;
   e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&p->d_status), p->h_status, 0);
   if (e != cudaSuccess) { release(p); return cuda_fail(e, "status word device address"); }
+  if (p->layout == 1 && p->prec_kernel == P_F32 && p->n[0] == p->n[1] && p->total_bands > 0) {
+    // batch-fastest: plane stages over groups of bands of one k-point, where they fit
+    const int bgs = plane_bg_group(p->n[0]);
+    if (bgs > 1 && plane_bg_smem(p->n[0], p->n[1], p->xmax, bgs) <= kSmemLimit) {
+      e = prepare_plane_bg(p->n[0], p->xmax);
+      if (e != cudaSuccess) { release(p); return cuda_fail(e, "kernel attributes"); }
+      const int o0 = plane_bg_occupancy(M_G2R, p->n[0], p->xmax), o1 = plane_bg_occupancy(M_R2G, p->n[0], p->xmax);
+      if (o0 >= 1 && o1 >= 1) {
+        p->band_grp.assign(p->total_bands, -1);
+        int b0 = 0;
+        for (int k = 0; k < p->nk; ++k) {
+          for (int b = 0; b < p->bands[k]; b += bgs) {
+            p->band_grp[b0 + b] = (int32_t)p->groups.size();
+            p->groups.push_back(make_int2(b0 + b, std::min(bgs, p->bands[k] - b)));
+          }
+          b0 += p->bands[k];
+        }
+        e = cudaMalloc(&p->d_groups, p->groups.size() * sizeof(int2));
+        if (e == cudaSuccess)
+          e = cudaMemcpy(p->d_groups, p->groups.data(), p->groups.size() * sizeof(int2), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "band group table"); }
+        // a launch takes whole groups: the stick buffer holds at least one
+        const size_t need = (size_t)std::max(p->chunk, bgs) * p->n[2] * p->tpitch * p->csize;
+        if (need > p->T_bytes) {
+          cudaFree(p->d_T);
+          p->d_T = nullptr;
+          p->T_bytes = 0;
+          if (cudaMalloc(&p->d_T, need) != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaMalloc stick scratch failed"); }
+          p->T_bytes = need;
+        }
+        p->bg_size = p->bg = bgs;
+        p->bg_occ[0] = o0;
+        p->bg_occ[1] = o1;
+        for (int i = 0; i < 2; ++i) p->plane_ctas[i] = p->sms * occ_in_use(p, i);
+      }
+    }
+  }
   if (p->a_glob) {
     // one double-buffered slab-plane block per persistent CTA (the most any mode launches)
     const int ctas = std::max(p->plane_ctas[0], std::max(p->plane_ctas[1], p->plane_ctas[2]));
@@ -545,6 +592,7 @@ FFTB_EXPORT fftb_status fftb_plan_sphere(fftb_plan p, int32_t k, int32_t* g_out)
   return FFTB_OK;
 }
 
+static int count_chunks(const fftb_plan_s* p, int first, int bands);
 static int kernels_per_chunk(fftb_direction d) {
   switch (d) {
     case FFTB_G_TO_R: return 2;
@@ -564,8 +612,7 @@ FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) 
   info->max_sticks = p->smax;
   info->max_slabs = p->xmax;
   info->chunk_bands = p->chunk;
-  const int nchunks = p->total_bands > 0 ? (p->total_bands + p->chunk - 1) / p->chunk : 0;
-  info->kernels_per_execute = nchunks * kernels_per_chunk(p->dir);
+  info->kernels_per_execute = count_chunks(p, 0, p->total_bands) * kernels_per_chunk(p->dir);
   info->complex_bytes = p->csize;
   info->stick_ctas = p->tiles;
   info->plane_ctas = p->plane_ctas[p->dir == FFTB_R_TO_G ? 1 : p->dir == FFTB_APPLY_LOCAL ? 2 : 0];
@@ -578,6 +625,7 @@ FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) 
   info->radix_schedule_plane = p->sched_plane;
   info->radix_schedule_stick = p->sched_stick;
   info->dependent_launch = p->pdl ? 1 : 0;
+  info->plane_band_group = p->bg;
   return FFTB_OK;
 }
 
@@ -623,7 +671,8 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
       Launch Lp = L;
       Lp.plane_ctas = p->plane_ctas[0];
       Lp.pf = pf_active(p, 0);
-      if (p->tc5) e = tc5_launch(M_G2R, Lp, p->tc5g[0], p->tc5_ctas);
+      if (p->bg) e = launch_plane_bg(M_G2R, Lp);
+      else if (p->tc5) e = tc5_launch(M_G2R, Lp, p->tc5g[0], p->tc5_ctas);
       else if (p->sched_plane & 1) e = launch_plane_alt(M_G2R, Lp);
       else e = Lp.pf ? launch_plane_pf(M_G2R, Lp) : launch_plane(pk, M_G2R, Lp);
       break;
@@ -632,7 +681,8 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
       Launch Lp = L;
       Lp.plane_ctas = p->plane_ctas[1];
       Lp.pf = pf_active(p, 1) && cube_in_16;
-      if (p->tc5 && cube_in_16) e = tc5_launch(M_R2G, Lp, p->tc5g[1], p->tc5_ctas);
+      if (p->bg) e = launch_plane_bg(M_R2G, Lp);
+      else if (p->tc5 && cube_in_16) e = tc5_launch(M_R2G, Lp, p->tc5g[1], p->tc5_ctas);
       else if (p->sched_plane & 2) e = launch_plane_alt(M_R2G, Lp);
       else e = Lp.pf ? launch_plane_pf(M_R2G, Lp) : launch_plane(pk, M_R2G, Lp);
       break;
@@ -659,7 +709,32 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
 
 static bool aligned(const void* q, int a) { return (reinterpret_cast<uintptr_t>(q) % (uintptr_t)a) == 0; }
 
-// Enqueues every band chunk's stages for the bands [first, first + bands).
+// The band chunk that starts at band b0 (< end): the plan's chunk of bands,
+// or for grouped plans whole band groups up to that many bands (at least one
+// group; b0 starts a group). Sets the chunk's bands and its groups.
+static void chunk_at(const fftb_plan_s* p, int b0, int end, int* nb, int* g0, int* ng) {
+  if (!p->bg) {
+    *nb = std::min(p->chunk, end - b0);
+    *g0 = *ng = 0;
+    return;
+  }
+  int g = p->band_grp[b0], n = 0;
+  *g0 = g;
+  while (g < (int)p->groups.size() && p->groups[g].x < end && (n == 0 || n + p->groups[g].y <= p->chunk)) {
+    n += p->groups[g].y;
+    ++g;
+  }
+  *nb = n;
+  *ng = g - *g0;
+}
+static int count_chunks(const fftb_plan_s* p, int first, int bands) {
+  int n = 0;
+  for (int b0 = first, nb = 0, g0, ng; b0 < first + bands; b0 += nb, ++n) chunk_at(p, b0, first + bands, &nb, &g0, &ng);
+  return n;
+}
+
+// Enqueues every band chunk's stages for the bands [first, first + bands)
+// (grouped plans: from a group start, whole groups).
 static fftb_status enqueue(fftb_plan_s* p, int bands, const void* in, void* out, void* cube, cudaStream_t s,
                            int first = 0) {
   Launch L{};
@@ -671,10 +746,14 @@ static fftb_status enqueue(fftb_plan_s* p, int bands, const void* in, void* out,
   L.inject = p->inject;
   L.status = p->d_status;
   L.pdl = p->pdl ? 1 : 0;
+  L.groups = static_cast<const int2*>(p->d_groups);
   L.stream = s;
-  for (int b0 = first; b0 < first + bands; b0 += p->chunk) {
+  if (p->bg && (first >= p->total_bands || p->band_grp[first] < 0))
+    return fail(FFTB_ERR_INVALID_ARG, "a grouped launch must start at a band group");
+  for (int b0 = first, nb = 0; b0 < first + bands; b0 += nb) {
+    chunk_at(p, b0, first + bands, &nb, &L.grp0, &L.ngrp);
     L.band0 = b0;
-    L.nb = std::min(p->chunk, first + bands - b0);
+    L.nb = nb;
     cudaError_t e = cudaSuccess;
     switch (p->dir) {
       case FFTB_G_TO_R:
@@ -720,7 +799,7 @@ static fftb_status launch_all(fftb_plan_s* p, int bands, const void* in, void* o
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) graph = false;
   }
   if (!graph) return enqueue(p, bands, in, out, cube, s);
-  const int64_t per_exec = (int64_t)((p->total_bands + p->chunk - 1) / p->chunk) * kernels_per_chunk(p->dir);
+  const int64_t per_exec = (int64_t)count_chunks(p, 0, p->total_bands) * kernels_per_chunk(p->dir);
   if (!(p->gexec && p->g_in == in && p->g_out == out && p->g_cube == cube && p->g_V == p->d_V)) {
     const int64_t before = p->launches;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
@@ -955,6 +1034,21 @@ FFTB_EXPORT fftb_status fftb_plan_set_pdl(fftb_plan p, int32_t enable) {
   return FFTB_OK;
 }
 
+FFTB_EXPORT fftb_status fftb_plan_set_band_groups(fftb_plan p, int32_t enable) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (enable && !p->bg_size)
+    return fail(FFTB_ERR_UNSUPPORTED, "no grouped plane kernels for this plan (batch-fastest FP32, N0 == N1, fitting)");
+  const int bg = enable ? p->bg_size : 0;
+  if (bg == p->bg) return FFTB_OK;
+  p->bg = bg;
+  for (int i = 0; i < 2; ++i) p->plane_ctas[i] = p->sms * occ_in_use(p, i);
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  return FFTB_OK;
+}
+
 FFTB_EXPORT fftb_status fftb_plan_inject(fftb_plan p, int32_t flags) {
   if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
   if (flags & ~FFTB_INJECT_SKIP_FIRST_PREFETCH) return fail(FFTB_ERR_INVALID_ARG, "unknown injection flag");
@@ -1122,6 +1216,7 @@ struct TuneChoice {
   int ctas[3] = {0, 0, 0};  // -1: one full wave of the kernel in use
   int sched_plane = 0, sched_stick = 0;  // radix schedule variants
   int pdl = 1;                           // programmatic dependent launch
+  int bg = 0;                            // band group of the plane stages (batch-fastest)
 };
 
 TuneChoice current_choice(const fftb_plan_s* p) {
@@ -1133,6 +1228,7 @@ TuneChoice current_choice(const fftb_plan_s* p) {
   c.sched_plane = p->sched_plane;
   c.sched_stick = p->sched_stick;
   c.pdl = p->pdl ? 1 : 0;
+  c.bg = p->bg;
   for (int i = 0; i < 3; ++i) c.ctas[i] = p->plane_ctas[i];
   return c;
 }
@@ -1148,10 +1244,10 @@ bool tune_cache_lookup(const std::string& key, TuneChoice* out) {
     std::string k;
     TuneChoice c;
     if ((ls >> k >> c.chunk >> c.ctas[0] >> c.ctas[1] >> c.ctas[2] >> c.tiles >> c.level >> c.a_bufs >>
-         c.sched_plane >> c.sched_stick >> c.pdl) &&
+         c.sched_plane >> c.sched_stick >> c.pdl >> c.bg) &&
         k == key && c.chunk >= 1 && c.level >= 0 && c.level <= 2 && (c.a_bufs == 1 || c.a_bufs == 2) &&
         c.sched_plane >= 0 && c.sched_plane <= 7 && (c.sched_stick == 0 || c.sched_stick == 1) &&
-        (c.pdl == 0 || c.pdl == 1)) {
+        (c.pdl == 0 || c.pdl == 1) && c.bg >= 0 && c.bg <= 4) {
       *out = c;
       found = true;  // the last entry wins
     }
@@ -1164,7 +1260,8 @@ void tune_cache_store(const std::string& key, const TuneChoice& c) {
   if (!path || !*path) return;
   std::ofstream f(path, std::ios::app);
   f << key << " " << c.chunk << " " << c.ctas[0] << " " << c.ctas[1] << " " << c.ctas[2] << " " << c.tiles << " "
-    << c.level << " " << c.a_bufs << " " << c.sched_plane << " " << c.sched_stick << " " << c.pdl << "\n";
+    << c.level << " " << c.a_bufs << " " << c.sched_plane << " " << c.sched_stick << " " << c.pdl << " " << c.bg
+    << "\n";
 }
 
 fftb_status resize_T(fftb_plan_s* p, int chunk) {
@@ -1191,9 +1288,10 @@ fftb_status apply_choice(fftb_plan_s* p, const TuneChoice& c) {
       return st;
     }
   }
-  fftb_status st = resize_T(p, c.chunk);
+  fftb_status st = resize_T(p, std::max(c.chunk, p->bg_size));
   if (st != FFTB_OK) return st;
   p->chunk = c.chunk;
+  p->bg = (c.bg && p->bg_size) ? p->bg_size : 0;
   p->pf_level = c.level;
   p->sched_plane = p->alt_plane_ok ? c.sched_plane : 0;
   p->sched_stick = (c.sched_stick && p->alt_stick_ok) ? 1 : 0;
@@ -1229,7 +1327,14 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   const size_t budget = (size_t)4 << 30;
   const int bands = (int)std::max<int64_t>(1, std::min<int64_t>(p->total_bands, (int64_t)(budget / std::max<size_t>(band_bytes, 1))));
   const size_t sph_b = (size_t)p->sphere_elems * p->csize;
-  const size_t cube_b = (size_t)bands * vol * p->csize;
+  // a batch-fastest band spreads over its whole k-point block of the cube:
+  // cover the blocks of every k-point the band prefix touches
+  int cube_bands = bands;
+  if (p->layout == 1) {
+    cube_bands = 0;
+    for (int k = 0; k < p->nk && cube_bands < bands; ++k) cube_bands += p->bands[k];
+  }
+  const size_t cube_b = (size_t)cube_bands * vol * p->csize;
   void *d_in = nullptr, *d_out = nullptr, *d_cube = nullptr, *d_v = nullptr;
   auto cleanup = [&]() {
     if (d_in) cudaFree(d_in);
@@ -1264,7 +1369,7 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
     if (std::find(chunks.begin(), chunks.end(), c) == chunks.end()) chunks.push_back(c);
   }
   const int max_chunk = *std::max_element(chunks.begin(), chunks.end());
-  fftb_status st = resize_T(p, max_chunk);
+  fftb_status st = resize_T(p, std::max(max_chunk, p->bg_size));
   if (st != FFTB_OK) {
     p->d_V = saved_v;
     cleanup();
@@ -1310,6 +1415,9 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   }
   std::vector<int> plane_scheds = {0}, stick_scheds = {0};
   if (p->alt_stick_ok) stick_scheds.push_back(1);
+  std::vector<int> bgs = {0};
+  if (p->bg_size) bgs.push_back(p->bg_size);
+  for (int bgv : bgs)
   for (int nb : nbufs) {
     if (st != FFTB_OK) break;
     for (int ss : stick_scheds) {
@@ -1326,11 +1434,13 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
           c.level = lv;
           c.sched_plane = sp;
           c.sched_stick = ss;
+          c.bg = bgv;
           c.tiles = c.tiles ? -1 : 0;              // z-stage: the same kind, one full wave of its schedule
           c.ctas[0] = c.ctas[1] = c.ctas[2] = -1;  // one full wave of the variant
           st = apply_choice(p, c);
           if (st != FFTB_OK) break;
-          int mask = p->sched_plane << 3;
+          // what the kernels in use depend on (the grouped G->r / r->G kernels on neither)
+          int mask = (p->bg ? 64 | (p->sched_plane & 4) : p->sched_plane) << 3;
           for (int i = 0; i < 3; ++i)
             if (pf_active(p, i)) mask |= 1 << i;
           if (std::find(masks.begin(), masks.end(), mask) != masks.end()) continue;

@@ -75,6 +75,8 @@ struct Launch {
   int32_t inject;       // INJECT_* bits (tests of the bounded waits)
   int32_t* status;      // device-visible status word (STATUS_* bits), set on a failed wait
   int32_t pdl;          // launch with programmatic dependent launch (overlaps launch and prologue)
+  const int2* groups;   // batch-fastest band groups (first band, bands), plan-global list
+  int32_t grp0, ngrp;   // the groups of this launch (they cover [band0, band0 + nb))
   cudaStream_t stream;
 };
 
@@ -118,6 +120,15 @@ cudaError_t prepare_alt(int n0, int n2, int xmax, int a_bufs);
 int plane_alt_occupancy(int mode, int n, int xmax, int a_bufs);
 int stick_alt_occupancy(int n);
 cudaError_t launch_plane_alt(int mode, const Launch& L);
+// FP32 y/x stages of batch-fastest plans over groups of bands of one k-point
+// (k_f32_bg.cu; N0 == N1): the group size of a length (0: none), shared
+// memory (0 if bg is not that size), kernel attributes, resident CTAs per SM
+// (G -> r or r -> G), launch over L.groups[grp0 .. grp0 + ngrp).
+int plane_bg_group(int n);
+size_t plane_bg_smem(int n0, int n1, int xmax, int bg);
+cudaError_t prepare_plane_bg(int n, int xmax);
+int plane_bg_occupancy(int mode, int n, int xmax);
+cudaError_t launch_plane_bg(int mode, const Launch& L);
 cudaError_t launch_stick_alt(int mode, const Launch& L, int ctas);
 // MIXED_TC plane stage on the 5th-generation tensor cores (k_tc5.cu): the
 // union over k-points of the occupied x values [xlo, xlo + xu) and of the

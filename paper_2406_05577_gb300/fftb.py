@@ -61,6 +61,7 @@ class fftb_plan_info_t(ctypes.Structure):
         ("radix_schedule_plane", ctypes.c_int32),
         ("radix_schedule_stick", ctypes.c_int32),
         ("dependent_launch", ctypes.c_int32),
+        ("plane_band_group", ctypes.c_int32),
     ]
 
 
@@ -91,6 +92,7 @@ EXPORTS = {
     "fftb_plan_set_slab_buffers": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fftb_plan_set_radix_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "fftb_plan_set_pdl": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "fftb_plan_set_band_groups": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fftb_plan_inject": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fftb_sphere_enumerate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_double,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -251,6 +253,10 @@ def fftb_plan_set_radix_schedule(plan, plane, stick):
 
 def fftb_plan_set_pdl(plan, enable):
     _check(lib().fftb_plan_set_pdl(plan, 1 if enable else 0))
+
+
+def fftb_plan_set_band_groups(plan, enable):
+    _check(lib().fftb_plan_set_band_groups(plan, 1 if enable else 0))
 
 
 def fftb_plan_check(plan):
@@ -414,6 +420,10 @@ class Plan:
 
     def set_pdl(self, enable=True):
         fftb_plan_set_pdl(self.handle, enable)
+        self.info = fftb_plan_get_info(self.handle)
+
+    def set_band_groups(self, enable=True):
+        fftb_plan_set_band_groups(self.handle, enable)
         self.info = fftb_plan_get_info(self.handle)
 
     def check(self):

@@ -183,3 +183,65 @@ def test_batch_fastest_host_pipeline(F, bands):
     assert plan.launches() - before >= pieces * 4 and plan.launches() - before <= (chunks + pieces) * 4
     assert np.array_equal(pin_out.numpy(), want)
     assert np.array_equal(cube2.cpu().numpy(), wcube)
+
+
+@pytest.mark.parametrize("n,r,ks,bands,group", [((64, 64, 64), 16.0, None, [7], 4),
+                                                ((32, 32, 32), 8.0, [(0.3, -0.2, 0.1), (-0.45, 0.4, -0.3)], [3, 5], 4),
+                                                ((48, 48, 48), 12.0, None, [6], 4),
+                                                ((96, 96, 96), 24.0, None, [5], 4),
+                                                ((128, 128, 128), 32.0, None, [3], 2),
+                                                ((160, 160, 160), 40.0, None, [2], 0)])
+def test_band_groups_same_results(F, n, r, ks, bands, group):
+    """The grouped plane kernels (several bands of one k-point per CTA, cube
+    rows band-contiguous) give the per-band kernels' results bit for bit,
+    including partial groups at k-point ends and a chunk smaller than a group."""
+    import torch
+    kw = dict(radius=r, bands=bands)
+    if ks is not None:
+        kw["kshift"] = np.array(ks)
+    p = F.Plan(n, "roundtrip", "fp32", layout=1, **kw)
+    assert p.info["plane_band_group"] == group
+    gs = [p.sphere(k) for k in range(len(bands))]
+    ngws = [len(g) for g in gs]
+    x = sph_bf(np.concatenate([fi.complex_gaussian((b, ng), 340 + k).astype(np.complex64).reshape(-1)
+                               for k, (ng, b) in enumerate(zip(ngws, bands))]), ngws, bands)
+    o1, c1 = execute(F, p, x, "roundtrip", torch.complex64)
+    if group == 0:
+        with pytest.raises(F.FFTBError) as ei:
+            p.set_band_groups(True)
+        assert ei.value.status == F.FFTB_ERR_UNSUPPORTED
+        return
+    p.set_band_groups(False)
+    assert p.info["plane_band_group"] == 0
+    o0, c0 = execute(F, p, x, "roundtrip", torch.complex64)
+    assert np.array_equal(o0, o1) and np.array_equal(c0, c1)
+    small = F.Plan(n, "roundtrip", "fp32", layout=1, max_chunk_bands=1, **kw)
+    assert small.info["plane_band_group"] == group
+    o2, c2 = execute(F, small, x, "roundtrip", torch.complex64)
+    assert np.array_equal(o2, o1) and np.array_equal(c2, c1)
+    vol = n[0] * n[1] * n[2]
+    assert relerr(o1, vol * x.astype(np.complex128)) <= 2e-6
+
+
+def test_batch_fastest_autotune(F, tmp_path, monkeypatch):
+    """The autotuner may choose grouped or per-band plane stages (and every
+    other schedule) for a batch-fastest plan; results stay at the FP32 bound,
+    and a band prefix of a large batch stays inside its k-point's cube block."""
+    import torch
+    monkeypatch.setenv("FFTB_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    n, r = (64, 64, 64), 16.0
+    bands = [9, 4]
+    ks = np.array([(0.2, 0.1, -0.3), (-0.1, 0.4, 0.25)])
+    p = F.Plan(n, "roundtrip", "fp32", radius=r, kshift=ks, bands=bands, layout=1)
+    p.autotune(2)
+    line = (tmp_path / "tune.txt").read_text().strip().split()
+    assert int(line[-1]) == p.info["plane_band_group"] and line[-1] in ("0", "4")
+    gs = [p.sphere(k) for k in range(2)]
+    ngws = [len(g) for g in gs]
+    parts = [fi.complex_gaussian((b, ng), 350 + k).astype(np.complex64) for k, (ng, b) in enumerate(zip(ngws, bands))]
+    x = sph_bf(np.concatenate([q.reshape(-1) for q in parts]), ngws, bands)
+    out, cube = execute(F, p, x, "roundtrip", torch.complex64)
+    vol = 64 ** 3
+    assert relerr(out, vol * x.astype(np.complex128)) <= 2e-6
+    blk = cube[9 * vol:13 * vol].reshape(64, 64, 64, 4)
+    assert relerr(blk[..., 3], oracle.g2r(gs[1], parts[1][3].astype(np.complex128), n)) <= 2e-6

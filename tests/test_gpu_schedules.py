@@ -97,6 +97,6 @@ def test_schedule_errors_and_autotune(F, tmp_path, monkeypatch):
     torch.cuda.synchronize()
     assert relerr(out.cpu().numpy(), 128 ** 3 * c.reshape(-1).astype(np.complex128)) <= 2e-6
     line = (tmp_path / "tune.txt").read_text().strip().split()
-    assert 0 <= int(line[-3]) <= 3 and line[-2] in ("0", "1") and line[-1] in ("0", "1")
-    assert int(line[-3]) == plan.info["radix_schedule_plane"] and int(line[-2]) == plan.info["radix_schedule_stick"]
-    assert int(line[-1]) == plan.info["dependent_launch"]
+    assert 0 <= int(line[-4]) <= 3 and line[-3] in ("0", "1") and line[-2] in ("0", "1") and line[-1] == "0"
+    assert int(line[-4]) == plan.info["radix_schedule_plane"] and int(line[-3]) == plan.info["radix_schedule_stick"]
+    assert int(line[-2]) == plan.info["dependent_launch"]
