@@ -1203,7 +1203,7 @@ std::string tune_key(const fftb_plan_s* p) {
   cudaGetDeviceProperties(&prop, p->device);
   std::ostringstream k;
   k << p->n[0] << "x" << p->n[1] << "x" << p->n[2] << "|S" << p->smax << "|X" << p->xmax << "|B" << p->total_bands
-    << "|K" << p->nk << "|d" << (int)p->dir << "|p" << (int)p->prec << "|" << prop.name;
+    << "|K" << p->nk << "|d" << (int)p->dir << "|p" << (int)p->prec << "|L" << p->layout << "|" << prop.name;
   std::string out = k.str();
   for (char& c : out)
     if (c == ' ') c = '_';

@@ -25,9 +25,17 @@ namespace {
 // lines per warp of the length-N engine (both plane lengths are N)
 template <int N> __host__ __device__ constexpr int bg_wx() { return 32 / Line<N>::G; }
 
+// Elements from one band's slab plane to the next: N rows of a_pitch(xmax),
+// rounded up to 8 past a multiple of 16, so that the lanes of two bands that
+// read one x-task position (a half warp of 8-byte accesses) fall on the two
+// halves of the banks.
+__host__ __device__ constexpr int bg_abuf(int n, int xmax) {
+  return n * a_pitch(xmax) + ((8 - (n * a_pitch(xmax)) % 16) + 16) % 16;
+}
+
 template <int N, int BG> size_t bg_smem(int xmax) {
   constexpr int SCR = bg_wx<N>() * Line<N>::PITCH;
-  return sizeof(float2) * ((size_t)BG * N * a_pitch(xmax) + (size_t)PlaneCfg<float>::NW * SCR + N);
+  return sizeof(float2) * ((size_t)BG * bg_abuf(N, xmax) + (size_t)PlaneCfg<float>::NW * SCR + N);
 }
 
 template <int N, int MODE, int BG>
@@ -44,7 +52,7 @@ __global__ void __launch_bounds__(PlaneCfg<float>::NW * 32, (plane_minb<float, N
   const int n2 = L.g.n2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane % LN::G, l = lane / LN::G;
-  const int abuf = N * a_pitch(L.g.xmax);
+  const int abuf = bg_abuf(N, L.g.xmax);
   C* A0 = reinterpret_cast<C*>(smem_raw);
   C* scr = A0 + BG * abuf + warp * SCR;
   C* tw = A0 + BG * abuf + NW * SCR;
