@@ -248,6 +248,20 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
 #define FFTB_PLANE_NW 8
 #endif
 template <typename T> struct PlaneCfg { static constexpr int NW = FFTB_PLANE_NW; };
+
+// In the variant with slab planes in global memory (EF), data read or written
+// once per plane (cube rows, the stick row) takes the evict-first cache
+// policy (ld/st.global.cs), so that it does not push the slab planes out of
+// L2. Elsewhere plain accesses keep the end of a written cube in L2 for the
+// next stage of a round trip.
+template <bool EF, typename C> __device__ __forceinline__ C ld_once(const C* p) {
+  if constexpr (EF) return __ldcs(p);
+  else return *p;
+}
+template <bool EF, typename C> __device__ __forceinline__ void st_once(C* p, C v) {
+  if constexpr (EF) __stcs(p, v);
+  else *p = v;
+}
 // resident CTAs per SM the register allocation must allow (measured best)
 template <typename T, int N0> __host__ __device__ constexpr int plane_minb() {
 #ifdef FFTB_PLANE_MINB
@@ -486,7 +500,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
             for (int j = 0; j < LY::R0; ++j) {
               const int d = ysigned(LY::first_pos(gy, m, j)) - ylo;
-              v[m * LY::R0 + j] = (unsigned)d < (unsigned)len ? Tr[sa + d] : czero<C>();
+              if constexpr (PF) v[m * LY::R0 + j] = (unsigned)d < (unsigned)len ? Tr[sa + d] : czero<C>();
+              else v[m * LY::R0 + j] = (unsigned)d < (unsigned)len ? ld_once<AG>(Tr + sa + d) : czero<C>();
             }
         } else {
           const int sbeg = __shfl_sync(0xffffffffu, ci.x, 0);
@@ -495,7 +510,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
           __syncwarp();
           for (int s = sbeg + lane; s < send; s += 32) {
             const int xy = sxy[s];
-            scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)] = Tr[s];
+            if constexpr (PF) scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)] = Tr[s];
+            else scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)] = ld_once<AG>(Tr + s);
           }
           __syncwarp();
 #pragma unroll
@@ -544,13 +560,13 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
             for (int m = 0; m < EX / LX::RL; ++m)
 #pragma unroll
-              for (int j = 0; j < LX::RL; ++j) out[LX::last_pos(gx, m, j)] = v[m * LX::RL + j];
+              for (int j = 0; j < LX::RL; ++j) st_once<AG>(out + LX::last_pos(gx, m, j), v[m * LX::RL + j]);
           } else if (live) {  // batch-fastest cube: points B_k apart
             C* out = static_cast<C*>(L.cube_out) + plane + (size_t)row * N0 * cst;
 #pragma unroll
             for (int m = 0; m < EX / LX::RL; ++m)
 #pragma unroll
-              for (int j = 0; j < LX::RL; ++j) out[(size_t)LX::last_pos(gx, m, j) * cst] = v[m * LX::RL + j];
+              for (int j = 0; j < LX::RL; ++j) st_once<AG>(out + (size_t)LX::last_pos(gx, m, j) * cst, v[m * LX::RL + j]);
           }
         } else {
           // V(r) * psi(r), then back to first-pass order and x-DFT (-)
@@ -619,14 +635,14 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
           for (int m = 0; m < EX / LX::R0; ++m)
 #pragma unroll
             for (int j = 0; j < LX::R0; ++j)
-              v[m * LX::R0 + j] = live ? in[LX::first_pos(gx, m, j)] : czero<C>();
+              v[m * LX::R0 + j] = live ? ld_once<AG>(in + LX::first_pos(gx, m, j)) : czero<C>();
         } else {  // batch-fastest cube: points B_k apart
           const C* in = static_cast<const C*>(L.cube_in) + plane + (size_t)(live ? row : 0) * N0 * cst;
 #pragma unroll
           for (int m = 0; m < EX / LX::R0; ++m)
 #pragma unroll
             for (int j = 0; j < LX::R0; ++j)
-              v[m * LX::R0 + j] = live ? in[(size_t)LX::first_pos(gx, m, j) * cst] : czero<C>();
+              v[m * LX::R0 + j] = live ? ld_once<AG>(in + (size_t)LX::first_pos(gx, m, j) * cst) : czero<C>();
         }
         if constexpr (TC) LX::template run_tc<-1>(v, gx, rowx, scr, tw0, tcx, wx_m);
         else LX::template run<-1>(v, gx, rowx, tw0, tcx);
