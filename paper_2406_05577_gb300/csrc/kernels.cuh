@@ -132,13 +132,23 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
     if constexpr (MODE == M_G2R) {
       const C* in = static_cast<const C*>(L.sph_in) + k.sph;
       const int len = k.si.y - k.si.x;
+      if (k.st == 1) {  // band-major: the stick's entries are adjacent
 #pragma unroll
-      for (int m = 0; m < EZ / LZ::R0; ++m)
+        for (int m = 0; m < EZ / LZ::R0; ++m)
 #pragma unroll
-        for (int j = 0; j < LZ::R0; ++j) {
-          const int d = zsigned(LZ::first_pos(g, m, j)) - k.si.w;
-          v[m * LZ::R0 + j] = (unsigned)d < (unsigned)len ? in[(int64_t)(k.si.z + d) * k.st] : czero<C>();
-        }
+          for (int j = 0; j < LZ::R0; ++j) {
+            const int d = zsigned(LZ::first_pos(g, m, j)) - k.si.w;
+            v[m * LZ::R0 + j] = (unsigned)d < (unsigned)len ? in[k.si.z + d] : czero<C>();
+          }
+      } else {  // batch-fastest: B_k apart
+#pragma unroll
+        for (int m = 0; m < EZ / LZ::R0; ++m)
+#pragma unroll
+          for (int j = 0; j < LZ::R0; ++j) {
+            const int d = zsigned(LZ::first_pos(g, m, j)) - k.si.w;
+            v[m * LZ::R0 + j] = (unsigned)d < (unsigned)len ? in[(int64_t)(k.si.z + d) * k.st] : czero<C>();
+          }
+      }
     } else {
       const C* Tb = static_cast<const C*>(L.T) + (size_t)k.bl * N2 * smax + k.s0 + (l < k.nl ? l : 0);
 #pragma unroll
@@ -166,13 +176,23 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
       if (k.canon) {
         if (l < k.nl) {
           const int len = k.si.y - k.si.x;
+          if (k.st == 1) {
 #pragma unroll
-          for (int m = 0; m < EZ / LZ::RL; ++m)
+            for (int m = 0; m < EZ / LZ::RL; ++m)
 #pragma unroll
-            for (int j = 0; j < LZ::RL; ++j) {
-              const int d = zsigned(LZ::last_pos(g, m, j)) - k.si.w;
-              if ((unsigned)d < (unsigned)len) out[(int64_t)(k.si.z + d) * k.st] = v[m * LZ::RL + j];
-            }
+              for (int j = 0; j < LZ::RL; ++j) {
+                const int d = zsigned(LZ::last_pos(g, m, j)) - k.si.w;
+                if ((unsigned)d < (unsigned)len) out[k.si.z + d] = v[m * LZ::RL + j];
+              }
+          } else {
+#pragma unroll
+            for (int m = 0; m < EZ / LZ::RL; ++m)
+#pragma unroll
+              for (int j = 0; j < LZ::RL; ++j) {
+                const int d = zsigned(LZ::last_pos(g, m, j)) - k.si.w;
+                if ((unsigned)d < (unsigned)len) out[(int64_t)(k.si.z + d) * k.st] = v[m * LZ::RL + j];
+              }
+          }
         }
       } else {
         const int ea = __shfl_sync(0xffffffffu, k.si.x, 0);
