@@ -250,6 +250,13 @@ def cpu_model():
                 return line.split(":", 1)[1].strip()
     except OSError:
         pass
+    try:  # Arm hosts name the core in lscpu only
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     import platform
     return platform.processor() or platform.machine()
 
