@@ -46,22 +46,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// longest suspension of one try_wait inside a bounded wait (the thread
-// resumes as soon as the phase completes; the bound is checked in between)
-constexpr uint32_t WAIT_SUSPEND_NS = 100000;
-
-// As mbar_try_wait, but a thread whose phase is not complete may stay
-// suspended for up to `hint_ns` (it resumes as soon as the phase completes):
-// a waiting warp then does not spin through issue slots the others need.
-__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
-      : "memory");
-  return ok != 0;
-}
 
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
@@ -74,7 +58,7 @@ __device__ __forceinline__ uint64_t global_ns() {
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
-  while (!mbar_try_wait_hint(bar, parity, WAIT_SUSPEND_NS)) {
+  while (!mbar_try_wait(bar, parity)) {
     if (global_ns() - t0 > limit_ns) return false;
   }
   return true;
