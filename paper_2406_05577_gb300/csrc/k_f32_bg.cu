@@ -22,6 +22,19 @@
 namespace fftb {
 namespace {
 
+// warps per CTA and resident CTAs per SM the register allocation allows
+#ifndef FFTB_BG_NW
+#define FFTB_BG_NW 8
+#endif
+constexpr int BG_NW = FFTB_BG_NW;
+template <int N> __host__ __device__ constexpr int bg_minb() {
+#ifdef FFTB_BG_MINB
+  return FFTB_BG_MINB;
+#else
+  return plane_minb<float, N>();
+#endif
+}
+
 // lines per warp of the length-N engine (both plane lengths are N)
 template <int N> __host__ __device__ constexpr int bg_wx() { return 32 / Line<N>::G; }
 
@@ -35,14 +48,14 @@ __host__ __device__ constexpr int bg_abuf(int n, int xmax) {
 
 template <int N, int BG> size_t bg_smem(int xmax) {
   constexpr int SCR = bg_wx<N>() * Line<N>::PITCH;
-  return sizeof(float2) * ((size_t)BG * bg_abuf(N, xmax) + (size_t)PlaneCfg<float>::NW * SCR + N);
+  return sizeof(float2) * ((size_t)BG * bg_abuf(N, xmax) + (size_t)BG_NW * SCR + N);
 }
 
 template <int N, int MODE, int BG>
-__global__ void __launch_bounds__(PlaneCfg<float>::NW * 32, (plane_minb<float, N>())) k_plane_bg(const Launch L) {
+__global__ void __launch_bounds__(BG_NW * 32, (bg_minb<N>())) k_plane_bg(const Launch L) {
   using C = float2;
   using LN = Line<N>;
-  constexpr int NW = PlaneCfg<float>::NW, NT = NW * 32;
+  constexpr int NW = BG_NW, NT = NW * 32;
   constexpr int W = bg_wx<N>(), E = LN::E;
   constexpr int RPT = W / BG;  // rows per x task
   static_assert(W % BG == 0, "a warp's lines must hold whole band groups");
@@ -248,7 +261,7 @@ template <int N, int BG> cudaError_t go_bg(int mode, const Launch& L) {
   const size_t smem = bg_smem<N, BG>(L.g.xmax);
   const int units = L.ngrp * L.g.n2;
   const dim3 grid(L.plane_ctas > 0 ? min(L.plane_ctas, units) : units);
-  constexpr int NT = PlaneCfg<float>::NW * 32;
+  constexpr int NT = BG_NW * 32;
   if (mode == M_G2R) return launch_k(k_plane_bg<N, M_G2R, BG>, grid, NT, smem, L, L);
   return launch_k(k_plane_bg<N, M_R2G, BG>, grid, NT, smem, L, L);
 }
@@ -300,7 +313,7 @@ int plane_bg_occupancy(int mode, int n, int xmax) {
 #define C_(N)                                                                                          \
   case N:                                                                                              \
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bg_fn<N, bg_of<N>()>(mode),              \
-                                                         PlaneCfg<float>::NW * 32,                     \
+                                                         BG_NW * 32,                                   \
                                                          bg_smem<N, bg_of<N>()>(xmax)) == cudaSuccess \
                ? nb                                                                                    \
                : 0;
