@@ -395,6 +395,7 @@ def run_ours(args):
     # timed region 1: steps bracketed by events, L2 flushed in between
     sampler = ClockSampler()
     launches0 = plan.launches()
+    graphs0 = fftb.fftb_plan_get_info(plan.handle)["graph_launches"]
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
@@ -409,6 +410,7 @@ def run_ours(args):
         dist.barrier()
     clocks = sampler.stop()
     launches = plan.launches() - launches0
+    graph_steps = fftb.fftb_plan_get_info(plan.handle)["graph_launches"] - graphs0
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = sum(step_ms) / len(step_ms)
     from paper_2406_05577_gb300.shard import max_over_ranks
@@ -658,7 +660,7 @@ def run_ours(args):
                 "config": {"workload": w.desc, "name": w.name, "grid": list(w.n), "radius": w.radius,
                            "ngw": ngws, "bands_per_gpu": w.total_bands, "precision": "fp32",
                            "parallelism": f"bands x{world}", "chunk_bands": plan.info["chunk_bands"],
-                           "graph": w.graph, "autotuned": w.tune,
+                           "graph": w.graph, "graph_launches_in_timed_steps": graph_steps, "autotuned": w.tune,
                            "l2": "flushed between timed steps (256 MiB write)"},
                 "rel_l2": err,
                 "fp64_gpu": fp64,

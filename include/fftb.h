@@ -126,6 +126,7 @@ typedef struct {
                               G->r / r->G plane stages one CTA runs together, so cube
                               rows move band-contiguous (4 up to 96 points, 2 at 128);
                               0: one band per plane (every other plan)                */
+  int64_t graph_launches;     /* executes so far that ran as one CUDA graph launch       */
 } fftb_plan_info_t;
 
 /* Builds the spheres, stick/slab tables and twiddles on the host, uploads
@@ -200,9 +201,11 @@ fftb_status fftb_plan_stage_times(fftb_plan plan, double* ms, int64_t* launches)
  * it sees a given set of buffers (in, out, cube, potential) and replays the
  * instantiated graph on later calls with the same buffers; new buffers update
  * the graph. Recording and instantiation allocate host-side driver
- * resources. Not used while per-kernel timing is enabled, on the legacy
- * default stream (NULL), or when `stream` is itself being captured (the
- * kernels then go into the caller's graph). Disabled by default. */
+ * resources. On the legacy default stream (NULL), which cannot be captured,
+ * the graph is recorded on a plan-owned stream and launched on the default
+ * stream. Not used while per-kernel timing is enabled or when `stream` is
+ * itself being captured (the kernels then go into the caller's graph).
+ * Disabled by default. */
 fftb_status fftb_plan_set_graph(fftb_plan plan, int32_t enable);
 
 /* Autotuner: times the candidate schedules of this plan -- first the kernel

@@ -95,6 +95,8 @@ struct fftb_plan_s {
   std::vector<int2> groups;        // (first band, bands) of every group, k-point by k-point
   std::vector<int32_t> band_grp;   // group of a band that starts one, else -1
   void* d_groups = nullptr;
+  cudaStream_t cap_stream = nullptr;  // graph capture for executes on the legacy default stream
+  int64_t graph_launches = 0;         // executes that replayed (or first launched) a recorded graph
   int device = 0;
   int32_t plane_ctas[3] = {0, 0, 0};  // persistent CTAs: G->r, r->G, apply
   int32_t a_bufs = 2;                 // slab-plane buffers of the plane stage
@@ -255,6 +257,7 @@ void release(fftb_plan_s* p) {
   if (p->h_status) cudaFreeHost(p->h_status);
   if (p->d_tc5w) cudaFree(p->d_tc5w);
   if (p->d_groups) cudaFree(p->d_groups);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   delete p;
 }
 
@@ -626,6 +629,7 @@ FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) 
   info->radix_schedule_stick = p->sched_stick;
   info->dependent_launch = p->pdl ? 1 : 0;
   info->plane_band_group = p->bg;
+  info->graph_launches = p->graph_launches;
   return FFTB_OK;
 }
 
@@ -791,22 +795,27 @@ static fftb_status enqueue(fftb_plan_s* p, int bands, const void* in, void* out,
   return FFTB_OK;
 }
 
-// Direct launches, or the recorded CUDA graph of this buffer set.
+// Direct launches, or the recorded CUDA graph of this buffer set. The legacy
+// default stream cannot be captured: for it the graph is recorded on a
+// plan-owned stream and launched on the default stream.
 static fftb_status launch_all(fftb_plan_s* p, int bands, const void* in, void* out, void* cube, cudaStream_t s) {
-  bool graph = p->use_graph && !p->timing && s != nullptr && bands == p->total_bands;
-  if (graph) {
+  bool graph = p->use_graph && !p->timing && bands == p->total_bands;
+  if (graph && s) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) graph = false;
   }
   if (!graph) return enqueue(p, bands, in, out, cube, s);
+  if (!s && !p->cap_stream && cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(FFTB_ERR_CUDA, "capture stream creation failed");
+  cudaStream_t cap = s ? s : p->cap_stream;
   const int64_t per_exec = (int64_t)count_chunks(p, 0, p->total_bands) * kernels_per_chunk(p->dir);
   if (!(p->gexec && p->g_in == in && p->g_out == out && p->g_cube == cube && p->g_V == p->d_V)) {
     const int64_t before = p->launches;
-    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "graph capture");
-    fftb_status st = enqueue(p, bands, in, out, cube, s);
+    fftb_status st = enqueue(p, bands, in, out, cube, cap);
     cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(s, &g);
+    e = cudaStreamEndCapture(cap, &g);
     p->launches = before;
     if (st != FFTB_OK) {
       if (g) cudaGraphDestroy(g);
@@ -834,6 +843,7 @@ static fftb_status launch_all(fftb_plan_s* p, int bands, const void* in, void* o
   }
   cudaError_t e = cudaGraphLaunch(p->gexec, s);
   if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  ++p->graph_launches;
   p->launches += per_exec;
   return FFTB_OK;
 }

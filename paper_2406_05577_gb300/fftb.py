@@ -62,6 +62,7 @@ class fftb_plan_info_t(ctypes.Structure):
         ("radix_schedule_stick", ctypes.c_int32),
         ("dependent_launch", ctypes.c_int32),
         ("plane_band_group", ctypes.c_int32),
+        ("graph_launches", ctypes.c_int64),
     ]
 
 

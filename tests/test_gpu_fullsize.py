@@ -187,3 +187,55 @@ def test_256_roundtrip_paper_shape(F, prec, tol):
     assert relerr(out.cpu().numpy(), 256 ** 3 * c64.reshape(-1)) <= tol
     R0 = cube[: 256 ** 3].view(256, 256, 256).cpu().numpy().astype(np.complex128)
     assert relerr(R0, oracle.g2r(g, c64[0], n)) <= tol
+
+
+@pytest.mark.parametrize("name", ["sphere64_rt", "sphere96_multik", "sphere128_apply", "sphere160_large",
+                                  "sphere256_e2", "sphere64_rt_batchfast"])
+def test_bench_workloads_in_their_timed_configuration(F, name, tmp_path, monkeypatch):
+    """Every bench workload at its full size, built by bench.py itself
+    (autotuned, graph-replayed where the bench replays one): the round trip
+    of the whole batch equals N0 N1 N2 times the input, and sampled outputs of
+    two bands of the first and last k-point match the oracle's direct sums
+    (gathered on the device: the 256^3 cube set is 34 GB)."""
+    import torch
+    import bench
+    monkeypatch.setenv("FFTB_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    w = bench.Workload(name)
+    plan, _ = bench.make_plan(F, w, "fp32", torch.device("cuda", 0))
+    gs = [plan.sphere(k) for k in range(w.nk)]
+    parts = w.coefficients(gs)
+    x = torch.from_numpy(np.concatenate([(p.T if w.layout else p).reshape(-1) for p in parts])
+                         .astype(np.complex64)).cuda()
+    out = torch.empty_like(x)
+    cube = None
+    if w.direction == "roundtrip":
+        cube = torch.empty(plan.info["cube_elems"], dtype=torch.complex64, device="cuda")
+    for _ in range(2):  # the second run replays the recorded graph where there is one
+        plan.execute(x, out, cube)
+    torch.cuda.synchronize()
+    plan.check()
+    vol = w.n[0] * w.n[1] * w.n[2]
+    if w.direction == "roundtrip":
+        err = (torch.linalg.vector_norm(out - vol * x) / torch.linalg.vector_norm(vol * x)).item()
+        assert err <= 2e-6
+    sph0 = np.concatenate([[0], np.cumsum([b * len(g) for b, g in zip(w.bands, gs)])])
+    band0 = np.concatenate([[0], np.cumsum(w.bands)])
+    pts = sample_points(w.n, 8, 31)
+    lin = (pts[:, 2] * w.n[1] + pts[:, 1]) * w.n[0] + pts[:, 0]
+    for k in sorted({0, w.nk - 1}):
+        g, b = gs[k], w.bands[k]
+        sel = np.array([0, b - 1])
+        c = parts[k][sel].astype(np.complex64).astype(np.complex128)
+        if w.direction == "apply":
+            v = w.potential().astype(np.float32).astype(np.float64)
+            got = out[int(sph0[k]):int(sph0[k + 1])].view(b, len(g))[torch.from_numpy(sel).cuda()].cpu().numpy()
+            assert relerr(got, oracle.apply_potential(g, c, v, w.n)) <= 2e-6
+            continue
+        if w.layout:  # [N2][N1][N0][B] per k-point
+            idx = band0[k] * vol + lin[None, :] * b + sel[:, None]
+        else:         # [B][N2][N1][N0]
+            idx = (band0[k] + sel[:, None]) * vol + lin[None, :]
+        got = cube[torch.from_numpy(idx.reshape(-1).astype(np.int64)).cuda()].cpu().numpy().reshape(2, -1)
+        assert relerr(got, oracle.g2r_points(g, c, w.n, pts)) <= 2e-6
+    del cube, out, x, plan
+    torch.cuda.empty_cache()

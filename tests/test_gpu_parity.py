@@ -254,6 +254,29 @@ def test_graph_replay_and_update(F):
         assert relerr(o.cpu().numpy(), want) <= TOL["fp32"]
     assert relerr(cube.cpu().numpy(), oracle.g2r(g, c.astype(np.complex128), n).reshape(-1)) <= TOL["fp32"]
     assert plan.launches() == 3 * plan.info["kernels_per_execute"]
+    assert F.fftb_plan_get_info(plan.handle)["graph_launches"] == 3
+
+
+def test_graph_on_the_default_stream(F):
+    """The legacy default stream cannot be captured: the plan records on its
+    own stream and replays the graph on the default stream."""
+    import torch
+    n, r, bands = (32, 32, 32), 8.0, 5
+    g = oracle.sphere_gvectors(n, r)
+    c = fi.complex_gaussian((bands, len(g)), 83).astype(np.complex64)
+    plan = F.Plan(n, "roundtrip", "fp32", radius=r, bands=[bands], max_chunk_bands=2)
+    plan.set_graph(True)
+    x = torch.from_numpy(c.reshape(-1)).cuda()
+    out = torch.empty_like(x)
+    cube = torch.empty(plan.info["cube_elems"], dtype=torch.complex64, device="cuda")
+    assert torch.cuda.current_stream().cuda_stream == 0
+    for _ in range(3):
+        out.zero_()
+        plan.execute(x, out, cube)
+    torch.cuda.synchronize()
+    assert F.fftb_plan_get_info(plan.handle)["graph_launches"] == 3
+    assert relerr(out.cpu().numpy(), np.prod(n) * c.reshape(-1).astype(np.complex128)) <= TOL["fp32"]
+    assert relerr(cube.cpu().numpy(), oracle.g2r(g, c.astype(np.complex128), n).reshape(-1)) <= TOL["fp32"]
 
 
 def test_autotune_keeps_results(F, tmp_path, monkeypatch):
