@@ -49,7 +49,7 @@ class Workload:
             self.n, self.radius, self.kshift, self.bands = (64, 64, 64), 16.0, None, [64]
             self.direction, self.desc = "roundtrip", \
                 "64^3 grid, |G|<=16 (17077 G), 64 bands, G->r->G round trip, cube kept in HBM"
-            self.envelope, self.seed, self.graph, self.tune = 8.0, 2, False, True
+            self.envelope, self.seed, self.graph, self.tune = 8.0, 2, True, True
         elif name == "sphere64_rt_batchfast":
             self.n, self.radius, self.kshift, self.bands = (64, 64, 64), 16.0, None, [64]
             self.direction, self.desc = "roundtrip", \
