@@ -305,6 +305,13 @@ template <int N0, int N1, int V = 0> __host__ __device__ constexpr int plane_scr
 template <typename C> __host__ __device__ constexpr int stage_pitch(int n) {
   return n + ((int)(64 / sizeof(C)) - n % (int)(128 / sizeof(C)) + (int)(128 / sizeof(C))) % (int)(128 / sizeof(C));
 }
+// Pitch of the staged rows of an r -> G x task. For 64-point rows the task's
+// rows arrive as one bulk copy, unpadded (measured faster: the copy-issue
+// instructions it saves outweigh the two-way bank conflicts of reading two
+// rows 512 bytes apart); longer rows are copied one by one at stage_pitch.
+template <typename C, int N0> __host__ __device__ constexpr int pf_row_pitch() {
+  return N0 == 64 ? N0 : stage_pitch<C>(N0);
+}
 // The r -> G prefetch hands every warp at least one x task per plane.
 template <typename T, int N0, int N1> __host__ __device__ constexpr bool rows_prefetchable() {
   return (N1 + 32 / Line<N0>::G - 1) / (32 / Line<N0>::G) >= PlaneCfg<T>::NW;
@@ -316,7 +323,7 @@ template <typename T, int N0, int N1> size_t plane_pf_bytes(int mode, int tp) {
   using C = typename cplx<T>::type;
   constexpr int NW = PlaneCfg<T>::NW, WX = 32 / Line<N0>::G;
   if (mode == 0) return 0;
-  if (mode == M_R2G) return sizeof(C) * (size_t)NW * WX * stage_pitch<C>(N0) + 8 * NW;
+  if (mode == M_R2G) return sizeof(C) * (size_t)NW * WX * pf_row_pitch<C, N0>() + 8 * NW;
   return sizeof(C) * (size_t)tp + 16;
 }
 template <typename T, int N0, int N1, int V = 0>
@@ -363,7 +370,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   C* tw0 = sbase + NW * SCR;
   C* tw1 = tw0 + N0;
   // prefetch staging (PF): a stick row, or NW blocks of WX cube rows at pitch RP
-  constexpr int RP = stage_pitch<C>(N0);
+  constexpr int RP = pf_row_pitch<C, N0>();
   C* stg = tw1 + N1;
   uint64_t* bars = reinterpret_cast<uint64_t*>(stg + (MODE == M_R2G ? NW * WX * RP : L.g.smax));
   C* wst = stg + warp * (WX * RP);
@@ -427,7 +434,11 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
                    (size_t)r0 * N0;
     fence_proxy_async_smem();
     mbar_arrive_expect(bars + warp, (uint32_t)(nr * N0 * sizeof(C)));
-    for (int r = 0; r < nr; ++r) bulk_g2s(wst + r * RP, src + (size_t)r * N0, (uint32_t)(N0 * sizeof(C)), bars + warp);
+    if constexpr (RP == N0) {
+      bulk_g2s(wst, src, (uint32_t)(nr * N0 * sizeof(C)), bars + warp);
+    } else {
+      for (int r = 0; r < nr; ++r) bulk_g2s(wst + r * RP, src + (size_t)r * N0, (uint32_t)(N0 * sizeof(C)), bars + warp);
+    }
   };
   // waits for the outstanding phase of barrier b; false if the limit ran out
   auto await = [&](uint64_t* b) {
