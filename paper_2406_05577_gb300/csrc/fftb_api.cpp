@@ -103,6 +103,7 @@ struct fftb_plan_s {
   bool a_glob = false;                // slab planes in global memory (FP64, large planes)
   void* d_A = nullptr;                // those slab planes, one block per persistent CTA
   size_t A_bytes = 0;
+  int32_t a_blocks = 0;               // CTA blocks d_A holds
   // device memory
   void* d_tables = nullptr;
   size_t tables_bytes = 0;
@@ -196,15 +197,15 @@ fftb_status configure_planes(fftb_plan_s* p) {
     p->pf_fit[i] = false;
     p->pf_occ[i] = 0;
   }
-  if (p->prec_kernel == P_F32 && !p->a_glob) {
+  if (p->prec_kernel == P_F32) {
     // prefetching plane kernels where their staging fits in shared memory
     for (int i = 0; i < 3; ++i) {
-      if (!plane_pf_supported(modes[i], p->n[0], p->n[1]) ||
-          plane_pf_smem(modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs, p->tpitch) > kSmemLimit)
+      if (!plane_pf_supported(modes[i], p->n[0], p->n[1], p->a_glob) ||
+          plane_pf_smem(modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs, p->tpitch, p->a_glob) > kSmemLimit)
         continue;
-      e = prepare_plane_pf(modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs, p->tpitch);
+      e = prepare_plane_pf(modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs, p->tpitch, p->a_glob);
       if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
-      p->pf_occ[i] = plane_pf_occupancy(modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs, p->tpitch);
+      p->pf_occ[i] = plane_pf_occupancy(modes[i], p->n[0], p->n[1], p->xmax, p->a_bufs, p->tpitch, p->a_glob);
       p->pf_fit[i] = p->pf_occ[i] >= 1;
     }
   }
@@ -569,8 +570,12 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
     }
   }
   if (p->a_glob) {
-    // one double-buffered slab-plane block per persistent CTA (the most any mode launches)
-    const int ctas = std::max(p->plane_ctas[0], std::max(p->plane_ctas[1], p->plane_ctas[2]));
+    // one double-buffered slab-plane block per persistent CTA: as many as the
+    // most resident CTAs of any plane kernel variant (plain or prefetching)
+    int occ = 1;
+    for (int i = 0; i < 3; ++i) occ = std::max({occ, p->plane_occ[i], p->pf_fit[i] ? p->pf_occ[i] : 0});
+    const int ctas = std::max({p->sms * occ, p->plane_ctas[0], p->plane_ctas[1], p->plane_ctas[2]});
+    p->a_blocks = ctas;
     p->A_bytes = (size_t)ctas * p->a_bufs * p->n[1] * (size_t)(p->xmax + 16) * p->csize;
     e = cudaMalloc(&p->d_A, p->A_bytes);
     if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaMalloc slab planes failed"); }
@@ -747,6 +752,7 @@ static fftb_status enqueue(fftb_plan_s* p, int bands, const void* in, void* out,
   L.V = p->d_V;
   L.a_bufs = p->a_bufs;
   L.a_glob = p->d_A;
+  L.a_blocks = p->a_blocks;
   L.inject = p->inject;
   L.status = p->d_status;
   L.pdl = p->pdl ? 1 : 0;
@@ -1416,7 +1422,8 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
     return FFTB_OK;
   };
   // stage 1: kernel variant (slab-plane buffers, prefetch level), each with a
-  // full wave of persistent plane CTAs and the plan's chunk
+  // full wave of persistent plane CTAs, at the plan's chunk and at the
+  // largest chunk (a variant with fewer resident CTAs can need long launches)
   std::vector<int> nbufs = {saved.a_bufs};
   {
     const int other = 3 - saved.a_bufs;
@@ -1427,6 +1434,9 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   if (p->alt_stick_ok) stick_scheds.push_back(1);
   std::vector<int> bgs = {0};
   if (p->bg_size) bgs.push_back(p->bg_size);
+  std::vector<int> chunks1 = {saved.chunk};
+  if (max_chunk != saved.chunk) chunks1.push_back(max_chunk);
+  for (int ck : chunks1)
   for (int bgv : bgs)
   for (int nb : nbufs) {
     if (st != FFTB_OK) break;
@@ -1445,6 +1455,7 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
           c.sched_plane = sp;
           c.sched_stick = ss;
           c.bg = bgv;
+          c.chunk = ck;
           c.tiles = c.tiles ? -1 : 0;              // z-stage: the same kind, one full wave of its schedule
           c.ctas[0] = c.ctas[1] = c.ctas[2] = -1;  // one full wave of the variant
           st = apply_choice(p, c);

@@ -71,6 +71,7 @@ struct Launch {
   int32_t plane_ctas;   // persistent plane-stage CTAs (0: one per plane)
   int32_t a_bufs;       // slab-plane buffers of the plane stage (1 or 2)
   void* a_glob;         // slab planes in global memory (per CTA), or NULL: shared memory
+  int32_t a_blocks;     // per-CTA slab-plane blocks a_glob holds (a launch uses at most that many CTAs)
   int32_t pf;           // plane stage: prefetch its inputs with bulk async copies
   int32_t inject;       // INJECT_* bits (tests of the bounded waits)
   int32_t* status;      // device-visible status word (STATUS_* bits), set on a failed wait
@@ -106,10 +107,11 @@ cudaError_t launch_plane(int prec, int mode, const Launch& L);
 // FP32 plane kernels with bulk-copy prefetch of their inputs (mode M_*; tp =
 // the stick-row pitch Geo::smax). Unsupported combinations return false, 0
 // or cudaErrorInvalidValue.
-bool plane_pf_supported(int mode, int n0, int n1);
-size_t plane_pf_smem(int mode, int n0, int n1, int xmax, int a_bufs, int tp);
-cudaError_t prepare_plane_pf(int mode, int n0, int n1, int xmax, int a_bufs, int tp);
-int plane_pf_occupancy(int mode, int n0, int n1, int xmax, int a_bufs, int tp);
+// ag: the variant with slab planes in global memory (grids 128-256).
+bool plane_pf_supported(int mode, int n0, int n1, bool ag = false);
+size_t plane_pf_smem(int mode, int n0, int n1, int xmax, int a_bufs, int tp, bool ag = false);
+cudaError_t prepare_plane_pf(int mode, int n0, int n1, int xmax, int a_bufs, int tp, bool ag = false);
+int plane_pf_occupancy(int mode, int n0, int n1, int xmax, int a_bufs, int tp, bool ag = false);
 cudaError_t launch_plane_pf(int mode, const Launch& L);
 // FP32 kernels with the alternative radix schedule of a length (k_f32_alt.cu;
 // lengths 64, 96, 128, 160): whether n has one, shared memory, kernel

@@ -818,7 +818,9 @@ template <typename T, bool TC, int N> cudaError_t go_plane(int mode, const Launc
     if (L.a_glob) {  // slab planes too large for shared memory: per-CTA blocks of a global buffer
       const size_t smem = plane_smem_c<T, N, N>(L.g.xmax, L.a_bufs, true);
       const int nplanes = L.nb * L.g.n2;
-      const dim3 grid(min(L.plane_ctas, nplanes));
+      const int ctas = min(min(L.plane_ctas, nplanes), L.a_blocks);  // never more CTAs than slab-plane blocks
+      if (ctas < 1) return cudaErrorInvalidValue;
+      const dim3 grid(ctas);
       constexpr int NT = PlaneCfg<T>::NW * 32;
       if (mode == M_G2R) return launch_k(k_plane<T, N, N, M_G2R, TC, true>, grid, NT, smem, L, L);
       if (mode == M_R2G) return launch_k(k_plane<T, N, N, M_R2G, TC, true>, grid, NT, smem, L, L);

@@ -248,3 +248,24 @@ def test_dependent_launch_same_results(F, n, r, prec, sched):
     vol = n[0] * n[1] * n[2]
     tol = 1e-12 if prec == "fp64" else (1e-5 if prec == "mixed" else 2e-6)
     assert relerr(cube1[:vol].reshape(n[2], n[1], n[0]), oracle.g2r(g, c[0].astype(np.complex128), n)) <= tol
+
+
+def test_prefetch_with_global_slab_planes(F):
+    """256^3 keeps its slab planes in global memory; the prefetching plane
+    kernels of that variant give the plain kernels' results bit for bit."""
+    import torch
+    n, r, bands = (256, 256, 256), 64.0, 2
+    plan = F.Plan(n, "roundtrip", "fp32", radius=r, bands=[bands])
+    assert plan.info["slab_planes_global"] == 1
+    g = plan.sphere(0)
+    c = fi.complex_gaussian((bands, len(g)), 85).astype(np.complex64)
+    x = torch.from_numpy(c.reshape(-1)).cuda()
+    plan.set_prefetch(2)
+    assert plan.info["prefetch"] & 2  # r -> G at least (its staging is small)
+    out_pf, cube_pf = run(plan, x, "roundtrip")
+    plan.check()
+    plan.set_prefetch(0)
+    assert plan.info["prefetch"] == 0
+    out0, cube0 = run(plan, x, "roundtrip")
+    assert np.array_equal(out_pf, out0) and np.array_equal(cube_pf, cube0)
+    assert relerr(out_pf, 256 ** 3 * c.reshape(-1).astype(np.complex128)) <= 2e-6
