@@ -233,11 +233,12 @@ fftb_status fftb_plan_autotune(fftb_plan plan, int32_t trials);
  * Errors: INVALID_ARG for a level outside 0..2. */
 fftb_status fftb_plan_set_prefetch(fftb_plan plan, int32_t level);
 
-/* Slab-plane buffers of the plane stage: 2 (default where it fits) lets a
- * CTA start the next plane's y stage while slower warps finish the current
- * plane's x stage, at twice the memory; 1 halves that memory (more resident
- * CTAs per SM on large grids, or slab planes that stay in L2 when they live
- * in global memory) for a second block barrier per plane. Resets the
+/* Slab-plane buffers of the plane stage: 2 (default where it fits in shared
+ * memory) lets a CTA start the next plane's y stage while slower warps
+ * finish the current plane's x stage, at twice the memory; 1 halves that
+ * memory (more resident CTAs per SM on large grids, or slab planes that stay
+ * in L2 when they live in global memory, where 1 is the default) for a
+ * second block barrier per plane. Resets the
  * persistent plane CTAs to one full wave; fftb_plan_autotune also tries
  * both. Errors: INVALID_ARG for a count other than 1 or 2; UNSUPPORTED when
  * 2 do not fit in shared memory. */

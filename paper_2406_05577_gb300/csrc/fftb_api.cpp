@@ -329,7 +329,11 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   const size_t smem_limit = kSmemLimit;
   if (plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, 2) > smem_limit) p->a_bufs = 1;
   if (plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, p->a_bufs) > smem_limit && p->n[0] >= 128) {
-    p->a_bufs = 2;  // slab planes in global memory, double buffered
+    // slab planes in global memory, one buffer per CTA by default (two double
+    // their L2 footprint: 30 % slower on the 256^3 round trip); room for two
+    // is allocated so that fftb_plan_set_slab_buffers and the autotuner may
+    // choose them
+    p->a_bufs = 1;
     p->a_glob = true;
   }
   if (stick_smem(p->prec_kernel, p->n[2]) > smem_limit ||
@@ -570,13 +574,13 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
     }
   }
   if (p->a_glob) {
-    // one double-buffered slab-plane block per persistent CTA: as many as the
+    // one slab-plane block (room for two buffers) per persistent CTA: as many as the
     // most resident CTAs of any plane kernel variant (plain or prefetching)
     int occ = 1;
     for (int i = 0; i < 3; ++i) occ = std::max({occ, p->plane_occ[i], p->pf_fit[i] ? p->pf_occ[i] : 0});
     const int ctas = std::max({p->sms * occ, p->plane_ctas[0], p->plane_ctas[1], p->plane_ctas[2]});
     p->a_blocks = ctas;
-    p->A_bytes = (size_t)ctas * p->a_bufs * p->n[1] * (size_t)(p->xmax + 16) * p->csize;
+    p->A_bytes = (size_t)ctas * 2 * p->n[1] * (size_t)(p->xmax + 16) * p->csize;
     e = cudaMalloc(&p->d_A, p->A_bytes);
     if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaMalloc slab planes failed"); }
   }

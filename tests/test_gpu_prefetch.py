@@ -269,3 +269,20 @@ def test_prefetch_with_global_slab_planes(F):
     out0, cube0 = run(plan, x, "roundtrip")
     assert np.array_equal(out_pf, out0) and np.array_equal(cube_pf, cube0)
     assert relerr(out_pf, 256 ** 3 * c.reshape(-1).astype(np.complex128)) <= 2e-6
+
+
+def test_global_slab_planes_one_or_two_buffers(F):
+    """Plans whose slab planes live in global memory start with one buffer per
+    CTA and may switch to two (the allocation holds both): same results."""
+    import torch
+    n, r, bands = (256, 256, 256), 64.0, 1
+    plan = F.Plan(n, "roundtrip", "fp32", radius=r, bands=[bands])
+    assert plan.info["slab_planes_global"] == 1 and plan.info["slab_buffers"] == 1
+    g = plan.sphere(0)
+    x = torch.from_numpy(fi.complex_gaussian((bands, len(g)), 86).astype(np.complex64).reshape(-1)).cuda()
+    out1, cube1 = run(plan, x, "roundtrip")
+    plan.set_slab_buffers(2)
+    assert plan.info["slab_buffers"] == 2
+    out2, cube2 = run(plan, x, "roundtrip")
+    plan.check()
+    assert np.array_equal(out1, out2) and np.array_equal(cube1, cube2)
