@@ -127,6 +127,8 @@ typedef struct {
                               rows move band-contiguous (4 up to 96 points, 2 at 128);
                               0: one band per plane (every other plan)                */
   int64_t graph_launches;     /* executes so far that ran as one CUDA graph launch       */
+  double scale_g2r;           /* output normalisation factors (fftb_plan_set_scale)     */
+  double scale_r2g;
 } fftb_plan_info_t;
 
 /* Builds the spheres, stick/slab tables and twiddles on the host, uploads
@@ -262,6 +264,15 @@ fftb_status fftb_plan_set_radix_schedule(fftb_plan plan, int32_t plane, int32_t 
  * before touching stage data, so launch latency and prologues overlap the
  * previous kernel's tail. 0 launches them plainly. */
 fftb_status fftb_plan_set_pdl(fftb_plan plan, int32_t enable);
+
+/* Optional normalisation (both 1 by default: the transforms are unscaled as
+ * in Sec. 2.1-2.2). G->r outputs (the cube of G_TO_R and ROUNDTRIP) are
+ * multiplied by g2r; r->G outputs by r2g, and the sphere output of ROUNDTRIP
+ * and APPLY_LOCAL by g2r * r2g (the maps are linear). E.g. r2g = 1/(N0 N1 N2)
+ * makes the round trip the identity. A factor other than 1 adds one
+ * elementwise kernel over that output per execute. INVALID_ARG for a
+ * non-finite factor. */
+fftb_status fftb_plan_set_scale(fftb_plan plan, double g2r, double r2g);
 
 /* Batch-fastest FP32 plans with N0 == N1 up to 128 run their G->r and r->G
  * plane stages over groups of bands of one k-point (on by default;

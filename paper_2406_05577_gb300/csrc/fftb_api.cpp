@@ -97,6 +97,7 @@ struct fftb_plan_s {
   void* d_groups = nullptr;
   cudaStream_t cap_stream = nullptr;  // graph capture for executes on the legacy default stream
   int64_t graph_launches = 0;         // executes that replayed (or first launched) a recorded graph
+  double scale_g2r = 1.0, scale_r2g = 1.0;  // output normalisation (fftb_plan_set_scale)
   int device = 0;
   int32_t plane_ctas[3] = {0, 0, 0};  // persistent CTAs: G->r, r->G, apply
   int32_t a_bufs = 2;                 // slab-plane buffers of the plane stage
@@ -605,6 +606,16 @@ FFTB_EXPORT fftb_status fftb_plan_sphere(fftb_plan p, int32_t k, int32_t* g_out)
 }
 
 static int count_chunks(const fftb_plan_s* p, int first, int bands);
+// output scalings an execute launches: the cube by scale_g2r (G->r, round
+// trip), the sphere by the product of the factors its path applies
+static double sphere_scale(const fftb_plan_s* p) {
+  if (p->dir == FFTB_G_TO_R) return 1.0;
+  return p->scale_r2g * ((p->dir == FFTB_ROUNDTRIP || p->dir == FFTB_APPLY_LOCAL) ? p->scale_g2r : 1.0);
+}
+static int scale_launches(const fftb_plan_s* p) {
+  const bool cube = p->scale_g2r != 1.0 && (p->dir == FFTB_G_TO_R || p->dir == FFTB_ROUNDTRIP);
+  return (cube ? 1 : 0) + (sphere_scale(p) != 1.0 ? 1 : 0);
+}
 static int kernels_per_chunk(fftb_direction d) {
   switch (d) {
     case FFTB_G_TO_R: return 2;
@@ -624,7 +635,10 @@ FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) 
   info->max_sticks = p->smax;
   info->max_slabs = p->xmax;
   info->chunk_bands = p->chunk;
-  info->kernels_per_execute = count_chunks(p, 0, p->total_bands) * kernels_per_chunk(p->dir);
+  info->kernels_per_execute = count_chunks(p, 0, p->total_bands) * kernels_per_chunk(p->dir) +
+                              (p->total_bands > 0 ? scale_launches(p) : 0);
+  info->scale_g2r = p->scale_g2r;
+  info->scale_r2g = p->scale_r2g;
   info->complex_bytes = p->csize;
   info->stick_ctas = p->tiles;
   info->plane_ctas = p->plane_ctas[p->dir == FFTB_R_TO_G ? 1 : p->dir == FFTB_APPLY_LOCAL ? 2 : 0];
@@ -802,6 +816,26 @@ static fftb_status enqueue(fftb_plan_s* p, int bands, const void* in, void* out,
     }
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   }
+  // Optional normalisation, after every chunk's stages, over this call's
+  // output ranges (whole k-point blocks in the batch-fastest layout). The
+  // maps are linear: the round trip's r->G stage reads the unscaled cube and
+  // its sphere output takes both factors.
+  const int64_t vol = (int64_t)p->n[0] * p->n[1] * p->n[2];
+  if (p->scale_g2r != 1.0 && (p->dir == FFTB_G_TO_R || p->dir == FFTB_ROUNDTRIP)) {
+    unsigned char* c = static_cast<unsigned char*>(p->dir == FFTB_G_TO_R ? out : cube);
+    cudaError_t e = launch_scale(p->csize, c + (size_t)first * vol * p->csize, (int64_t)bands * vol, p->scale_g2r, L,
+                                 p->sms);
+    if (e != cudaSuccess) return cuda_fail(e, "scale launch");
+    ++p->launches;
+  }
+  const double ss = sphere_scale(p);
+  if (ss != 1.0) {
+    unsigned char* o = static_cast<unsigned char*>(out);
+    const int64_t a = p->band_sph[first], b = p->band_sph[std::min(first + bands, p->total_bands)];
+    cudaError_t e = launch_scale(p->csize, o + (size_t)a * p->csize, b - a, ss, L, p->sms);
+    if (e != cudaSuccess) return cuda_fail(e, "scale launch");
+    ++p->launches;
+  }
   return FFTB_OK;
 }
 
@@ -818,7 +852,7 @@ static fftb_status launch_all(fftb_plan_s* p, int bands, const void* in, void* o
   if (!s && !p->cap_stream && cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return fail(FFTB_ERR_CUDA, "capture stream creation failed");
   cudaStream_t cap = s ? s : p->cap_stream;
-  const int64_t per_exec = (int64_t)count_chunks(p, 0, p->total_bands) * kernels_per_chunk(p->dir);
+  const int64_t per_exec = (int64_t)count_chunks(p, 0, p->total_bands) * kernels_per_chunk(p->dir) + scale_launches(p);
   if (!(p->gexec && p->g_in == in && p->g_out == out && p->g_cube == cube && p->g_V == p->d_V)) {
     const int64_t before = p->launches;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
@@ -1051,6 +1085,18 @@ FFTB_EXPORT fftb_status fftb_plan_set_pdl(fftb_plan p, int32_t enable) {
     p->gexec = nullptr;
   }
   p->pdl = enable != 0;
+  return FFTB_OK;
+}
+
+FFTB_EXPORT fftb_status fftb_plan_set_scale(fftb_plan p, double g2r, double r2g) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (!std::isfinite(g2r) || !std::isfinite(r2g)) return fail(FFTB_ERR_INVALID_ARG, "scale factors must be finite");
+  if ((g2r != p->scale_g2r || r2g != p->scale_r2g) && p->gexec) {
+    cudaGraphExecDestroy(p->gexec);  // recorded with the other scalings
+    p->gexec = nullptr;
+  }
+  p->scale_g2r = g2r;
+  p->scale_r2g = r2g;
   return FFTB_OK;
 }
 

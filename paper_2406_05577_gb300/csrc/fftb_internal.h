@@ -131,6 +131,9 @@ size_t plane_bg_smem(int n0, int n1, int xmax, int bg);
 cudaError_t prepare_plane_bg(int n, int xmax);
 int plane_bg_occupancy(int mode, int n, int xmax);
 cudaError_t launch_plane_bg(int mode, const Launch& L);
+// Multiplies n complex elements (csize bytes each) at data by s on L.stream
+// (k_scale.cu): the optional output normalisation.
+cudaError_t launch_scale(int csize, void* data, int64_t n, double s, const Launch& L, int sms);
 cudaError_t launch_stick_alt(int mode, const Launch& L, int ctas);
 // MIXED_TC plane stage on the 5th-generation tensor cores (k_tc5.cu): the
 // union over k-points of the occupied x values [xlo, xlo + xu) and of the

@@ -63,6 +63,8 @@ class fftb_plan_info_t(ctypes.Structure):
         ("dependent_launch", ctypes.c_int32),
         ("plane_band_group", ctypes.c_int32),
         ("graph_launches", ctypes.c_int64),
+        ("scale_g2r", ctypes.c_double),
+        ("scale_r2g", ctypes.c_double),
     ]
 
 
@@ -94,6 +96,7 @@ EXPORTS = {
     "fftb_plan_set_radix_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "fftb_plan_set_pdl": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fftb_plan_set_band_groups": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "fftb_plan_set_scale": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]),
     "fftb_plan_inject": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fftb_sphere_enumerate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_double,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -254,6 +257,10 @@ def fftb_plan_set_radix_schedule(plan, plane, stick):
 
 def fftb_plan_set_pdl(plan, enable):
     _check(lib().fftb_plan_set_pdl(plan, 1 if enable else 0))
+
+
+def fftb_plan_set_scale(plan, g2r=1.0, r2g=1.0):
+    _check(lib().fftb_plan_set_scale(plan, float(g2r), float(r2g)))
 
 
 def fftb_plan_set_band_groups(plan, enable):
@@ -421,6 +428,10 @@ class Plan:
 
     def set_pdl(self, enable=True):
         fftb_plan_set_pdl(self.handle, enable)
+        self.info = fftb_plan_get_info(self.handle)
+
+    def set_scale(self, g2r=1.0, r2g=1.0):
+        fftb_plan_set_scale(self.handle, g2r, r2g)
         self.info = fftb_plan_get_info(self.handle)
 
     def set_band_groups(self, enable=True):

@@ -177,3 +177,7 @@ def test_glist_from_offsets_errors(fftb):
         fftb.fftb_glist_from_offsets(n, (0, 0, 0), (7, 7, 7), ok_off, np.zeros(2, np.int32))
     with pytest.raises(E):  # z outside the domain
         fftb.fftb_glist_from_offsets(n, (0, 0, 0), (7, 7, 3), ok_off, np.array([5], np.int32))
+
+
+def test_scale_needs_a_plan(fftb):
+    assert fftb.lib().fftb_plan_set_scale(None, 1.0, 1.0) == fftb.FFTB_ERR_INVALID_ARG
