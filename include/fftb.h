@@ -222,12 +222,13 @@ fftb_status fftb_plan_set_graph(fftb_plan plan, int32_t enable);
  * Synchronises the device. */
 fftb_status fftb_plan_autotune(fftb_plan plan, int32_t trials);
 
-/* Bulk-copy prefetch in the plane stage (FP32 plans). A prefetching plane
- * kernel receives each plane's stick row (G->r, apply) or each warp's next
- * cube rows (r->G; cube buffers 16-byte aligned, grids of 64 and up)
- * through cp.async.bulk copies completed on shared-memory mbarriers, issued
- * one step ahead of their use; the other kernels load with ordinary
- * instructions. level 0: never; 1 (default): where the staging buffers fit
+/* Bulk-copy prefetch in the plane stage (FP32 plans, slab planes in shared
+ * or in global memory). A prefetching plane kernel receives each plane's
+ * stick row (G->r, apply) or each warp's next cube rows (r->G; band-major
+ * cube buffers 16-byte aligned, grids of 64 and up) through cp.async.bulk
+ * copies completed on shared-memory mbarriers, issued one step ahead of
+ * their use; the other kernels load with ordinary instructions. Batch-
+ * fastest plans prefetch stick rows only (their cube rows are strided). level 0: never; 1 (default): where the staging buffers fit
  * in shared memory without lowering the resident CTAs per SM; 2: wherever
  * they fit. Changing the level resets the persistent plane CTAs of the
  * affected stages to one full wave; fftb_plan_autotune also tries the
