@@ -404,6 +404,24 @@ class Plan:
         fftb_execute(self.handle, self._ptr(x, cd, nin, "in"), self._ptr(out, cd, nout, "out"),
                      self._ptr(cube, cd, cub, "cube"), s.cuda_stream)
 
+    def execute_host(self, x, out, cube=None, stream=None):
+        """fftb_execute_host: x and out are contiguous CPU tensors of the
+        plan's complex type (page-locked for full-speed, overlapped copies);
+        cube (ROUNDTRIP only, optional) is a CUDA tensor. Returns when done."""
+        import torch
+        sph, cub = self.info["sphere_elems"], self.info["cube_elems"]
+        nin = cub if self.direction == FFTB_R_TO_G else sph
+        nout = cub if self.direction == FFTB_G_TO_R else sph
+        cd = self.complex_dtype
+        for t, n, what in ((x, nin, "in"), (out, nout, "out")):
+            if t.is_cuda or t.dtype != cd or not t.is_contiguous():
+                raise ValueError(f"{what}: need a contiguous CPU tensor of {cd}")
+            if t.numel() < n:
+                raise ValueError(f"{what}: need at least {n} elements, got {t.numel()}")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        fftb_execute_host(self.handle, x.data_ptr(), out.data_ptr(), self._ptr(cube, cd, cub, "cube"),
+                          s.cuda_stream)
+
     def launches(self):
         return fftb_plan_launches(self.handle)
 
@@ -448,6 +466,13 @@ class Plan:
         if self.handle:
             fftb_destroy(self.handle)
             self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
     def __del__(self):
         try:

@@ -233,6 +233,28 @@ def test_host_pipeline_matches_device_execute(F, direction):
         assert torch.equal(cube2, cd)
 
 
+def test_plan_execute_host_method_and_context(F):
+    """The Plan class's host-buffer call (pinned CPU tensors) equals the
+    device call; a plan used as a context manager is released on exit."""
+    import torch
+    n, r, bands = (32, 32, 32), 8.0, 3
+    with F.Plan(n, "roundtrip", "fp32", radius=r, bands=[bands]) as plan:
+        g = plan.sphere(0)
+        c = fi.complex_gaussian((bands, len(g)), 84).astype(np.complex64).reshape(-1)
+        x = torch.from_numpy(c).cuda()
+        out = torch.empty_like(x)
+        cube = torch.empty(plan.info["cube_elems"], dtype=torch.complex64, device="cuda")
+        plan.execute(x, out, cube)
+        torch.cuda.synchronize()
+        hin = torch.from_numpy(c).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        plan.execute_host(hin, hout)
+        assert np.array_equal(hout.numpy(), out.cpu().numpy())
+        with pytest.raises(ValueError):
+            plan.execute_host(x, hout)  # a device tensor where host memory is expected
+    assert plan.handle is None
+
+
 def test_graph_replay_and_update(F):
     import torch
     n, r, bands = (32, 32, 48), 10.0, 6
