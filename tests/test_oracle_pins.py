@@ -258,3 +258,35 @@ def test_pins_catch_swapped_axes():
     wrong = np.fft.ifftn(pad, norm="forward")
     assert relerr(wrong, brute_g2r(g, c, n)) > 0.5
     assert relerr(g2r(g, c, n), brute_g2r(g, c, n)) < 1e-13
+
+
+def test_g2r_r2g_match_bruteforce_on_random_shapes():
+    """The brute-force pins on random small grids (odd and even extents),
+    radii, k-shifts and coefficients (hypothesis, where installed)."""
+    hyp = pytest.importorskip("hypothesis")
+    from hypothesis import given, settings, strategies as st
+
+    ext = st.integers(3, 9)
+
+    @settings(max_examples=40, deadline=None)
+    @given(n=st.tuples(ext, ext, ext), frac=st.floats(0.0, 1.0), k=st.tuples(*[st.floats(-0.5, 0.5)] * 3),
+           seed=st.integers(0, 2 ** 31 - 1))
+    def check(n, frac, k, seed):
+        # the largest ball that cannot alias: |G + k| <= r needs r + |k_d| < N_d / 2 - ... per axis
+        rmax = min(n[d] // 2 - abs(k[d]) - 0.01 for d in range(3))
+        if rmax <= 0:
+            return
+        r = frac * rmax
+        try:
+            g = sphere_gvectors(n, r, np.array(k))
+        except ValueError:
+            return  # a ball that would alias is rejected, which is tested elsewhere
+        if not len(g):
+            return
+        rng = np.random.default_rng(seed)
+        c = rng.standard_normal(len(g)) + 1j * rng.standard_normal(len(g))
+        assert relerr(g2r(g, c, n), brute_g2r(g, c, n)) < 1e-13
+        R = rng.standard_normal((n[2], n[1], n[0])) + 1j * rng.standard_normal((n[2], n[1], n[0]))
+        assert relerr(r2g(g, R, n), brute_r2g(g, R, n)) < 1e-13
+
+    check()
