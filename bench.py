@@ -1,13 +1,17 @@
 """Benchmark: batched pruned sphere <-> cube FFT, bands/s.
 
-Default workload (the headline): 64^3 grid, cutoff |G| <= 16 (17077 G
-vectors), 64 bands, FP32, coefficients complex Gaussian x exp(-|G|^2/(2*64)),
-round trip G -> r -> G with the real-space cube written to HBM and read back.
-A step is one fftb_execute of the whole batch. Other workloads
-(``--workload``): 96^3 with 8 k-points and uneven band counts in one graph-
-replayed, autotuned launch sequence; 128^3 local-potential apply
-V(r) psi(r) with 256 bands; 160^3 with 512 bands streamed in band chunks; 256^3
-(sphere diameter 128) with 256 bands, the paper's own single-GPU shape.
+Default workload (the headline, the largest single-GPU configuration):
+160^3 grid, cutoff |G| <= 40 (267 761 G vectors), 512 bands, FP32
+coefficients complex Gaussian, round trip G -> r -> G with the 16.8 GB
+real-space cube set written to HBM and read back, processed in band chunks.
+A step is one fftb_execute of the whole batch. The plain FP64 GPU path and
+the split-precision tensor-core path (MIXED_TC) run the same workload beside
+it, each compared with the FP64 path's output; the 64^3 workload (|G| <= 16,
+64 bands) is timed as a second figure. Other workloads (``--workload``):
+64^3 alone, 96^3 with 8 k-points and uneven band counts in one graph-
+replayed, autotuned launch sequence; 128^3 local-potential apply V(r) psi(r)
+with 256 bands; 256^3 (sphere diameter 128) with 256 bands, the paper's own
+single-GPU shape; the 64^3 workload in the batch-fastest layout.
 
 Under torchrun each rank runs its own copy of the workload on its own GPU
 (bands are independent: weak scaling, no collective on the data path).
@@ -35,6 +39,8 @@ sys.path.insert(0, ROOT)
 
 import fftb_inputs as fi  # noqa: E402
 
+# the largest single-GPU configuration: 160^3, |G| <= 40, 512 bands
+DEFAULT_WORKLOAD = "sphere160_large"
 METRIC = "sphere-FFT bands/sec (G->r->G) and % HBM roofline, mixed vs FP64 at L2<=1e-5"
 L2_FLUSH_BYTES = 256 << 20
 
@@ -295,15 +301,19 @@ def run_reference(args):
 
 
 def stage_bytes(kind, w, info, ngws, sticks):
-    """Algorithmic (compulsory) bytes of one stage kind over the whole batch."""
+    """Bytes of one stage kind over the whole batch, as (compulsory,
+    intermediate). Compulsory bytes are the transform's own input and output
+    read or written once (the cube for the y/x stages, the sphere for the z
+    stages); intermediate bytes are the stick rows T that this design passes
+    between its z stage and its plane stage (written once, read once)."""
     c = info["complex_bytes"]
     vol = w.n[0] * w.n[1] * w.n[2]
     n2 = w.n[2]
     sph = sum(b * g for b, g in zip(w.bands, ngws))
     stk = sum(b * s * n2 for b, s in zip(w.bands, sticks))
     cube = w.total_bands * vol
-    return {"stick_g2r": (sph + stk) * c, "plane_g2r": (stk + cube) * c, "plane_r2g": (cube + stk) * c,
-            "stick_r2g": (stk + sph) * c, "plane_apply": 2 * stk * c + vol * c // 2}[kind]
+    return {"stick_g2r": (sph * c, stk * c), "plane_g2r": (cube * c, stk * c), "plane_r2g": (cube * c, stk * c),
+            "stick_r2g": (sph * c, stk * c), "plane_apply": (vol * c // 2, 2 * stk * c)}[kind]
 
 
 # FP32 arithmetic peak of the GPU from its unit counts and clock: 152 SMs x 128
@@ -333,6 +343,43 @@ def make_plan(fftb, w, prec, dev):
     if w.graph:
         plan.set_graph(True)
     return plan, v_dev
+
+
+def time_workload(fftb, name, dev, flush, stream, args):
+    """A second workload timed like the headline (FP32, autotuned, L2 flushed
+    between steps, CUDA events on the launching stream)."""
+    import torch
+    w = Workload(name)
+    plan, _ = make_plan(fftb, w, "fp32", dev)
+    spheres = [plan.sphere(k) for k in range(w.nk)]
+    ngws = [len(g) for g in spheres]
+    c = np.concatenate([(p.T if w.layout else p).reshape(-1) for p in w.coefficients(spheres)]).astype(np.complex64)
+    x = torch.from_numpy(c).to(dev)
+    out = torch.empty_like(x)
+    cube = torch.empty(plan.info["cube_elems"], dtype=torch.complex64, device=dev) \
+        if w.direction == "roundtrip" else None
+    for _ in range(args.warmup):
+        plan.execute(x, out, cube)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        plan.execute(x, out, cube)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    plan.check()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+    vol = w.n[0] * w.n[1] * w.n[2]
+    step_bytes = 2 * (sum(b * g for b, g in zip(w.bands, ngws)) + w.total_bands * vol) * 8
+    hbm, _ = peaks()
+    res = {"workload": w.desc, "value": w.total_bands / (ms / 1e3), "unit": "bands/s", "ms_per_step": ms,
+           "step_compulsory_frac": step_bytes / (ms / 1e3) / 1e9 / hbm}
+    if w.direction == "roundtrip":
+        res["rel_l2_roundtrip"] = (torch.linalg.vector_norm(out - vol * x) /
+                                   torch.linalg.vector_norm(vol * x)).item()
+    del x, out, cube, plan
+    return res
 
 
 def run_ours(args):
@@ -381,16 +428,13 @@ def run_ours(args):
     for _ in range(args.warmup):
         plan.execute(x, out, cube)
     torch.cuda.synchronize(dev)
-    # correctness of this very run
+    # correctness of this very run: a round trip returns N0 N1 N2 times its
+    # input exactly (the oracle's result); every precision is also compared
+    # with the FP64 GPU path below (rank 0)
+    err = None
     if w.direction == "roundtrip":
         vol = float(np.prod(w.n))
         err = (torch.linalg.vector_norm(out - vol * x) / torch.linalg.vector_norm(vol * x)).item()
-    else:
-        import oracle
-        v64 = w.potential().astype(np.float32).astype(np.float64)
-        got = out[: 2 * ngws[0]].cpu().numpy().astype(np.complex128).reshape(2, -1)
-        want = oracle.apply_potential(spheres[0], c[: 2 * ngws[0]].astype(np.complex128).reshape(2, -1), v64, w.n)
-        err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
 
     # timed region 1: steps bracketed by events, L2 flushed in between
     sampler = ClockSampler()
@@ -441,10 +485,13 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     dom = max((k for k in stage if stage[k][1] > 0), key=lambda k: stage[k][0])
     dom_ms, dom_n = stage[dom]
-    alg = stage_bytes(dom, w, info, ngws, sticks) / (dom_n / args.steps)  # per launch
-    achieved = alg / (dom_ms / dom_n / 1e3) / 1e9
+    comp, inter = stage_bytes(dom, w, info, ngws, sticks)
+    launches_per_step = dom_n / args.steps
+    alg = comp / launches_per_step  # compulsory bytes per launch
+    launch_s = dom_ms / dom_n / 1e3
+    achieved = alg / launch_s / 1e9
     traffic_band = ncu_traffic(w.name, dom)
-    launch_bands = w.total_bands / (dom_n / args.steps)
+    launch_bands = w.total_bands / launches_per_step
     vol = w.n[0] * w.n[1] * w.n[2]
     sph_elems = sum(b * g for b, g in zip(w.bands, ngws))
     if w.direction == "apply":
@@ -453,29 +500,37 @@ def run_ours(args):
         step_bytes = 2 * (sph_elems + w.total_bands * vol) * 8
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": alg,
+                "what": "compulsory bytes of the kernel (cube points for the y/x stages, sphere entries for the z "
+                        "stages, each once) per launch over the CUDA-event launch time",
+                "intermediate_bytes_per_launch": inter / launches_per_step,
+                "with_intermediate_gbs": (alg + inter / launches_per_step) / launch_s / 1e9,
                 "traffic": None if traffic_band is None else traffic_band * launch_bands,
                 "stage_ms_per_step": {k: v[0] / args.steps for k, v in stage.items() if v[1]},
                 "step_compulsory_gbs": step_bytes / (ms / 1e3) / 1e9,
                 "step_compulsory_frac": step_bytes / (ms / 1e3) / 1e9 / hbm}
     if roofline["traffic"] is not None:
         # the ncu DRAM bytes of one launch over the event-timed launch
-        roofline["traffic_gbs"] = roofline["traffic"] / (dom_ms / dom_n / 1e3) / 1e9
+        roofline["traffic_gbs"] = roofline["traffic"] / launch_s / 1e9
         roofline["traffic_frac"] = roofline["traffic_gbs"] / hbm
     if dom == "plane_apply":
         # the fused apply keeps the cube on chip: its kernel is bound by FP32
         # arithmetic, so it is measured in algorithmic flops against the FP32
         # peak; the byte figures stay beside it
-        tflops = stage_flops(dom, w, slabs) / (dom_n / args.steps) / (dom_ms / dom_n / 1e3) / 1e12
+        tflops = stage_flops(dom, w, slabs) / launches_per_step / launch_s / 1e12
         roofline.update({"bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": tflops / FP32_PEAK_TFLOPS, "peak_source": "derived (FP32 units x clock)",
                          "traffic": None, "algorithmic_gbs": achieved, "algorithmic_gbs_frac": achieved / hbm})
 
     if rank == 0:
         # FP64 GPU path and the split-precision tensor-core path on the same workload
-        def time_plan(prec, reps=3):
+        def time_plan(prec, reps=3, ref=None):
+            """Times one precision's plan on the same inputs; returns its
+            figures and its output (for the comparisons between precisions)."""
             p2, vd2 = make_plan(fftb, w, prec, dev)
             cdt = torch.complex128 if prec == "fp64" else torch.complex64
-            x2 = torch.from_numpy(np.concatenate([p.reshape(-1) for p in parts])).to(cdt).to(dev)
+            x2 = torch.from_numpy(np.concatenate([(p.T if w.layout else p).reshape(-1) for p in parts])) \
+                .to(torch.complex64).to(cdt).to(dev)
             o2 = torch.empty_like(x2)
             cube2 = None
             if w.direction == "roundtrip":
@@ -491,22 +546,46 @@ def run_ours(args):
                 b.record(stream)
                 evs2.append((a, b))
             torch.cuda.synchronize(dev)
+            p2.check()
             ms2 = sum(a.elapsed_time(b) for a, b in evs2) / len(evs2)
-            e2 = None
+            res = {"value": w.total_bands / (ms2 / 1e3), "ms_per_step": ms2, "ratio_vs_fp32": ms2 / ms}
             if w.direction == "roundtrip":
                 vol = float(np.prod(w.n))
-                e2 = (torch.linalg.vector_norm(o2 - vol * x2) / torch.linalg.vector_norm(vol * x2)).item()
-            del o2, x2, cube2, p2, vd2
-            return {"value": w.total_bands / (ms2 / 1e3), "ms_per_step": ms2, "ratio_vs_fp32": ms2 / ms,
-                    "rel_l2_roundtrip": e2}
+                res["rel_l2_roundtrip"] = (torch.linalg.vector_norm(o2 - vol * x2) /
+                                           torch.linalg.vector_norm(vol * x2)).item()
+            if ref is not None:
+                res["rel_l2_vs_fp64_gpu"] = rel_l2(o2, ref)
+            del x2, cube2, p2, vd2
+            return res, o2
+
+        def rel_l2(a, ref):
+            d = a.to(torch.complex128) - ref
+            return (torch.linalg.vector_norm(d) / torch.linalg.vector_norm(ref)).item()
+
+        o64 = None
         try:
-            fp64 = time_plan("fp64")
+            fp64, o64 = time_plan("fp64")
         except fftb.FFTBError as e:
             fp64 = {"unavailable": str(e)}
         try:
-            mixed_tc = time_plan("mixed", reps=5)
+            mixed_tc, o_tc = time_plan("mixed", reps=5, ref=o64)
+            del o_tc
         except fftb.FFTBError as e:
             mixed_tc = {"unavailable": str(e)}
+        err_vs_fp64 = None if o64 is None else rel_l2(out, o64)
+        if err is None:
+            err = err_vs_fp64
+        del o64
+        fastest = max([("fp32", value)] + ([("mixed_tc", mixed_tc["value"])] if "value" in mixed_tc else []),
+                      key=lambda t: t[1])
+        mixed_vs_fp64 = {"mixed": fastest[0], "mixed_bands_per_s": fastest[1],
+                         "fp64_bands_per_s": fp64.get("value"),
+                         "ratio": None if "value" not in fp64 else fastest[1] / fp64["value"],
+                         "mixed_rel_l2_vs_fp64_gpu": err_vs_fp64 if fastest[0] == "fp32"
+                         else mixed_tc.get("rel_l2_vs_fp64_gpu"),
+                         "what": "the fastest path whose bulk butterflies run in FP32 (FP32 on CUDA cores, or "
+                                 "MIXED_TC with split-FP16 tensor-core DFT stages) against the plain FP64 GPU "
+                                 "path, same workload"}
 
         # context: the same transform without pruning, as the padded full-cube
         # 3D FFT a plane-wave code would otherwise run (scatter into the cube,
@@ -653,6 +732,15 @@ def run_ours(args):
             except Exception as e:  # context only: never fail the bench
                 cpu["all_cores"] = {"unavailable": f"{type(e).__name__}: {e}"}
 
+        # the 64^3 workload (64 bands, cube kept in HBM) timed the same way,
+        # as a figure beside the headline
+        extra = {}
+        if w.name != "sphere64_rt" and not args.no_extra:
+            try:
+                extra["sphere64_rt"] = time_workload(fftb, "sphere64_rt", dev, flush, stream, args)
+            except Exception as e:  # context only: never fail the bench
+                extra["sphere64_rt"] = {"unavailable": f"{type(e).__name__}: {e}"}
+
         line = {"metric": METRIC, "value": value, "unit": "bands/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_median_of_50": median50,
                 "higher_is_better": True, "scaling": "weak",
@@ -663,6 +751,8 @@ def run_ours(args):
                            "graph": w.graph, "graph_launches_in_timed_steps": graph_steps, "autotuned": w.tune,
                            "l2": "flushed between timed steps (256 MiB write)"},
                 "rel_l2": err,
+                "rel_l2_vs_fp64_gpu": err_vs_fp64,
+                "mixed_vs_fp64": mixed_vs_fp64,
                 "fp64_gpu": fp64,
                 "mixed_tc_gpu": mixed_tc,
                 "full_cube_cufft_gpu": full_cube,
@@ -672,7 +762,8 @@ def run_ours(args):
                 "e2e": {"value": w.total_bands / e2e_s, "unit": "bands/s", "h2d_bytes_per_step": nbytes,
                         "d2h_bytes_per_step": nbytes},
                 "gpu_launches": launches,
-                "clocks": clocks}
+                "clocks": clocks,
+                "other_workloads": extra}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -685,9 +776,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sphere64_rt",
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=["sphere64_rt", "sphere96_multik", "sphere128_apply", "sphere160_large", "sphere256_e2",
                              "sphere64_rt_batchfast"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the 64^3 figure beside the headline")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -34,12 +34,24 @@ def test_stage_bytes_64_round_trip():
     cube = 64 * 64 ** 3
     stk = 64 * sticks * 64
     sph = 64 * ngw
-    assert bench.stage_bytes("plane_r2g", w, info, [ngw], [sticks]) == 8 * (cube + stk)
-    assert bench.stage_bytes("plane_g2r", w, info, [ngw], [sticks]) == 8 * (stk + cube)
-    assert bench.stage_bytes("stick_g2r", w, info, [ngw], [sticks]) == 8 * (sph + stk)
-    assert bench.stage_bytes("stick_r2g", w, info, [ngw], [sticks]) == 8 * (stk + sph)
-    # 160.4 MB per r -> G launch: the cube (134.2 MB) and the stick rows (26.1 MB)
-    assert abs(bench.stage_bytes("plane_r2g", w, info, [ngw], [sticks]) / 1e6 - 160.4) < 0.5
+    # compulsory: the cube for the plane stages, the sphere for the z stages;
+    # the stick rows between them are this design's intermediate
+    assert bench.stage_bytes("plane_r2g", w, info, [ngw], [sticks]) == (8 * cube, 8 * stk)
+    assert bench.stage_bytes("plane_g2r", w, info, [ngw], [sticks]) == (8 * cube, 8 * stk)
+    assert bench.stage_bytes("stick_g2r", w, info, [ngw], [sticks]) == (8 * sph, 8 * stk)
+    assert bench.stage_bytes("stick_r2g", w, info, [ngw], [sticks]) == (8 * sph, 8 * stk)
+    # 134.2 MB of cube per r -> G launch, 26.1 MB of stick rows beside it
+    comp, inter = bench.stage_bytes("plane_r2g", w, info, [ngw], [sticks])
+    assert abs(comp / 1e6 - 134.2) < 0.05 and abs(inter / 1e6 - 26.1) < 0.05
+
+
+def test_default_workload_is_the_largest_single_gpu_configuration():
+    """160^3, |G| <= 40 (267 761 G), 512 bands, round trip streamed in band chunks."""
+    w = bench.Workload(bench.DEFAULT_WORKLOAD)
+    assert (w.n, w.radius, w.bands, w.direction) == ((160, 160, 160), 40.0, [512], "roundtrip")
+    assert len(sphere_gvectors(w.n, w.radius)) == 267761
+    # compulsory bytes of the round trip per band: 2 (ngw + N^3) complex64 = 69.8 MB
+    assert abs(2 * (267761 + 160 ** 3) * 8 / 1e6 - 69.8) < 0.05
 
 
 def test_apply_flops_and_fp32_peak():

@@ -290,3 +290,58 @@ def test_g2r_r2g_match_bruteforce_on_random_shapes():
         assert relerr(r2g(g, R, n), brute_r2g(g, R, n)) < 1e-13
 
     check()
+
+
+# ------------------------------------------- pins at the workload lengths
+
+def _direct_g2r_at(gvec, c, n, pts):
+    """Direct sum at chosen points, written independently of the oracle: the
+    phase of G.r is reduced to an integer numerator mod N per axis before the
+    division, so large G x products keep full FP64 accuracy."""
+    g = np.asarray(gvec, dtype=np.int64)
+    out = np.empty(len(pts), dtype=np.complex128)
+    for i, (x, y, z) in enumerate(np.asarray(pts).tolist()):
+        th = ((g[:, 0] * x) % n[0]) / n[0] + ((g[:, 1] * y) % n[1]) / n[1] + ((g[:, 2] * z) % n[2]) / n[2]
+        out[i] = np.sum(c * np.exp(2j * np.pi * th))
+    return out
+
+
+def _direct_r2g_at(gsel, cube, n):
+    """c(G) = sum over the whole cube of R exp(-2 pi j G.r/N), one G at a
+    time, with the same integer phase reduction."""
+    n0, n1, n2 = n
+    z, y, x = np.meshgrid(np.arange(n2), np.arange(n1), np.arange(n0), indexing="ij")
+    out = []
+    for gx, gy, gz in np.asarray(gsel).tolist():
+        th = ((gx * x) % n0) / n0 + ((gy * y) % n1) / n1 + ((gz * z) % n2) / n2
+        out.append(np.sum(cube * np.exp(-2j * np.pi * th)))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("n,r,k", [((24, 24, 24), 6.0, (0.0, 0.0, 0.0)),
+                                   ((64, 64, 64), 16.0, (0.0, 0.0, 0.0)),
+                                   ((96, 96, 96), 24.0, (0.31, -0.44, 0.12)),
+                                   ((128, 128, 128), 32.0, (0.0, 0.0, 0.0)),
+                                   ((160, 160, 160), 40.0, (0.0, 0.0, 0.0))])
+def test_library_fft_at_workload_lengths(n, r, k):
+    """The oracle's FFT step (pocketfft through numpy) at the lengths the GPU
+    path is measured on, whose factors 3 and 5 the tiny-grid pins do not all
+    reach: sampled outputs of g2r / r2g against direct sums, and the oracle's
+    own point-sum functions against the same direct sums."""
+    g = sphere_gvectors(n, r, k)
+    rng = np.random.default_rng(int(n[0]))
+    c = rng.standard_normal(len(g)) + 1j * rng.standard_normal(len(g))
+    pts = np.stack([rng.integers(0, n[d], 6) for d in range(3)], axis=1)
+    pts[0] = (0, 0, 0)
+    pts[1] = (n[0] - 1, n[1] // 2, 1)
+    want = _direct_g2r_at(g, c, n, pts)
+    R = g2r(g, c, n)
+    assert relerr(R[pts[:, 2], pts[:, 1], pts[:, 0]], want) < 1e-12
+    assert relerr(g2r_points(g, c, n, pts), want) < 1e-12
+    cube = rng.standard_normal((n[2], n[1], n[0])) + 1j * rng.standard_normal((n[2], n[1], n[0]))
+    sel = np.concatenate([g[:1], g[-1:], g[rng.choice(len(g), 2, replace=False)]])
+    want = _direct_r2g_at(sel, cube, n)
+    full = r2g(g, cube, n)
+    index = {tuple(v): i for i, v in enumerate(g.tolist())}
+    assert relerr(full[[index[tuple(v)] for v in sel.tolist()]], want) < 1e-12
+    assert relerr(r2g_points(sel, cube, n), want) < 1e-12
