@@ -1,5 +1,5 @@
-// fft_core.cuh -- register codelets and shared-memory Stockham passes for the
-// batched 1D DFTs of the staged sphere <-> cube transform.
+// fft_core.cuh -- complex arithmetic, register codelets and the exchange-row
+// layout of the batched 1D DFTs of the staged sphere <-> cube transform.
 //
 // A 1D DFT of length N (Sec. 2.1: y = DFT_n x, omega_n = e^{-j 2 pi/n}; the
 // G -> r direction uses the conjugate root, Sec. 2.2) is factored
@@ -10,10 +10,6 @@
 // outputs spaced L apart at (i - k) R + k. After the last pass the data are
 // in natural order.
 //
-// Many independent lines run together. Every thread of the CTA takes
-// (line, butterfly) work items; a pass first loads all of its items into
-// registers, synchronises, then computes and stores, so a pass may work in
-// place on a shared-memory buffer.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -205,6 +201,103 @@ template <int S, typename C> __device__ __forceinline__ void dft12(C* v) {
   }
 }
 
+// ------------------------------------------------- compile-time twiddles
+// cos and sin of 2 pi m / L for integers m and L, evaluated by the compiler
+// in double precision: the angle is reduced exactly (integer arithmetic in
+// units of a turn / (8 L)) to an octant, folded to [0, pi/4] by the
+// symmetries of the circle, and the Taylor series of cos and sin about 0 is
+// summed to 30 terms (the terms at pi/4 fall below 1e-17 after 11).
+namespace ctw {
+constexpr double kPi = 3.141592653589793238462643383279502884;
+__host__ __device__ constexpr double taylor_cos(double x) {
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 30; ++k) {
+    term *= -x * x / double((2 * k - 1) * (2 * k));
+    sum += term;
+  }
+  return sum;
+}
+__host__ __device__ constexpr double taylor_sin(double x) {
+  double term = x, sum = x;
+  for (int k = 1; k < 30; ++k) {
+    term *= -x * x / double((2 * k) * (2 * k + 1));
+    sum += term;
+  }
+  return sum;
+}
+// (cos, sin)(2 pi m / L) as c (sel = 0) or s (sel = 1)
+__host__ __device__ constexpr double cs(int m, int L, int sel) {
+  const long q = ((long)m % L + L) % L;     // turn fraction q / L in [0, 1)
+  const long t = 8 * q;                     // in units of a turn / (8 L)
+  const int oct = (int)(t / L);             // octant 0..7
+  const long r = t - (long)oct * L;         // angle inside the octant: (pi/4) r / L
+  double c = 0, s = 0;
+  if (oct % 2 == 0) {                       // alpha = (pi/4) r / L in [0, pi/4)
+    const double a = (kPi / 4) * (double(r) / double(L));
+    c = taylor_cos(a);
+    s = taylor_sin(a);
+  } else {                                  // alpha = pi/4 + (pi/4) r / L: use pi/2 - alpha in (0, pi/4]
+    const double b = (kPi / 4) * (double(L - r) / double(L));
+    c = taylor_sin(b);
+    s = taylor_cos(b);
+  }
+  const int quad = oct / 2;                 // rotate by quad quarter turns
+  const double cc = quad == 0 ? c : quad == 1 ? -s : quad == 2 ? -c : s;
+  const double ss = quad == 0 ? s : quad == 1 ? c : quad == 2 ? -s : -c;
+  return sel == 0 ? cc : ss;
+}
+}  // namespace ctw
+
+// v * e^{S 2 pi j m / L} with the constant evaluated by the compiler; quarter
+// turns become sign changes and swaps.
+template <int M, int L, int S, typename C> __device__ __forceinline__ C wconst(C a) {
+  using T = decltype(C::x);
+  constexpr int q = ((M % L) + L) % L;
+  if constexpr (q == 0) return a;
+  else if constexpr (4 * q == L) return mulj<S>(a);
+  else if constexpr (2 * q == L) return mk(-a.x, -a.y);
+  else if constexpr (4 * q == 3 * L) return mulj<-S>(a);
+  else {
+    constexpr T c = T(ctw::cs(q, L, 0));
+    constexpr T sn = T(S) * T(ctw::cs(q, L, 1));
+    return mk(a.x * c - a.y * sn, a.x * sn + a.y * c);
+  }
+}
+
+template <int R, int S, typename C> __device__ __forceinline__ void dft(C* v);
+
+// y[n2][k1] *= W^(n2 k1) for every element, index I = n2 A + k1
+template <int A, int B, int S, int I, typename C> __device__ __forceinline__ void ct_twiddle(C (&y)[B][A]) {
+  if constexpr (I < A * B) {
+    y[I / A][I % A] = wconst<(I / A) * (I % A), A * B, S>(y[I / A][I % A]);
+    ct_twiddle<A, B, S, I + 1>(y);
+  }
+}
+
+// Composite radix A * B in registers (Cooley-Tukey, Sec. 2.1): input index
+// n = B n1 + n2, output index k = k1 + A k2; a DFT-A over n1 for each n2,
+// the twiddles W^(n2 k1) (W = e^{S 2 pi j / (A B)}, compile-time constants),
+// then a DFT-B over n2 for each k1.
+template <int A, int B, int S, typename C> __device__ __forceinline__ void dft_ct(C* v) {
+  C y[B][A];
+#pragma unroll
+  for (int n2 = 0; n2 < B; ++n2) {
+#pragma unroll
+    for (int n1 = 0; n1 < A; ++n1) y[n2][n1] = v[B * n1 + n2];
+    dft<A, S>(y[n2]);
+  }
+  ct_twiddle<A, B, S, 0>(y);
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) {
+    C t[B];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) t[n2] = y[n2][k1];
+    dft<B, S>(t);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = t[k2];
+  }
+}
+
 template <int R, int S, typename C> __device__ __forceinline__ void dft(C* v) {
   if constexpr (R == 2) dft2<S>(v[0], v[1]);
   else if constexpr (R == 3) dft3<S>(v[0], v[1], v[2]);
@@ -215,194 +308,27 @@ template <int R, int S, typename C> __device__ __forceinline__ void dft(C* v) {
   else if constexpr (R == 10) dft10<S>(v);
   else if constexpr (R == 12) dft12<S>(v);
   else if constexpr (R == 16) dft16<S>(v);
+  else if constexpr (R == 20) dft_ct<4, 5, S>(v);
+  else if constexpr (R == 24) dft_ct<8, 3, S>(v);
+  else if constexpr (R == 32) dft_ct<8, 4, S>(v);
+  else if constexpr (R == 40) dft_ct<8, 5, S>(v);
   else static_assert(R == 2, "unsupported radix");
 }
 
-// ------------------------------------------------------------ radix plan
-// Radices taken in this order: 8 while 8 | N, then 4, 2, 3, 5.
-template <int N> struct first_radix {
-  static constexpr int value = (N % 8 == 0) ? 8 : (N % 4 == 0) ? 4 : (N % 2 == 0) ? 2
-                               : (N % 3 == 0) ? 3 : (N % 5 == 0) ? 5 : 0;
-};
-template <int N> struct min_radix {
-  static constexpr int R = first_radix<N>::value;
-  static constexpr int rest = (R == 0 || R == N) ? 0 : min_radix<N / R>::value;
-  static constexpr int value = (rest == 0 || R < rest) ? R : rest;
-};
-template <> struct min_radix<1> { static constexpr int value = 0; };
-
-// ------------------------------------------------------------ fast division
-// q = n / d for n, d < 2^16 via one multiply-high (m = ceil(2^32 / d)).
-struct FastDiv {
-  uint32_t d, m;
-  __device__ __forceinline__ FastDiv(uint32_t dd) : d(dd), m(dd ? (uint32_t)((0x100000000ull + dd - 1) / dd) : 0u) {}
-  __device__ __forceinline__ uint32_t div(uint32_t n) const { return d == 1 ? n : __umulhi(n, m); }
-};
-
-// --------------------------------------------------------------- one pass
-// MAP_ELEM: consecutive threads take consecutive butterflies of one line
-// (coalesced along the transformed dimension); otherwise consecutive
-// threads take consecutive lines.
-template <int N, int R, int P, int S, int NT, int MAXIT, bool MAP_ELEM, typename C,
-          typename Src, typename Dst>
-__device__ __forceinline__ void stockham_pass(int nl, const C* __restrict__ tw, Src&& src, Dst&& dst) {
-  constexpr int NB = N / R;
-  const int total = nl * NB;
-  const FastDiv fd(nl > 0 ? nl : 1);
-  C v[MAXIT][R];
-#pragma unroll
-  for (int it = 0; it < MAXIT; ++it) {
-    const int w = threadIdx.x + it * NT;
-    if (w < total) {
-      int line, i;
-      if constexpr (MAP_ELEM) { line = w / NB; i = w - line * NB; }
-      else { i = (int)fd.div((uint32_t)w); line = w - i * nl; }
-#pragma unroll
-      for (int j = 0; j < R; ++j) v[it][j] = src(line, i + j * NB);
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int it = 0; it < MAXIT; ++it) {
-    const int w = threadIdx.x + it * NT;
-    if (w < total) {
-      int line, i;
-      if constexpr (MAP_ELEM) { line = w / NB; i = w - line * NB; }
-      else { i = (int)fd.div((uint32_t)w); line = w - i * nl; }
-      const int k = i % P;
-      if constexpr (P > 1) {
-        constexpr int STEP = N / (P * R);
-#pragma unroll
-        for (int j = 1; j < R; ++j) {
-          const C w_ = tw[j * k * STEP];
-          v[it][j] = (S > 0) ? cmul(v[it][j], w_) : cmulc(v[it][j], w_);
-        }
-      }
-      dft<R, S>(v[it]);
-      const int base = (i - k) * R + k;
-#pragma unroll
-      for (int j = 0; j < R; ++j) dst(line, base + j * P, v[it][j]);
-    }
-  }
-  __syncthreads();
-}
-
-// ---------------------------------------------------------- whole line FFT
-// Runs every pass of a length-N DFT on nl lines (nl * N <= NT * EPT).
-// first(line, e) reads the input, mid_ld / mid_st address the in-place
-// shared buffer used between passes, last(line, e, v) receives the output.
-template <int N, int REM, int P, int S, int NT, int EPT, bool MAP_ELEM, bool FIRST, typename C,
-          typename First, typename MidLd, typename MidSt, typename Last>
-__device__ __forceinline__ void fft_passes(int nl, const C* __restrict__ tw, First&& first,
-                                           MidLd&& mid_ld, MidSt&& mid_st, Last&& last) {
-  constexpr int R = first_radix<REM>::value;
-  static_assert(R != 0, "length must be 2^a 3^b 5^c");
-  constexpr int MAXIT = (EPT * NT / N * (N / R) + NT - 1) / NT;  // ceil(lines_max * N/R / NT)
-  constexpr bool LAST = (REM == R);
-  if constexpr (FIRST && LAST) {
-    stockham_pass<N, R, P, S, NT, MAXIT, MAP_ELEM, C>(nl, tw, first, last);
-  } else if constexpr (FIRST) {
-    stockham_pass<N, R, P, S, NT, MAXIT, MAP_ELEM, C>(nl, tw, first, mid_st);
-  } else if constexpr (LAST) {
-    stockham_pass<N, R, P, S, NT, MAXIT, MAP_ELEM, C>(nl, tw, mid_ld, last);
-  } else {
-    stockham_pass<N, R, P, S, NT, MAXIT, MAP_ELEM, C>(nl, tw, mid_ld, mid_st);
-  }
-  if constexpr (!LAST)
-    fft_passes<N, REM / R, P * R, S, NT, EPT, MAP_ELEM, false, C>(nl, tw, first, mid_ld, mid_st, last);
-}
-
-template <int N, int S, int NT, int EPT, bool MAP_ELEM, typename C, typename First, typename MidLd,
-          typename MidSt, typename Last>
-__device__ __forceinline__ void fft_lines(int nl, const C* __restrict__ tw, First&& first, MidLd&& mid_ld,
-                                          MidSt&& mid_st, Last&& last) {
-  fft_passes<N, N, 1, S, NT, EPT, MAP_ELEM, true, C>(nl, tw, first, mid_ld, mid_st, last);
-}
-
-// Lines of length N one pass-set can hold with NT threads and EPT elements each.
-template <int N, int NT, int EPT> struct lines_per_chunk {
-  static constexpr int value = (NT * EPT) / N;
-};
-
-__host__ __device__ constexpr int odd_pitch(int n) { return (n & 1) ? n : n + 1; }
-
-// ------------------------------------------------------- warp-level passes
-// A warp owns a few whole lines and runs all passes of their DFTs alone,
-// synchronising with __syncwarp only. Between passes the lines sit in the
-// warp's private shared-memory scratch, row-major with one pad element after
-// every 8 (wpad): stride-R butterfly stores then fall on distinct banks.
-// The row pitch is = 8 (mod 16) complex elements, so the two lines a
-// half-warp touches use opposite bank halves.
-__host__ __device__ constexpr int wpitch(int n) {
-  return (n + n / 8) + ((8 - (n + n / 8) % 16) + 16) % 16;
+// ------------------------------------------------------- exchange rows
+// Between passes the lines of a warp sit in the warp's private shared-memory
+// scratch, row-major with one pad element after every 8 (wpad): stride-R
+// butterfly stores then fall on distinct banks. The G lanes of one line touch
+// a window of about G consecutive elements (2 G words) at a time, so the row
+// pitch is chosen = G (mod 2 G) complex elements for G = 2, 4, 8: the windows
+// of the 32 / G lines of a warp then start 2 G words apart modulo an odd
+// multiple, and together tile the 32 banks.
+__host__ __device__ constexpr int wpitch(int n, int g = 8) {
+  const int base = n + n / 8;
+  const int m = (g >= 2 && g <= 8) ? 2 * g : 16;
+  const int r = (g >= 2 && g <= 8) ? g : 8;
+  return base + ((r - base % m) % m + m) % m;
 }
 __device__ __forceinline__ int wpad(int e) { return e + (e >> 3); }
-
-template <int N, int R, int P, int S, int MAXIT, typename C, typename Src, typename Dst>
-__device__ __forceinline__ void wpass(int nl, const C* __restrict__ tw, Src&& src, Dst&& dst) {
-  constexpr int NB = N / R;
-  const int lane = threadIdx.x & 31;
-  const int total = nl * NB;
-  C v[MAXIT][R];
-#pragma unroll
-  for (int it = 0; it < MAXIT; ++it) {
-    const int w = lane + 32 * it;
-    if (w < total) {
-      const int line = w / NB, i = w - line * NB;
-#pragma unroll
-      for (int j = 0; j < R; ++j) v[it][j] = src(line, i + j * NB);
-    }
-  }
-  __syncwarp();
-#pragma unroll
-  for (int it = 0; it < MAXIT; ++it) {
-    const int w = lane + 32 * it;
-    if (w < total) {
-      const int line = w / NB, i = w - line * NB;
-      const int k = i % P;
-      if constexpr (P > 1) {
-        constexpr int STEP = N / (P * R);
-#pragma unroll
-        for (int j = 1; j < R; ++j) {
-          const C w_ = tw[j * k * STEP];
-          v[it][j] = (S > 0) ? cmul(v[it][j], w_) : cmulc(v[it][j], w_);
-        }
-      }
-      dft<R, S>(v[it]);
-      const int base = (i - k) * R + k;
-#pragma unroll
-      for (int j = 0; j < R; ++j) dst(line, base + j * P, v[it][j]);
-    }
-  }
-  __syncwarp();
-}
-
-// All passes of a length-N DFT on nl <= LMAX lines owned by one warp.
-template <int N, int REM, int P, int S, int LMAX, bool FIRST, typename C, typename First,
-          typename MidLd, typename MidSt, typename Last>
-__device__ __forceinline__ void wfft_passes(int nl, const C* __restrict__ tw, First&& first,
-                                            MidLd&& mid_ld, MidSt&& mid_st, Last&& last) {
-  constexpr int R = first_radix<REM>::value;
-  static_assert(R != 0, "length must be 2^a 3^b 5^c");
-  constexpr int MAXIT = (LMAX * (N / R) + 31) / 32;
-  constexpr bool LAST = (REM == R);
-  if constexpr (FIRST && LAST) {
-    wpass<N, R, P, S, MAXIT, C>(nl, tw, first, last);
-  } else if constexpr (FIRST) {
-    wpass<N, R, P, S, MAXIT, C>(nl, tw, first, mid_st);
-  } else if constexpr (LAST) {
-    wpass<N, R, P, S, MAXIT, C>(nl, tw, mid_ld, last);
-  } else {
-    wpass<N, R, P, S, MAXIT, C>(nl, tw, mid_ld, mid_st);
-  }
-  if constexpr (!LAST)
-    wfft_passes<N, REM / R, P * R, S, LMAX, false, C>(nl, tw, first, mid_ld, mid_st, last);
-}
-
-template <int N, int S, int LMAX, typename C, typename First, typename MidLd, typename MidSt, typename Last>
-__device__ __forceinline__ void wfft(int nl, const C* __restrict__ tw, First&& first, MidLd&& mid_ld,
-                                     MidSt&& mid_st, Last&& last) {
-  wfft_passes<N, N, 1, S, LMAX, true, C>(nl, tw, first, mid_ld, mid_st, last);
-}
 
 }  // namespace fftb

@@ -710,7 +710,10 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
       Lp.pf = pf_active(p, 1) && cube_in_16;
       if (p->bg) e = launch_plane_bg(M_R2G, Lp);
       else if (p->tc5 && cube_in_16) e = tc5_launch(M_R2G, Lp, p->tc5g[1], p->tc5_ctas);
-      else if (p->sched_plane & 2) e = launch_plane_alt(M_R2G, Lp);
+      else if (p->sched_plane & 2) {
+        Lp.pf = cube_in_16;  // the alternative kernel loads whole cube rows by bulk copies
+        e = launch_plane_alt(M_R2G, Lp);
+      }
       else e = Lp.pf ? launch_plane_pf(M_R2G, Lp) : launch_plane(pk, M_R2G, Lp);
       break;
     }

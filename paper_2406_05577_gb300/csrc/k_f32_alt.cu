@@ -1,6 +1,7 @@
 // k_f32_alt.cu -- float stick and plane kernels with the alternative radix
-// schedule (LPV<N, 1>) of the lengths that have one; the autotuner chooses
-// between them and the default schedule.
+// schedule of the lengths that have one (LPV<N, 1>; the plane stages of 160
+// take the two-pass schedule LPV<160, 2>); the autotuner chooses between them
+// and the default schedule.
 #include "kernels.cuh"
 
 namespace fftb {
@@ -8,19 +9,23 @@ namespace {
 
 #define FFTB_ALT_SIZES(X) X(64) X(96) X(128) X(160)
 
+// schedule variant of the alternative plane kernels
+template <int N> constexpr int plane_v() { return N == 160 ? 2 : 1; }
+
 template <int N, int MODE> const void* plane_fn() {
-  return (const void*)k_plane<float, N, N, MODE, false, false, false, 1>;
+  return (const void*)k_plane<float, N, N, MODE, false, false, false, plane_v<N>()>;
 }
 template <int N, int MODE> const void* stick_fn() { return (const void*)k_stick<float, N, MODE, false, 1>; }
 
 template <int N> cudaError_t go_plane_v(int mode, const Launch& L) {
-  const size_t smem = plane_smem_c<float, N, N, 1>(L.g.xmax, L.a_bufs);
+  constexpr int V = plane_v<N>();
+  const size_t smem = plane_smem_c<float, N, N, V>(L.g.xmax, L.a_bufs);
   const int nplanes = L.nb * L.g.n2;
   const dim3 grid(L.plane_ctas > 0 ? min(L.plane_ctas, nplanes) : nplanes);
   constexpr int NT = PlaneCfg<float>::NW * 32;
-  if (mode == M_G2R) return launch_k(k_plane<float, N, N, M_G2R, false, false, false, 1>, grid, NT, smem, L, L);
-  if (mode == M_R2G) return launch_k(k_plane<float, N, N, M_R2G, false, false, false, 1>, grid, NT, smem, L, L);
-  return launch_k(k_plane<float, N, N, M_APPLY, false, false, false, 1>, grid, NT, smem, L, L);
+  if (mode == M_G2R) return launch_k(k_plane<float, N, N, M_G2R, false, false, false, V>, grid, NT, smem, L, L);
+  if (mode == M_R2G) return launch_k(k_plane<float, N, N, M_R2G, false, false, false, V>, grid, NT, smem, L, L);
+  return launch_k(k_plane<float, N, N, M_APPLY, false, false, false, V>, grid, NT, smem, L, L);
 }
 template <int N> cudaError_t go_stick_v(int mode, const Launch& L, int ctas) {
   constexpr int WZ = 32 / Line<N, 1>::G;
@@ -32,7 +37,7 @@ template <int N> cudaError_t go_stick_v(int mode, const Launch& L, int ctas) {
   return launch_k(k_stick<float, N, M_R2G, false, 1>, grid, STICK_NW * 32, smem, L, L);
 }
 template <int N> cudaError_t prep_plane_v(int xmax, int a_bufs) {
-  const int s = (int)plane_smem_c<float, N, N, 1>(xmax, a_bufs);
+  const int s = (int)plane_smem_c<float, N, N, plane_v<N>()>(xmax, a_bufs);
   cudaError_t e = raise_smem_limit(plane_fn<N, M_G2R>(), s);
   if (e == cudaSuccess) e = raise_smem_limit(plane_fn<N, M_R2G>(), s);
   if (e == cudaSuccess) e = raise_smem_limit(plane_fn<N, M_APPLY>(), s);
@@ -45,7 +50,7 @@ template <int N> cudaError_t prep_stick_v() {
   return e;
 }
 template <int N> int occ_plane_v(int mode, int xmax, int a_bufs) {
-  const size_t s = plane_smem_c<float, N, N, 1>(xmax, a_bufs);
+  const size_t s = plane_smem_c<float, N, N, plane_v<N>()>(xmax, a_bufs);
   const void* fn = mode == M_G2R ? plane_fn<N, M_G2R>() : mode == M_R2G ? plane_fn<N, M_R2G>() : plane_fn<N, M_APPLY>();
   int nb = 0;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, PlaneCfg<float>::NW * 32, s) == cudaSuccess ? nb : 0;
@@ -71,7 +76,7 @@ bool alt_schedule(int n) {
 
 size_t plane_alt_smem(int n, int xmax, int a_bufs) {
   switch (n) {
-#define C_(N) case N: return plane_smem_c<float, N, N, 1>(xmax, a_bufs);
+#define C_(N) case N: return plane_smem_c<float, N, N, plane_v<N>()>(xmax, a_bufs);
     FFTB_ALT_SIZES(C_)
 #undef C_
   }

@@ -53,6 +53,12 @@ FFTB_LPV(96, 24, 12, 8, 0, 0);
 FFTB_LPV(128, 16, 8, 16, 0, 0);
 FFTB_LPV(160, 20, 10, 4, 4, 0);
 #undef FFTB_LPV
+// Two-pass schedules for the plane stages: a composite DFT of the whole E in
+// registers, one exchange, then radix-G butterflies on G = N / E lanes.
+template <> struct LPV<160, 2> {
+  static constexpr int E = 40;
+  static constexpr int R[4] = {40, 4, 0, 0};
+};
 
 // ----------------------------------------------------------- tensor cores
 // A radix-8 pass as a dense product on the tensor cores (split precision):
@@ -94,7 +100,7 @@ template <int N, int V = 0> struct Line {
   static constexpr int NP = LPN::R[1] == 0 ? 1 : LPN::R[2] == 0 ? 2 : LPN::R[3] == 0 ? 3 : 4;
   static constexpr int R0 = LPN::R[0];
   static constexpr int RL = LPN::R[NP - 1];
-  static constexpr int PITCH = wpitch(N);
+  static constexpr int PITCH = wpitch(N, G);
   static_assert(32 % G == 0, "lanes per line must divide the warp");
   static_assert(R0 * (NP > 1 ? LPN::R[1] : 1) * (NP > 2 ? LPN::R[2] : 1) * (NP > 3 ? LPN::R[3] : 1) == N,
                 "radix schedule must multiply to N");
@@ -352,6 +358,20 @@ template <int N, int V = 0> struct Line {
   __device__ __forceinline__ static void run(C (&v)[E], int g, C* __restrict__ row, const C* __restrict__ tw,
                                              const TwCache<C>& tc) {
     passes<0, S>(v, g, row, tw, tc);
+  }
+
+  // As run() for a two-pass schedule, with two hooks around its one exchange:
+  // before() runs (on every lane) before the exchange rows are written,
+  // after() once every lane has read them back (the rows are free again).
+  template <int S, typename C, typename B, typename A>
+  __device__ __forceinline__ static void run2(C (&v)[E], int g, C* __restrict__ row, const C* __restrict__ tw,
+                                              const TwCache<C>& tc, B&& before, A&& after) {
+    static_assert(NP == 2 && G > 1, "one exchange between two passes");
+    compute<0, S>(v, g, tw, tc);
+    before();
+    exchange<0>(v, g, row);
+    after();
+    compute<1, S>(v, g, tw, tc);
   }
 };
 

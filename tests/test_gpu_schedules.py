@@ -1,6 +1,7 @@
-"""Alternative radix schedules (64 = 16x4, 96 = 12x8, 128 = 8x16, 160 =
-10x4x4; radix-10 and radix-12 codelets) against the FP64 oracle, and the
-autotuner's choice among them."""
+"""Alternative radix schedules (64 = 16x4, 96 = 12x8, 128 = 8x16; the plane
+stages of 160 = 40x4 with a composite 40-point DFT in registers and cube rows
+fetched by bulk copies, its z lines 10x4x4; radix-10 and radix-12 codelets)
+against the FP64 oracle, and the autotuner's choice among them."""
 import numpy as np
 import pytest
 
@@ -100,3 +101,48 @@ def test_schedule_errors_and_autotune(F, tmp_path, monkeypatch):
     assert 0 <= int(line[-4]) <= 3 and line[-3] in ("0", "1") and line[-2] in ("0", "1") and line[-1] == "0"
     assert int(line[-4]) == plan.info["radix_schedule_plane"] and int(line[-3]) == plan.info["radix_schedule_stick"]
     assert int(line[-2]) == plan.info["dependent_launch"]
+
+
+def test_160_two_pass_rows_by_bulk_copies(F):
+    """The 160 = 40 x 4 plane schedule fetches each warp's next cube rows by
+    bulk copies on a per-warp barrier: r -> G of random cubes against direct
+    sums, from a 16-byte aligned cube (copies) and from a cube 8 bytes off
+    (lane loads); then one copy withheld: the bounded wait runs out, the
+    status is reported, and the next execute is correct."""
+    import torch
+    n, r, bands = (160, 160, 160), 40.0, 3
+    vol = 160 ** 3
+    plan = F.Plan(n, "r2g", "fp32", radius=r, bands=[bands])
+    plan.set_radix_schedule(1, 0)
+    g = plan.sphere(0)
+    R = fi.complex_gaussian((bands, 160, 160, 160), 96).astype(np.complex64)
+    sel = np.random.default_rng(97).choice(len(g), 5, replace=False)
+    want = oracle.r2g_points(g[sel], R.astype(np.complex128), n)
+    buf = torch.empty(bands * vol + 1, dtype=torch.complex64, device="cuda")
+    out = torch.empty(plan.info["sphere_elems"], dtype=torch.complex64, device="cuda")
+    for off in (0, 1):  # 16-byte aligned, then 8 bytes off
+        x = buf[off:off + bands * vol]
+        x.copy_(torch.from_numpy(R.reshape(-1)))
+        assert (x.data_ptr() % 16 == 0) == (off == 0)
+        out.zero_()
+        plan.execute(x, out)
+        torch.cuda.synchronize()
+        plan.check()
+        got = out.cpu().numpy().reshape(bands, -1)[:, sel]
+        assert relerr(got, want) <= 2e-6, off
+        if off == 0:
+            ref = out.clone()
+    x = buf[:bands * vol]
+    x.copy_(torch.from_numpy(R.reshape(-1)))
+    plan.inject(F.FFTB_INJECT_SKIP_FIRST_PREFETCH)
+    plan.execute(x, out)
+    torch.cuda.synchronize()
+    with pytest.raises(F.FFTBError) as ei:
+        plan.check()
+    assert ei.value.status == F.FFTB_ERR_DEVICE_TIMEOUT
+    plan.inject(0)
+    out.zero_()
+    plan.execute(x, out)
+    torch.cuda.synchronize()
+    plan.check()
+    assert torch.equal(out, ref)
