@@ -61,7 +61,10 @@ typedef enum {
   FFTB_ERR_UNSUPPORTED = 2,    /* valid request this build has no kernel for       */
   FFTB_ERR_ALLOC = 3,          /* device or host allocation failed                 */
   FFTB_ERR_CUDA = 4,           /* a CUDA runtime call failed                       */
-  FFTB_ERR_DEVICE_TIMEOUT = 5  /* a device-side bounded wait gave up               */
+  FFTB_ERR_DEVICE_TIMEOUT = 5, /* a device-side bounded wait gave up               */
+  FFTB_ERR_DEVICE_BOUNDS = 6   /* a checked build (FFTB_CHECK, libfftb_check.so)
+                                  found a kernel index outside its buffer; the
+                                  access was skipped                              */
 } fftb_status;
 
 typedef enum {
@@ -134,6 +137,12 @@ typedef struct {
 /* Builds the spheres, stick/slab tables and twiddles on the host, uploads
  * them to the current CUDA device and allocates the plan's scratch. The only
  * call that allocates device memory or synchronises the device.
+ * Paper: the sphere is the cutoff rule of Sec. 2.2 (1/2 |g|^2 <= E_cut, here
+ * |G + k| <= r in grid units) or an explicit list / offset array (Sec. 3.3,
+ * Fig. 6); the plan fixes the 1D DFT factorisations (Sec. 2.1) and the staged
+ * padding order of Fig. 3 (z, then y, then x): the create construct of the
+ * paper's API (Sec. 3.1), a transform object built once from its description
+ * and then executed (Sec. 3.2).
  * Errors: INVALID_ARG for a bad description (grid extent outside the
  * supported list, sphere that does not fit the grid and would alias, G
  * outside [-N/2, N/2), duplicate G, negative bands, layout other than 0 or
@@ -159,6 +168,12 @@ fftb_status fftb_set_potential(fftb_plan plan, const void* v_dev);
 
 /* Enqueues the transform on `stream` (a cudaStream_t; NULL = legacy default
  * stream). Asynchronous: no synchronisation and no allocation.
+ * Paper: G_TO_R is psi(r) = sum_g c(g) e^{+j g r} over the sphere (Sec. 2.2),
+ * computed by padding one dimension at a time and transforming it (Fig. 3);
+ * R_TO_G is the forward DFT with omega_n = e^{-j 2 pi / n} (Sec. 2.1) sampled
+ * on the sphere; APPLY_LOCAL fuses padding, both transforms and the
+ * pointwise product (Sec. 2.3). No scaling in either direction. The execute
+ * construct of the paper's API (Sec. 3.1).
  *   G_TO_R      : in_dev = sphere batch, out_dev = cube batch, cube_dev NULL
  *   R_TO_G      : in_dev = cube batch,   out_dev = sphere batch, cube_dev NULL
  *   ROUNDTRIP   : in_dev = sphere batch, out_dev = sphere batch,
@@ -287,21 +302,28 @@ fftb_status fftb_plan_set_band_groups(fftb_plan plan, int32_t enable);
  * usable but the result is invalid. fftb_plan_check synchronises the device,
  * returns FFTB_ERR_DEVICE_TIMEOUT if the word is set since the previous check
  * (and clears it), else FFTB_OK. fftb_execute_host checks it after its own
- * synchronisation. */
+ * synchronisation. In the checked build (libfftb_check.so, compiled with
+ * FFTB_CHECK: every global and slab-plane index of the stick and plane kernels
+ * is tested against its buffer before the access) an index outside its buffer
+ * is skipped and reported the same way, as FFTB_ERR_DEVICE_BOUNDS. */
 fftb_status fftb_plan_check(fftb_plan plan);
 
 /* Test hook for the bounded waits: with FFTB_INJECT_SKIP_FIRST_PREFETCH the
  * first prefetch of CTA 0 (warp 0 in r->G) is not issued in each prefetching
- * plane launch, so its wait runs out (about one second, twice: the wait, then
- * the exit's wait for copies in flight) and the status word is set. 0 turns
- * injection off. Unknown bits: FFTB_ERR_INVALID_ARG. */
+ * plane launch (also in the r->G launches of the 160-point two-pass schedule,
+ * whose cube rows arrive by bulk copies), so its wait runs out (about one
+ * second, twice: the wait, then the exit's wait for copies in flight) and the
+ * status word is set. 0 turns injection off. Unknown bits:
+ * FFTB_ERR_INVALID_ARG. */
 #define FFTB_INJECT_SKIP_FIRST_PREFETCH 1
 fftb_status fftb_plan_inject(fftb_plan plan, int32_t flags);
 
 /* Kernel launches this plan has issued so far (all executes). */
 int64_t fftb_plan_launches(fftb_plan plan);
 
-/* Releases the plan's device memory and tables. NULL is accepted. */
+/* Releases the plan's device memory and tables (the clean-up construct of
+ * the paper's API, Sec. 3.1). NULL is accepted. Only call it when no execute
+ * of the plan is in flight. */
 fftb_status fftb_destroy(fftb_plan plan);
 
 /* Static description of a status code. */
@@ -321,22 +343,37 @@ const char* fftb_last_error(void);
  * kernels): in_dev = [bands][ngw] complex64 sphere coefficients in canonical
  * order (fftb_sphere_enumerate gives the G list), out_dev = [bands][N2][N1][N0]
  * complex64 cube. Both are caller-owned device buffers, 8-byte aligned.
- * Enqueued on `stream`; no synchronisation.
+ * Enqueued on `stream`. The geometry tables are built on the host and
+ * uploaded with a copy from pageable host memory on `stream`: the call may
+ * block the host until those bytes are staged (about 50 bytes per band plus
+ * the sphere's records); the transform itself runs asynchronously.
  *
  * Scratch: the stick buffer and the geometry tables live in two file-scope
  * device arrays of FFTB_NOALLOC_SCRATCH_BYTES and FFTB_NOALLOC_TABLE_BYTES,
  * which every GPU that loads the library holds until the process exits.
- * Bands are processed in chunks that fit the scratch. A sphere whose single
- * band's stick buffer (N2 * sticks * 8 bytes) or whose tables exceed these
- * sizes is rejected with FFTB_ERR_UNSUPPORTED and a message saying which.
+ * Bands are processed in chunks that fit the scratch. Limits, each rejected
+ * with FFTB_ERR_UNSUPPORTED and a message saying which:
+ *   - one band's stick buffer (N2 * sticks * 8 bytes) above the scratch;
+ *   - tables above FFTB_NOALLOC_TABLE_BYTES (48 bytes per band plus about
+ *     8 bytes per sphere entry: some 40 000 bands of the 160^3, |G| <= 40
+ *     sphere per call);
+ *   - more than 65535 bands per call (the plans' limit);
+ *   - a slab plane (N1 x occupied x values, complex64) that does not fit in
+ *     shared memory beside the kernel's exchange rows: on 256-point grids
+ *     from |G| <= 41 (83 occupied x values) up, on 128- and 160-point grids
+ *     only for spheres far wider than the cube-width = 2 x diameter rule
+ *     (a plan keeps such slab planes in device memory instead).
  * Every call shares the arrays and leaves its contents there; nothing in them
  * needs to start at zero. Calls that overlap on the GPU (different streams or
  * host threads) race on the arrays and must be serialised by the caller.
  * The first call on a device looks up the arrays' device addresses once for
- * that device (cudaGetSymbolAddress, with the device current); make that
- * first call before any stream capture.
+ * that device (cudaGetSymbolAddress, with the device current) and keeps them
+ * for the life of the process; make that first call before any stream
+ * capture. A device reset ends the context those addresses belong to: calls
+ * after cudaDeviceReset are not supported.
  * Errors: INVALID_ARG (bad pointer, alignment, sphere that does not fit the
- * grid), UNSUPPORTED (grid extent, size limits above), CUDA. */
+ * grid), UNSUPPORTED (grid extent, the limits above, or `stream` being
+ * captured while the pageable table upload is issued), CUDA. */
 #define FFTB_NOALLOC_SCRATCH_BYTES (16u << 20)
 #define FFTB_NOALLOC_TABLE_BYTES (4u << 20)
 fftb_status fftb_g2r_noalloc(const int32_t n[3], double radius, const double* kshift,

@@ -3,8 +3,10 @@
 Compiles the CUDA translation units and the host C++ in parallel into
 ``_build/`` and links ``libfftb.so`` next to this file. Objects are rebuilt
 when their source or any header is newer. ``FFTB_NVCC_FLAGS`` (environment)
-adds nvcc flags, e.g. ``-DFFTB_PLANE_EPT_F32=16`` to try a kernel tuning
-knob; it forces a rebuild.
+adds nvcc flags, e.g. ``-DFFTB_PLANE_NW=12`` to try a kernel tuning knob; it
+forces a rebuild. ``build(check=True)`` makes the checked library
+``libfftb_check.so`` in ``_build_check/`` instead: the kernels compiled with
+``-DFFTB_CHECK`` test every index against its buffer before the access.
 """
 from __future__ import annotations
 
@@ -19,6 +21,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfftb.so")
+BUILD_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(HERE, "libfftb_check.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["k_f32.cu", "k_f32_pf.cu", "k_f32_alt.cu", "k_f32_bg.cu", "k_scale.cu", "k_f64.cu", "k_tc.cu", "k_tc5.cu", "noalloc.cu"]
@@ -58,10 +62,13 @@ def _run(cmd, verbose):
         print(r.stdout + r.stderr, flush=True)
 
 
-def build(verbose: bool = False, ptxas_verbose: bool = False) -> str:
-    """Builds (if needed) and returns the path of libfftb.so."""
+def build(verbose: bool = False, ptxas_verbose: bool = False, check: bool = False) -> str:
+    """Builds (if needed) and returns the path of libfftb.so, or with check
+    the path of libfftb_check.so (device bounds checks compiled in)."""
     cuda = _cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
+    BUILD = BUILD_CHECK if check else globals()["BUILD"]
+    LIB = LIB_CHECK if check else globals()["LIB"]
     os.makedirs(BUILD, exist_ok=True)
     deps = _headers()
     jobs = []
@@ -73,6 +80,8 @@ def build(verbose: bool = False, ptxas_verbose: bool = False) -> str:
                    "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I", CSRC, "-I", INCLUDE]
             if ptxas_verbose:
                 cmd += ["-Xptxas", "-v"]
+            if check:
+                cmd += ["-DFFTB_CHECK"]
             cmd += os.environ.get("FFTB_NVCC_FLAGS", "").split()
             jobs.append(cmd)
     for s in CPP_SOURCES:

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <fstream>
 #include <new>
@@ -15,6 +16,11 @@
 #include "../../include/fftb.h"
 #include "fftb_internal.h"
 #include "geometry.h"
+#include "tables.h"
+
+// NVTX ranges (header-only; a no-op unless a profiler is attached): one per
+// execute, per host-buffer execute, per autotune and per stage launch.
+#include <nvtx3/nvToolsExt.h>
 
 #define FFTB_EXPORT extern "C" __attribute__((visibility("default")))
 
@@ -230,17 +236,6 @@ fftb_status configure_planes(fftb_plan_s* p) {
 
 bool valid_direction(int d) { return d == FFTB_G_TO_R || d == FFTB_R_TO_G || d == FFTB_ROUNDTRIP || d == FFTB_APPLY_LOCAL; }
 
-template <typename T> void make_twiddles(int n, std::vector<unsigned char>& out) {
-  // e^{+2 pi j m / n}, m = 0..n-1, evaluated in double and rounded once.
-  out.resize(sizeof(T) * 2 * n);
-  T* p = reinterpret_cast<T*>(out.data());
-  for (int m = 0; m < n; ++m) {
-    const double a = 2.0 * M_PI * (double)m / (double)n;
-    p[2 * m] = (T)std::cos(a);
-    p[2 * m + 1] = (T)std::sin(a);
-  }
-}
-
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 void release(fftb_plan_s* p) {
@@ -264,6 +259,8 @@ void release(fftb_plan_s* p) {
 }
 
 }  // namespace
+
+static void debug_report(const fftb_plan_s* p, const char* when);
 
 FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fftb_direction dir,
                                          fftb_precision prec) {
@@ -397,52 +394,31 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   if (ent_base >= (int64_t(1) << 31)) { release(p); return fail(FFTB_ERR_UNSUPPORTED, "total sphere entries above 2^31"); }
   for (const BandInfo& bi : band) p->band_sph.push_back(bi.sph);
   p->band_sph.push_back(sph);
-  if (band.empty()) band.push_back(BandInfo{});
-  if (ent_pos.empty()) { ent_pos.push_back(0); ent_zs.push_back(0); }
-  if (stick_xy.empty()) stick_xy.push_back(0);
-  if (stick_info.empty()) stick_info.assign(4, 0);
-  if (col_info.empty()) col_info.assign(4, 0);
-  std::vector<unsigned char> tw[3];
+  TableParts tp;
+  tp.band = std::move(band);
+  tp.kinfo = std::move(kinfo);
+  tp.stick_info = std::move(stick_info);
+  tp.ent_pos = std::move(ent_pos);
+  tp.ent_zs = std::move(ent_zs);
+  tp.stick_xy = std::move(stick_xy);
+  tp.col_info = std::move(col_info);
+  tp.xmap = std::move(xmap);
   for (int dd = 0; dd < 3; ++dd) {
-    if (p->prec_kernel == P_F64) make_twiddles<double>(p->n[dd], tw[dd]);
-    else make_twiddles<float>(p->n[dd], tw[dd]);
+    if (p->prec_kernel == P_F64) make_twiddles<double>(p->n[dd], tp.tw[dd]);
+    else make_twiddles<float>(p->n[dd], tp.tw[dd]);
   }
-
-  struct Part { const void* src; size_t bytes; size_t off; };
-  std::vector<Part> parts = {
-      {band.data(), band.size() * sizeof(BandInfo), 0}, {nullptr, 0, 0},
-      {kinfo.data(), kinfo.size() * sizeof(KInfo), 0}, {stick_info.data(), stick_info.size() * 4, 0},
-      {ent_pos.data(), ent_pos.size() * 4, 0},     {ent_zs.data(), ent_zs.size() * 4, 0},
-      {stick_xy.data(), stick_xy.size() * 4, 0},   {xmap.data(), xmap.size() * 2, 0},
-      {tw[0].data(), tw[0].size(), 0},             {tw[1].data(), tw[1].size(), 0},
-      {tw[2].data(), tw[2].size(), 0},             {col_info.data(), col_info.size() * 4, 0}};
-  size_t total = 0;
-  for (auto& pt : parts) {
-    pt.off = total;
-    total = align_up(total + pt.bytes, 256);
-  }
+  const TableLayout tl = table_layout(tp);
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) { release(p); return cuda_fail(e, "cudaGetDevice"); }
-  e = cudaMalloc(&p->d_tables, total);
+  e = cudaMalloc(&p->d_tables, tl.total);
   if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaMalloc tables failed"); }
-  p->tables_bytes = total;
-  std::vector<unsigned char> blob(total, 0);
-  for (auto& pt : parts)
-    if (pt.bytes) std::memcpy(blob.data() + pt.off, pt.src, pt.bytes);
-  e = cudaMemcpy(p->d_tables, blob.data(), total, cudaMemcpyHostToDevice);
+  p->tables_bytes = tl.total;
+  std::vector<unsigned char> blob(tl.total);
+  table_fill(tp, tl, blob.data());
+  e = cudaMemcpy(p->d_tables, blob.data(), tl.total, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { release(p); return cuda_fail(e, "cudaMemcpy tables"); }
-  unsigned char* base = static_cast<unsigned char*>(p->d_tables);
   Geo& g = p->g;
-  g.band = reinterpret_cast<const BandInfo*>(base + parts[0].off);
-  g.stick_info = reinterpret_cast<const int4*>(base + parts[3].off);
-  g.ent_pos = reinterpret_cast<const int32_t*>(base + parts[4].off);
-  g.ent_zs = reinterpret_cast<const int32_t*>(base + parts[5].off);
-  g.stick_xy = reinterpret_cast<const int32_t*>(base + parts[6].off);
-  g.col_info = reinterpret_cast<const int4*>(base + parts[11].off);
-  g.xmap = reinterpret_cast<const int16_t*>(base + parts[7].off);
-  g.tw0 = base + parts[8].off;
-  g.tw1 = base + parts[9].off;
-  g.tw2 = base + parts[10].off;
+  table_geo(g, p->d_tables, tl);
   g.n0 = p->n[0];
   g.n1 = p->n[1];
   g.n2 = p->n[2];
@@ -587,6 +563,7 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   }
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) { release(p); return cuda_fail(e, "plan synchronise"); }
+  debug_report(p, "plan created");
   *out = p;
   return FFTB_OK;
 }
@@ -624,6 +601,25 @@ static int kernels_per_chunk(fftb_direction d) {
     case FFTB_APPLY_LOCAL: return 3;
   }
   return 0;
+}
+
+// FFTB_DEBUG=1 in the environment: one line on stderr per plan decision
+// (after creation and after autotuning) with the launch configuration.
+static void debug_report(const fftb_plan_s* p, const char* when) {
+  const char* e = std::getenv("FFTB_DEBUG");
+  if (!e || !*e || std::strcmp(e, "0") == 0) return;
+  fftb_plan_info_t i{};
+  fftb_plan_get_info(const_cast<fftb_plan_s*>(p), &i);
+  std::fprintf(stderr,
+               "[fftb] %s: grid %dx%dx%d dir %d prec %d layout %d k-points %d bands %d | sticks %d slabs %d | "
+               "chunk %d bands, %lld kernels/execute | z CTAs %d, plane CTAs %d | slab buffers %d%s | "
+               "prefetch mask %d | schedule plane %d stick %d | tcgen05 %d | band group %d | PDL %d | "
+               "scratch %lld bytes\n",
+               when, p->n[0], p->n[1], p->n[2], (int)p->dir, (int)p->prec, p->layout, p->nk, p->total_bands,
+               i.max_sticks, i.max_slabs, i.chunk_bands, (long long)i.kernels_per_execute, i.stick_ctas,
+               i.plane_ctas, i.slab_buffers, i.slab_planes_global ? " (global)" : "", i.prefetch,
+               i.radix_schedule_plane, i.radix_schedule_stick, i.tensor_core_planes, i.plane_band_group,
+               i.dependent_launch, (long long)i.scratch_bytes);
 }
 
 FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) {
@@ -665,6 +661,14 @@ FFTB_EXPORT fftb_status fftb_set_potential(fftb_plan p, const void* v) {
 }
 
 enum StageKind { K_STICK_G2R = 0, K_PLANE_G2R = 1, K_PLANE_R2G = 2, K_STICK_R2G = 3, K_PLANE_APPLY = 4 };
+static const char* const kStageName[5] = {"fftb z stage G->r", "fftb y/x stages G->r", "fftb x/y stages r->G",
+                                          "fftb z stage r->G", "fftb y/x apply"};
+
+// RAII NVTX range
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 static cudaEvent_t next_event(fftb_plan_s* p, int* idx) {
   if (p->ev_used == (int)p->ev_pool.size()) {
@@ -678,6 +682,7 @@ static cudaEvent_t next_event(fftb_plan_s* p, int* idx) {
 
 // Launches one stage kernel, bracketed by events when timing is enabled.
 static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
+  NvtxRange range(kStageName[kind]);
   int a = -1, b = -1;
   cudaEvent_t ea = nullptr, eb = nullptr;
   if (p->timing) {
@@ -778,6 +783,10 @@ static fftb_status enqueue(fftb_plan_s* p, int bands, const void* in, void* out,
   L.status = p->d_status;
   L.pdl = p->pdl ? 1 : 0;
   L.groups = static_cast<const int2*>(p->d_groups);
+  L.lim_sph = p->sphere_elems;
+  L.lim_cube = p->cube_elems;
+  L.lim_T = (int64_t)(p->T_bytes / p->csize);
+  L.lim_V = (int64_t)p->n[0] * p->n[1] * p->n[2];
   L.stream = s;
   if (p->bg && (first >= p->total_bands || p->band_grp[first] < 0))
     return fail(FFTB_ERR_INVALID_ARG, "a grouped launch must start at a band group");
@@ -896,6 +905,7 @@ static fftb_status launch_all(fftb_plan_s* p, int bands, const void* in, void* o
 }
 
 FFTB_EXPORT fftb_status fftb_execute(fftb_plan p, const void* in, void* out, void* cube, void* stream) {
+  NvtxRange range("fftb_execute");
   if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
   if (p->total_bands == 0) return FFTB_OK;
   if (!in || !out) return fail(FFTB_ERR_INVALID_ARG, "in and out must be device pointers");
@@ -912,6 +922,14 @@ FFTB_EXPORT fftb_status fftb_execute(fftb_plan p, const void* in, void* out, voi
   return launch_all(p, p->total_bands, in, out, cube, static_cast<cudaStream_t>(stream));
 }
 
+// The error a nonzero device status word stands for (bits STATUS_BOUNDS of a
+// checked build, else a bounded wait that ran out).
+static fftb_status device_status_error(int32_t st, const char* tail) {
+  if (st & 2)
+    return fail(FFTB_ERR_DEVICE_BOUNDS, std::string("a checked kernel found an index outside its buffer; ") + tail);
+  return fail(FFTB_ERR_DEVICE_TIMEOUT, std::string("a plane-stage wait for an asynchronous copy ran out; ") + tail);
+}
+
 static fftb_status ensure(void** ptr, size_t* have, size_t need) {
   if (*have >= need && *ptr) return FFTB_OK;
   if (*ptr) cudaFree(*ptr);
@@ -924,6 +942,7 @@ static fftb_status ensure(void** ptr, size_t* have, size_t need) {
 
 FFTB_EXPORT fftb_status fftb_execute_host(fftb_plan p, const void* in_host, void* out_host, void* cube_dev,
                                           void* stream) {
+  NvtxRange range("fftb_execute_host");
   if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
   if (!in_host || !out_host) return fail(FFTB_ERR_INVALID_ARG, "in_host and out_host must be given");
   if (p->total_bands == 0) return FFTB_OK;
@@ -1005,9 +1024,9 @@ FFTB_EXPORT fftb_status fftb_execute_host(fftb_plan p, const void* in_host, void
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_end, 0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
-  if (*reinterpret_cast<volatile int32_t*>(p->h_status)) {
+  if (const int32_t st = *reinterpret_cast<volatile int32_t*>(p->h_status)) {
     *p->h_status = 0;
-    return fail(FFTB_ERR_DEVICE_TIMEOUT, "a plane-stage wait for an asynchronous copy ran out; the result is invalid");
+    return device_status_error(st, "the result is invalid");
   }
   return FFTB_OK;
 }
@@ -1016,10 +1035,9 @@ FFTB_EXPORT fftb_status fftb_plan_check(fftb_plan p) {
   if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "device synchronise");
-  if (*reinterpret_cast<volatile int32_t*>(p->h_status)) {
+  if (const int32_t st = *reinterpret_cast<volatile int32_t*>(p->h_status)) {
     *p->h_status = 0;
-    return fail(FFTB_ERR_DEVICE_TIMEOUT, "a plane-stage wait for an asynchronous copy ran out; results since the "
-                                         "previous check are invalid");
+    return device_status_error(st, "results since the previous check are invalid");
   }
   return FFTB_OK;
 }
@@ -1144,6 +1162,7 @@ FFTB_EXPORT const char* fftb_error_string(fftb_status s) {
     case FFTB_ERR_ALLOC: return "allocation failed";
     case FFTB_ERR_CUDA: return "CUDA error";
     case FFTB_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case FFTB_ERR_DEVICE_BOUNDS: return "device-side bounds check failed";
   }
   return "unknown status";
 }
@@ -1373,6 +1392,7 @@ fftb_status apply_choice(fftb_plan_s* p, const TuneChoice& c) {
 }  // namespace
 
 FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
+  NvtxRange range("fftb_plan_autotune");
   if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
   if (trials < 1) return fail(FFTB_ERR_INVALID_ARG, "trials must be >= 1");
   if (p->total_bands == 0) return FFTB_OK;
@@ -1568,5 +1588,6 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   if (st != FFTB_OK) return st;
   if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
   tune_cache_store(key, best_c);
+  debug_report(p, "autotuned");
   return FFTB_OK;
 }

@@ -78,6 +78,9 @@ struct Launch {
   int32_t pdl;          // launch with programmatic dependent launch (overlaps launch and prologue)
   const int2* groups;   // batch-fastest band groups (first band, bands), plan-global list
   int32_t grp0, ngrp;   // the groups of this launch (they cover [band0, band0 + nb))
+  // buffer extents in complex elements from the base pointers above, read by
+  // the bounds checks of a checked build (FFTB_CHECK) only
+  int64_t lim_sph, lim_cube, lim_T, lim_V;
   cudaStream_t stream;
 };
 

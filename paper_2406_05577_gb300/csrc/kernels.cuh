@@ -26,6 +26,7 @@
 #include <utility>
 
 #include "async_copy.cuh"
+#include "check.cuh"
 #include "fft_core.cuh"
 #include "fftb_internal.h"
 #include "line_fft.cuh"
@@ -138,7 +139,9 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
 #pragma unroll
           for (int j = 0; j < LZ::R0; ++j) {
             const int d = zsigned(LZ::first_pos(g, m, j)) - k.si.w;
-            v[m * LZ::R0 + j] = (unsigned)d < (unsigned)len ? in[k.si.z + d] : czero<C>();
+            v[m * LZ::R0 + j] = (unsigned)d < (unsigned)len && FFTB_IN(k.sph + k.si.z + d, L.lim_sph, L.status)
+                                    ? in[k.si.z + d]
+                                    : czero<C>();
           }
       } else {  // batch-fastest: B_k apart
 #pragma unroll
@@ -146,15 +149,22 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
 #pragma unroll
           for (int j = 0; j < LZ::R0; ++j) {
             const int d = zsigned(LZ::first_pos(g, m, j)) - k.si.w;
-            v[m * LZ::R0 + j] = (unsigned)d < (unsigned)len ? in[(int64_t)(k.si.z + d) * k.st] : czero<C>();
+            v[m * LZ::R0 + j] =
+                (unsigned)d < (unsigned)len && FFTB_IN(k.sph + (int64_t)(k.si.z + d) * k.st, L.lim_sph, L.status)
+                    ? in[(int64_t)(k.si.z + d) * k.st]
+                    : czero<C>();
           }
       }
     } else {
-      const C* Tb = static_cast<const C*>(L.T) + (size_t)k.bl * N2 * smax + k.s0 + (l < k.nl ? l : 0);
+      const size_t tb = (size_t)k.bl * N2 * smax + k.s0 + (l < k.nl ? l : 0);
+      const C* Tb = static_cast<const C*>(L.T) + tb;
 #pragma unroll
       for (int m = 0; m < EZ / LZ::R0; ++m)
 #pragma unroll
-        for (int j = 0; j < LZ::R0; ++j) v[m * LZ::R0 + j] = Tb[(size_t)LZ::first_pos(g, m, j) * smax];
+        for (int j = 0; j < LZ::R0; ++j)
+          v[m * LZ::R0 + j] = FFTB_IN(tb + (size_t)LZ::first_pos(g, m, j) * smax, L.lim_T, L.status)
+                                  ? Tb[(size_t)LZ::first_pos(g, m, j) * smax]
+                                  : czero<C>();
     }
   };
   // transform and write a task whose inputs are in v
@@ -163,11 +173,14 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
       if constexpr (TC) LZ::template run_tc<+1>(v, g, row, scr, tw, tc, tcw);
       else LZ::template run<+1>(v, g, row, tw, tc);
       if (l < k.nl) {
-        C* Tb = static_cast<C*>(L.T) + (size_t)k.bl * N2 * smax + k.s0 + l;
+        const size_t tb = (size_t)k.bl * N2 * smax + k.s0 + l;
+        C* Tb = static_cast<C*>(L.T) + tb;
 #pragma unroll
         for (int m = 0; m < EZ / LZ::RL; ++m)
 #pragma unroll
-          for (int j = 0; j < LZ::RL; ++j) Tb[(size_t)LZ::last_pos(g, m, j) * smax] = v[m * LZ::RL + j];
+          for (int j = 0; j < LZ::RL; ++j)
+            if (FFTB_IN(tb + (size_t)LZ::last_pos(g, m, j) * smax, L.lim_T, L.status))
+              Tb[(size_t)LZ::last_pos(g, m, j) * smax] = v[m * LZ::RL + j];
       }
     } else {
       if constexpr (TC) LZ::template run_tc<-1>(v, g, row, scr, tw, tc, tcw);
@@ -182,7 +195,8 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
 #pragma unroll
               for (int j = 0; j < LZ::RL; ++j) {
                 const int d = zsigned(LZ::last_pos(g, m, j)) - k.si.w;
-                if ((unsigned)d < (unsigned)len) out[k.si.z + d] = v[m * LZ::RL + j];
+                if ((unsigned)d < (unsigned)len && FFTB_IN(k.sph + k.si.z + d, L.lim_sph, L.status))
+                  out[k.si.z + d] = v[m * LZ::RL + j];
               }
           } else {
 #pragma unroll
@@ -190,7 +204,9 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
 #pragma unroll
               for (int j = 0; j < LZ::RL; ++j) {
                 const int d = zsigned(LZ::last_pos(g, m, j)) - k.si.w;
-                if ((unsigned)d < (unsigned)len) out[(int64_t)(k.si.z + d) * k.st] = v[m * LZ::RL + j];
+                if ((unsigned)d < (unsigned)len &&
+                    FFTB_IN(k.sph + (int64_t)(k.si.z + d) * k.st, L.lim_sph, L.status))
+                  out[(int64_t)(k.si.z + d) * k.st] = v[m * LZ::RL + j];
               }
           }
         }
@@ -204,7 +220,8 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
         __syncwarp();
         for (int e = ea + lane; e < eb; e += 32) {
           const uint32_t zs = (uint32_t)L.g.ent_zs[e];
-          out[(int64_t)L.g.ent_pos[e] * k.st] = scr[((int)(zs & 0xFFFFFFu) - k.s0) * LZ::PITCH + wpad((int)(zs >> 24))];
+          if (FFTB_IN(k.sph + (int64_t)L.g.ent_pos[e] * k.st, L.lim_sph, L.status))
+            out[(int64_t)L.g.ent_pos[e] * k.st] = scr[((int)(zs & 0xFFFFFFu) - k.s0) * LZ::PITCH + wpad((int)(zs >> 24))];
         }
         __syncwarp();
       }
@@ -219,7 +236,8 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
     __syncwarp();
     for (int e = ea + lane; e < eb; e += 32) {
       const uint32_t zs = (uint32_t)L.g.ent_zs[e];
-      scr[((int)(zs & 0xFFFFFFu) - k.s0) * LZ::PITCH + wpad((int)(zs >> 24))] = in[(int64_t)L.g.ent_pos[e] * k.st];
+      if (FFTB_IN(k.sph + (int64_t)L.g.ent_pos[e] * k.st, L.lim_sph, L.status))
+        scr[((int)(zs & 0xFFFFFFu) - k.s0) * LZ::PITCH + wpad((int)(zs >> 24))] = in[(int64_t)L.g.ent_pos[e] * k.st];
     }
     __syncwarp();
 #pragma unroll
@@ -432,7 +450,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   auto issue_trow = [&](int pp) {
     const int bl2 = pp / n2, z2 = pp - bl2 * n2;
     const int S2 = L.g.band[L.band0 + bl2].ki.S;
-    const uint32_t bytes = (uint32_t)((S2 * (int)sizeof(C) + 15) & ~15);
+    uint32_t bytes = (uint32_t)((S2 * (int)sizeof(C) + 15) & ~15);
+    if (bytes && !FFTB_IN(((size_t)bl2 * n2 + z2) * L.g.smax + bytes / sizeof(C) - 1, L.lim_T, L.status)) bytes = 0;
     fence_proxy_async_smem();
     mbar_arrive_expect(bars, bytes);
     if (bytes) bulk_g2s(stg, static_cast<const C*>(L.T) + ((size_t)bl2 * n2 + z2) * L.g.smax, bytes, bars);
@@ -446,9 +465,13 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   auto issue_rows = [&](int pp, int t) {
     const int bl2 = pp / n2, z2 = pp - bl2 * n2;
     const int r0 = t * WX, nr = min(WX, N1 - r0);
-    const C* src = static_cast<const C*>(L.cube_in) + ((size_t)(L.band0 + bl2) * n2 + z2) * (size_t)(N1 * N0) +
-                   (size_t)r0 * N0;
+    const size_t first = ((size_t)(L.band0 + bl2) * n2 + z2) * (size_t)(N1 * N0) + (size_t)r0 * N0;
+    const C* src = static_cast<const C*>(L.cube_in) + first;
     fence_proxy_async_smem();
+    if (!FFTB_IN(first + (size_t)nr * N0 - 1, L.lim_cube, L.status)) {
+      mbar_arrive_expect(bars + warp, 0);  // nothing copied: the phase completes at once
+      return;
+    }
     mbar_arrive_expect(bars + warp, (uint32_t)(nr * N0 * sizeof(C)));
     if constexpr (RP == N0) {
       bulk_g2s(wst, src, (uint32_t)(nr * N0 * sizeof(C)), bars + warp);
@@ -492,9 +515,13 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   auto issue_xrows = [&](int pp, int t) {
     const int bl2 = pp / n2, z2 = pp - bl2 * n2;
     const int r0 = t * WX, nr = min(WX, N1 - r0);
-    const C* src = static_cast<const C*>(L.cube_in) + ((size_t)(L.band0 + bl2) * n2 + z2) * (size_t)(N1 * N0) +
-                   (size_t)r0 * N0;
+    const size_t first = ((size_t)(L.band0 + bl2) * n2 + z2) * (size_t)(N1 * N0) + (size_t)r0 * N0;
+    const C* src = static_cast<const C*>(L.cube_in) + first;
     fence_proxy_async_smem();
+    if (!FFTB_IN(first + (size_t)nr * N0 - 1, L.lim_cube, L.status)) {
+      mbar_arrive_expect(xbar + warp, 0);  // nothing copied: the phase completes at once
+      return;
+    }
     mbar_arrive_expect(xbar + warp, (uint32_t)(nr * N0 * sizeof(C)));
     for (int r = 0; r < nr; ++r)
       bulk_g2s(xrows + r * LX::PITCH, src + (size_t)r * N0, (uint32_t)(N0 * sizeof(C)), xbar + warp);
@@ -535,7 +562,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
     C* A = A0 + parity * abuf;
     const int4* __restrict__ cinfo = L.g.col_info + ki.col_base;
     const int32_t* sxy = L.g.stick_xy + ki.stick_base;
-    C* Tz = static_cast<C*>(L.T) + ((size_t)bl * n2 + z) * L.g.smax;
+    const size_t tz = ((size_t)bl * n2 + z) * L.g.smax;  // first element of this plane's stick row
+    C* Tz = static_cast<C*>(L.T) + tz;
     const size_t plane = (size_t)bi.cube + (size_t)z * (size_t)(N1 * N0) * (size_t)cst;
     const int ty = (X + WY - 1) / WY;       // y tasks of this plane
     const int tx = (N1 + WX - 1) / WX;      // x tasks
@@ -564,7 +592,10 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
             for (int j = 0; j < LY::R0; ++j) {
               const int d = ysigned(LY::first_pos(gy, m, j)) - ylo;
               if constexpr (PF) v[m * LY::R0 + j] = (unsigned)d < (unsigned)len ? Tr[sa + d] : czero<C>();
-              else v[m * LY::R0 + j] = (unsigned)d < (unsigned)len ? ld_once<AG>(Tr + sa + d) : czero<C>();
+              else
+                v[m * LY::R0 + j] = (unsigned)d < (unsigned)len && FFTB_IN(tz + sa + d, L.lim_T, L.status)
+                                        ? ld_once<AG>(Tr + sa + d)
+                                        : czero<C>();
             }
         } else {
           const int sbeg = __shfl_sync(0xffffffffu, ci.x, 0);
@@ -574,7 +605,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
           for (int s = sbeg + lane; s < send; s += 32) {
             const int xy = sxy[s];
             if constexpr (PF) scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)] = Tr[s];
-            else scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)] = ld_once<AG>(Tr + s);
+            else if (FFTB_IN(tz + s, L.lim_T, L.status))
+              scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)] = ld_once<AG>(Tr + s);
           }
           __syncwarp();
 #pragma unroll
@@ -589,7 +621,9 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
           for (int m = 0; m < EY / LY::RL; ++m)
 #pragma unroll
-            for (int j = 0; j < LY::RL; ++j) A[LY::last_pos(gy, m, j) * XP + c0 + ly] = v[m * LY::RL + j];
+            for (int j = 0; j < LY::RL; ++j)
+              if (FFTB_IN(LY::last_pos(gy, m, j) * XP + c0 + ly, abuf, L.status))
+                A[LY::last_pos(gy, m, j) * XP + c0 + ly] = v[m * LY::RL + j];
         }
       }
       if constexpr (PF) {
@@ -613,7 +647,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
         for (int q = 0; q < EX; ++q) {
           const int xi = xin.get(q);
-          v[q] = (live && xi != 255) ? A[row * XP + xi] : czero<C>();
+          v[q] = (live && xi != 255 && FFTB_IN(row * XP + xi, abuf, L.status)) ? A[row * XP + xi] : czero<C>();
         }
         if constexpr (TC) LX::template run_tc<+1>(v, gx, rowx, scr, tw0, tcx, wx_p);
         else LX::template run<+1>(v, gx, rowx, tw0, tcx);
@@ -623,13 +657,17 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
             for (int m = 0; m < EX / LX::RL; ++m)
 #pragma unroll
-              for (int j = 0; j < LX::RL; ++j) st_once<AG>(out + LX::last_pos(gx, m, j), v[m * LX::RL + j]);
+              for (int j = 0; j < LX::RL; ++j)
+                if (FFTB_IN(plane + (size_t)row * N0 + LX::last_pos(gx, m, j), L.lim_cube, L.status))
+                  st_once<AG>(out + LX::last_pos(gx, m, j), v[m * LX::RL + j]);
           } else if (live) {  // batch-fastest cube: points B_k apart
             C* out = static_cast<C*>(L.cube_out) + plane + (size_t)row * N0 * cst;
 #pragma unroll
             for (int m = 0; m < EX / LX::RL; ++m)
 #pragma unroll
-              for (int j = 0; j < LX::RL; ++j) st_once<AG>(out + (size_t)LX::last_pos(gx, m, j) * cst, v[m * LX::RL + j]);
+              for (int j = 0; j < LX::RL; ++j)
+                if (FFTB_IN(plane + (size_t)row * N0 * cst + (size_t)LX::last_pos(gx, m, j) * cst, L.lim_cube, L.status))
+                  st_once<AG>(out + (size_t)LX::last_pos(gx, m, j) * cst, v[m * LX::RL + j]);
           }
         } else {
           // V(r) * psi(r), then back to first-pass order and x-DFT (-)
@@ -639,7 +677,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
             for (int j = 0; j < LX::RL; ++j) {
               const int x = LX::last_pos(gx, m, j);
-              rowx[wpad(x)] = scale(v[m * LX::RL + j], __ldg(vr + x));
+              const bool vin = FFTB_IN((size_t)z * (N1 * N0) + (size_t)(live ? row : 0) * N0 + x, L.lim_V, L.status);
+              rowx[wpad(x)] = scale(v[m * LX::RL + j], vin ? __ldg(vr + x) : T(0));
             }
           __syncwarp();
 #pragma unroll
@@ -653,7 +692,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
             for (int q = 0; q < EX; ++q) {
               const int xi = xout.get(q);
-              if (xi != 255) A[row * XP + xi] = v[q];
+              if (xi != 255 && FFTB_IN(row * XP + xi, abuf, L.status)) A[row * XP + xi] = v[q];
             }
           }
         }
@@ -727,14 +766,21 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
           for (int m = 0; m < EX / LX::R0; ++m)
 #pragma unroll
             for (int j = 0; j < LX::R0; ++j)
-              v[m * LX::R0 + j] = live ? ld_once<AG>(in + LX::first_pos(gx, m, j)) : czero<C>();
+              v[m * LX::R0 + j] =
+                  live && FFTB_IN(plane + (size_t)row * N0 + LX::first_pos(gx, m, j), L.lim_cube, L.status)
+                      ? ld_once<AG>(in + LX::first_pos(gx, m, j))
+                      : czero<C>();
         } else {  // batch-fastest cube: points B_k apart
           const C* in = static_cast<const C*>(L.cube_in) + plane + (size_t)(live ? row : 0) * N0 * cst;
 #pragma unroll
           for (int m = 0; m < EX / LX::R0; ++m)
 #pragma unroll
             for (int j = 0; j < LX::R0; ++j)
-              v[m * LX::R0 + j] = live ? ld_once<AG>(in + (size_t)LX::first_pos(gx, m, j) * cst) : czero<C>();
+              v[m * LX::R0 + j] =
+                  live && FFTB_IN(plane + (size_t)row * N0 * cst + (size_t)LX::first_pos(gx, m, j) * cst, L.lim_cube,
+                                  L.status)
+                      ? ld_once<AG>(in + (size_t)LX::first_pos(gx, m, j) * cst)
+                      : czero<C>();
         }
         if constexpr (TC) LX::template run_tc<-1>(v, gx, rowx, scr, tw0, tcx, wx_m);
         else if constexpr (XS) {
@@ -751,7 +797,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
           for (int q = 0; q < EX; ++q) {
             const int xi = xout.get(q);
-            if (xi != 255) A[row * XP + xi] = v[q];
+            if (xi != 255 && FFTB_IN(row * XP + xi, abuf, L.status)) A[row * XP + xi] = v[q];
           }
         }
       }
@@ -782,7 +828,10 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
         for (int m = 0; m < EY / LY::R0; ++m)
 #pragma unroll
-          for (int j = 0; j < LY::R0; ++j) v[m * LY::R0 + j] = A[LY::first_pos(gy, m, j) * XP + col];
+          for (int j = 0; j < LY::R0; ++j)
+            v[m * LY::R0 + j] = FFTB_IN(LY::first_pos(gy, m, j) * XP + col, abuf, L.status)
+                                    ? A[LY::first_pos(gy, m, j) * XP + col]
+                                    : czero<C>();
         if constexpr (TC) LY::template run_tc<-1>(v, gy, rowy, scr, tw1, tcy, wy_m);
         else LY::template run<-1>(v, gy, rowy, tw1, tcy);
         if (ki.flags & KF_CONTIGUOUS_COLUMNS) {
@@ -793,7 +842,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
               for (int j = 0; j < LY::RL; ++j) {
                 const int d = ysigned(LY::last_pos(gy, m, j)) - ylo;
-                if ((unsigned)d < (unsigned)len) Tz[sa + d] = v[m * LY::RL + j];
+                if ((unsigned)d < (unsigned)len && FFTB_IN(tz + sa + d, L.lim_T, L.status)) Tz[sa + d] = v[m * LY::RL + j];
               }
           }
         } else {
@@ -806,7 +855,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
           const int send = __shfl_sync(0xffffffffu, ci.x + ci.y, (nl - 1) * LY::G);
           for (int s = sbeg + lane; s < send; s += 32) {
             const int xy = sxy[s];
-            Tz[s] = scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)];
+            if (FFTB_IN(tz + s, L.lim_T, L.status)) Tz[s] = scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)];
           }
           __syncwarp();
         }

@@ -12,8 +12,10 @@
 // the library holds until the process exits.
 //
 // The first call on a device looks up the arrays' device addresses
-// (cudaGetSymbolAddress, once per device, with that device current); make
-// that first call before any stream capture.
+// (cudaGetSymbolAddress, once per device, with that device current) and
+// keeps them for the life of the process; make that first call before any
+// stream capture. A device reset (cudaDeviceReset) ends the context those
+// addresses belong to: calls after a reset are not supported.
 //
 // The scratch is the stick buffer T between the z-stage and the plane stage
 // (the same kernels as a G_TO_R plan). Every call shares both arrays and
@@ -33,6 +35,7 @@
 #include "../../include/fftb.h"
 #include "fftb_internal.h"
 #include "geometry.h"
+#include "tables.h"
 
 namespace fftb {
 template <typename T, bool TC> size_t plane_smem_t(int, int, int, int, bool);
@@ -76,8 +79,6 @@ fftb_status device_arrays(int dev, void** scratch, void** tables) {
   return FFTB_OK;
 }
 
-size_t align256(size_t v) { return (v + 255) / 256 * 256; }
-
 }  // namespace
 
 extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
@@ -86,6 +87,7 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
   using namespace fftb;
   if (!n) return err(FFTB_ERR_INVALID_ARG, "n is NULL");
   if (bands < 0) return err(FFTB_ERR_INVALID_ARG, "bands must be >= 0");
+  if (bands > 65535) return err(FFTB_ERR_UNSUPPORTED, "at most 65535 bands per call (as per plan)");
   if (!grid_size_supported(n[0]) || !grid_size_supported(n[1]) || !grid_size_supported(n[2]) ||
       !plane_size_supported(n[0], n[1]))
     return err(FFTB_ERR_UNSUPPORTED, "grid extents must be one of 12,16,20,24,32,40,48,64,96,128,160,256 with N0 == N1");
@@ -111,53 +113,45 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
   const int chunk = (int)std::min<size_t>((size_t)bands, FFTB_NOALLOC_SCRATCH_BYTES / t_band);
   const int a_bufs = plane_smem_t<float, false>(n[0], n[1], G.X, 2, false) <= 227 * 1024 ? 2 : 1;
   if (plane_smem_t<float, false>(n[0], n[1], G.X, a_bufs, false) > 227 * 1024)
-    return err(FFTB_ERR_UNSUPPORTED, "plane does not fit in shared memory");
+    return err(FFTB_ERR_UNSUPPORTED, "the slab plane (N1 x " + std::to_string(G.X) +
+                                         " occupied x values) does not fit in shared memory; this entry point has "
+                                         "no global slab-plane scratch (a plan has)");
 
-  // tables, packed like a one-k-point plan
+  // tables of a one-k-point plan, packed by the plans' own helper
   KInfo ki{G.S, G.X, 0, 0, 0,
            (G.contiguous_columns ? KF_CONTIGUOUS_COLUMNS : 0) | (G.canonical_sticks ? KF_CANONICAL_STICKS : 0), 1};
   const int64_t vol = (int64_t)n[0] * n[1] * n[2];
-  std::vector<BandInfo> band((size_t)bands);
+  TableParts tp;
+  tp.band.resize((size_t)bands);
   for (int b = 0; b < bands; ++b) {
-    band[b].ki = ki;
-    band[b].sph = (int64_t)b * G.ngw;
-    band[b].cube = (int64_t)b * vol;
+    tp.band[b].ki = ki;
+    tp.band[b].sph = (int64_t)b * G.ngw;
+    tp.band[b].cube = (int64_t)b * vol;
   }
-  std::vector<float> tw[3];
-  for (int d = 0; d < 3; ++d) {
-    tw[d].resize(2 * (size_t)n[d]);
-    for (int m = 0; m < n[d]; ++m) {
-      const double a = 2.0 * M_PI * (double)m / (double)n[d];
-      tw[d][2 * m] = (float)std::cos(a);
-      tw[d][2 * m + 1] = (float)std::sin(a);
-    }
-  }
-  std::vector<int32_t> one_zero(1, 0), sinfo, cinfo;
-  stick_records(G, n, 0, sinfo);
-  slab_records(G, n, cinfo);
-  if (sinfo.empty()) sinfo.assign(4, 0);
-  if (cinfo.empty()) cinfo.assign(4, 0);
-  const std::vector<int32_t>& pos = G.ent_pos.empty() ? one_zero : G.ent_pos;
-  const std::vector<int32_t>& zs = G.ent_zs.empty() ? one_zero : G.ent_zs;
-  const std::vector<int32_t>& sxy = G.stick_xy.empty() ? one_zero : G.stick_xy;
-  struct Part { const void* p; size_t bytes; size_t off; };
-  Part parts[] = {{band.data(), band.size() * sizeof(BandInfo), 0}, {nullptr, 0, 0},
-                  {&ki, sizeof(KInfo), 0},                {sinfo.data(), sinfo.size() * 4, 0},
-                  {pos.data(), pos.size() * 4, 0},         {zs.data(), zs.size() * 4, 0},
-                  {sxy.data(), sxy.size() * 4, 0},         {G.xmap.data(), G.xmap.size() * 2, 0},
-                  {tw[0].data(), tw[0].size() * 4, 0},     {tw[1].data(), tw[1].size() * 4, 0},
-                  {tw[2].data(), tw[2].size() * 4, 0},     {cinfo.data(), cinfo.size() * 4, 0}};
-  size_t total = 0;
-  for (Part& p : parts) {
-    p.off = total;
-    total = align256(total + p.bytes);
-  }
-  if (total > FFTB_NOALLOC_TABLE_BYTES)
-    return err(FFTB_ERR_UNSUPPORTED, "geometry tables (" + std::to_string(total) +
-                                         " bytes) exceed FFTB_NOALLOC_TABLE_BYTES");
+  tp.kinfo.push_back(ki);
+  stick_records(G, n, 0, tp.stick_info);
+  slab_records(G, n, tp.col_info);
+  tp.ent_pos = G.ent_pos;
+  tp.ent_zs = G.ent_zs;
+  tp.stick_xy = G.stick_xy;
+  tp.xmap = G.xmap;
+  for (int d = 0; d < 3; ++d) make_twiddles<float>(n[d], tp.tw[d]);
+  const TableLayout tl = table_layout(tp);
+  if (tl.total > FFTB_NOALLOC_TABLE_BYTES)
+    return err(FFTB_ERR_UNSUPPORTED, "geometry tables for " + std::to_string(bands) + " bands (" +
+                                         std::to_string(tl.total) + " bytes: 48 per band plus the sphere's records) "
+                                         "exceed FFTB_NOALLOC_TABLE_BYTES; split the bands over several calls");
 
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the table upload below copies from pageable host memory, which a stream
+  // capture does not take
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+  if (ce != cudaSuccess) return err(FFTB_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce));
+  if (cap != cudaStreamCaptureStatusNone)
+    return err(FFTB_ERR_UNSUPPORTED, "stream is being captured: the table upload copies from pageable host memory");
   int dev = 0;
-  cudaError_t ce = cudaGetDevice(&dev);
+  ce = cudaGetDevice(&dev);
   if (ce != cudaSuccess) return err(FFTB_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
   void* scratch = nullptr;
   void* tables = nullptr;
@@ -166,26 +160,15 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
   ce = prepare_t<float, false>(n[0], n[1], n[2], G.X, a_bufs, false);
   if (ce != cudaSuccess) return err(FFTB_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(ce));
 
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  std::vector<unsigned char> blob(total, 0);
-  for (const Part& p : parts)
-    if (p.bytes) std::memcpy(blob.data() + p.off, p.p, p.bytes);
-  // pageable source: the call returns once the bytes are staged, so blob may go
-  ce = cudaMemcpyAsync(tables, blob.data(), total, cudaMemcpyHostToDevice, s);
+  std::vector<unsigned char> blob(tl.total);
+  table_fill(tp, tl, blob.data());
+  // pageable source: the copy returns once the bytes are staged (it may block
+  // the host until then), so blob may go when the call returns
+  ce = cudaMemcpyAsync(tables, blob.data(), tl.total, cudaMemcpyHostToDevice, s);
   if (ce != cudaSuccess) return err(FFTB_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(ce));
 
-  unsigned char* base = static_cast<unsigned char*>(tables);
   Launch L{};
-  L.g.band = reinterpret_cast<const BandInfo*>(base + parts[0].off);
-  L.g.stick_info = reinterpret_cast<const int4*>(base + parts[3].off);
-  L.g.ent_pos = reinterpret_cast<const int32_t*>(base + parts[4].off);
-  L.g.ent_zs = reinterpret_cast<const int32_t*>(base + parts[5].off);
-  L.g.stick_xy = reinterpret_cast<const int32_t*>(base + parts[6].off);
-  L.g.col_info = reinterpret_cast<const int4*>(base + parts[11].off);
-  L.g.xmap = reinterpret_cast<const int16_t*>(base + parts[7].off);
-  L.g.tw0 = base + parts[8].off;
-  L.g.tw1 = base + parts[9].off;
-  L.g.tw2 = base + parts[10].off;
+  table_geo(L.g, tables, tl);
   L.g.n0 = n[0];
   L.g.n1 = n[1];
   L.g.n2 = n[2];
@@ -195,6 +178,10 @@ extern "C" __attribute__((visibility("default"))) fftb_status fftb_g2r_noalloc(
   L.cube_out = out_dev;
   L.T = scratch;
   L.a_bufs = a_bufs;
+  L.lim_sph = (int64_t)bands * G.ngw;
+  L.lim_cube = (int64_t)bands * vol;
+  L.lim_T = (int64_t)(FFTB_NOALLOC_SCRATCH_BYTES / 8);
+  L.lim_V = 0;
   L.stream = s;
   for (int b0 = 0; b0 < bands; b0 += chunk) {
     L.band0 = b0;

@@ -14,10 +14,12 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libfftb.so")
+# FFTB_LIBRARY selects another in-tree build of the library, e.g. the checked
+# one (build.build(check=True) -> libfftb_check.so)
+LIB_PATH = os.environ.get("FFTB_LIBRARY") or os.path.join(HERE, "libfftb.so")
 
 FFTB_OK, FFTB_ERR_INVALID_ARG, FFTB_ERR_UNSUPPORTED, FFTB_ERR_ALLOC, FFTB_ERR_CUDA, \
-    FFTB_ERR_DEVICE_TIMEOUT = range(6)
+    FFTB_ERR_DEVICE_TIMEOUT, FFTB_ERR_DEVICE_BOUNDS = range(7)
 FFTB_G_TO_R, FFTB_R_TO_G, FFTB_ROUNDTRIP, FFTB_APPLY_LOCAL = 1, -1, 0, 2
 FFTB_FP64, FFTB_FP32, FFTB_MIXED_TC = 0, 1, 2
 FFTB_INJECT_SKIP_FIRST_PREFETCH = 1
