@@ -350,7 +350,7 @@ size_t plane_smem_c(int xmax, int a_bufs, bool ag = false, int pf_mode = 0, int 
   using C = typename cplx<T>::type;
   return sizeof(C) * ((ag ? 0 : (size_t)a_bufs * N1 * a_pitch(xmax)) +
                       (size_t)PlaneCfg<T>::NW * plane_scratch<N0, N1, V>() + N0 + N1) +
-         plane_pf_bytes<T, N0, N1>(pf_mode, tp) + (V == 2 ? sizeof(uint64_t) * PlaneCfg<T>::NW : 0);
+         plane_pf_bytes<T, N0, N1>(pf_mode, tp) + (V == 2 ? sizeof(uint64_t) * PlaneCfg<T>::NW : 0) + 16;
 }
 
 // packed per-lane slab indices: byte q of w[q / 4] = xi of position q, 255 = empty
@@ -401,6 +401,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   constexpr bool XS = V == 2 && !AG && !PF && !TC;
   static_assert(!XS || (LX::PITCH * sizeof(C)) % 16 == 0, "staged rows start on 16-byte boundaries");
   uint64_t* xbar = reinterpret_cast<uint64_t*>(tw1 + N1);
+  // end of the layout (8-byte aligned): the slab-plane barrier of single-buffer kernels
+  uint64_t* afree = PF ? bars + (MODE == M_R2G ? NW : 1) : (XS ? xbar + NW : reinterpret_cast<uint64_t*>(tw1 + N1));
   C* wst = stg + warp * (WX * RP);
   {
     const C* t0 = static_cast<const C*>(L.g.tw0);
@@ -419,6 +421,10 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
       mbar_init(xbar + threadIdx.x, 1);
       mbar_init_fence();
     }
+  }
+  if (threadIdx.x == 0 && nbuf == 1) {
+    mbar_init(afree, NW);
+    mbar_init_fence();
   }
   pdl_launch_dependents();
   __syncthreads();
@@ -526,6 +532,31 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
     for (int r = 0; r < nr; ++r)
       bulk_g2s(xrows + r * LX::PITCH, src + (size_t)r * N0, (uint32_t)(N0 * sizeof(C)), xbar + warp);
   };
+  // One slab-plane buffer: instead of a block barrier at the end of every
+  // plane, each warp arrives on afree after its last read of the plane's slab
+  // plane, and waits for that phase before its first write of the next
+  // plane's, so warps still finishing a plane overlap the others' start of
+  // the next (one phase per plane, NW arrivals; at most one phase ahead).
+  const bool a_single = nbuf == 1;
+  uint32_t a_phase = 0;     // this CTA's plane count: the phase of the current plane
+  bool a_got = false;       // this warp has waited for the previous plane's phase
+  bool a_rel = false;       // this warp has arrived for the current plane
+  auto a_acquire = [&]() {  // warp-uniform, before a slab-plane write
+    if (a_single && a_phase > 0 && !a_got) {
+      if (!mbar_wait(afree, (a_phase - 1) & 1, WAIT_LIMIT_NS)) {
+        bad = true;
+        *reinterpret_cast<volatile int32_t*>(L.status) = STATUS_WAIT_TIMEOUT;
+      }
+      a_got = true;
+    }
+  };
+  auto a_release = [&]() {  // warp-uniform, after the warp's last slab-plane read of the plane
+    if (a_single && !a_rel) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(afree);
+      a_rel = true;
+    }
+  };
   int cur_k = -1;
   XiPack<EX> xin, xout;  // slab index of this lane's first-pass / last-pass x positions
   int parity = 0;
@@ -617,6 +648,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
         }
         if constexpr (TC) LY::template run_tc<+1>(v, gy, rowy, scr, tw1, tcy, wy_p);
         else LY::template run<+1>(v, gy, rowy, tw1, tcy);
+        a_acquire();
         if (ly < nl) {
 #pragma unroll
           for (int m = 0; m < EY / LY::RL; ++m)
@@ -649,6 +681,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
           const int xi = xin.get(q);
           v[q] = (live && xi != 255 && FFTB_IN(row * XP + xi, abuf, L.status)) ? A[row * XP + xi] : czero<C>();
         }
+        if (MODE == M_G2R && t + NW >= tx) a_release();
         if constexpr (TC) LX::template run_tc<+1>(v, gx, rowx, scr, tw0, tcx, wx_p);
         else LX::template run<+1>(v, gx, rowx, tw0, tcx);
         if constexpr (MODE == M_G2R) {
@@ -793,6 +826,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
             }
           });
         } else LX::template run<-1>(v, gx, rowx, tw0, tcx);
+        a_acquire();
         if (live) {
 #pragma unroll
           for (int q = 0; q < EX; ++q) {
@@ -832,6 +866,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
             v[m * LY::R0 + j] = FFTB_IN(LY::first_pos(gy, m, j) * XP + col, abuf, L.status)
                                     ? A[LY::first_pos(gy, m, j) * XP + col]
                                     : czero<C>();
+        if (t + NW >= ty) a_release();
         if constexpr (TC) LY::template run_tc<-1>(v, gy, rowy, scr, tw1, tcy, wy_m);
         else LY::template run<-1>(v, gy, rowy, tw1, tcy);
         if (ki.flags & KF_CONTIGUOUS_COLUMNS) {
@@ -861,7 +896,11 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
         }
       }
     }
-    if (nbuf == 1) __syncthreads();
+    // the end of this plane: warps without a slab-plane read arrive now
+    a_release();
+    ++a_phase;
+    a_got = false;
+    a_rel = false;
   }
 }
 
