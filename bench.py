@@ -13,8 +13,11 @@ replayed, autotuned launch sequence; 128^3 local-potential apply V(r) psi(r)
 with 256 bands; 256^3 (sphere diameter 128) with 256 bands, the paper's own
 single-GPU shape; the 64^3 workload in the batch-fastest layout.
 
-Under torchrun each rank runs its own copy of the workload on its own GPU
-(bands are independent: weak scaling, no collective on the data path).
+Under torchrun the job is one global batch of world x B bands per k-point;
+each rank transforms its contiguous shard of B bands (band_shard) on its own
+GPU (bands are independent: weak scaling, no collective on the data path;
+the only collectives are the timing barrier and the max of the step time
+over ranks).
 Timing follows the paper's protocol (Sec. 4.2: warm-up iterations, then
 timed iterations, mean) with CUDA events on the launching stream; L2 is
 flushed between timed steps. ``--impl reference`` times the FP64 CPU oracle
@@ -102,12 +105,17 @@ class Workload:
             kw["kshift"] = self.kshift
         return kw
 
-    def coefficients(self, spheres, rank=0):
-        """This rank's bands: rank r holds bands [r B, (r + 1) B) of a global
-        batch of world * B bands (weak scaling), drawn with per-rank seeds."""
+    def coefficients(self, spheres, rank=0, world=1):
+        """This rank's bands of the job's global batch: per k-point the job
+        holds world * B_k bands (weak scaling: B_k per rank), split by
+        band_shard into contiguous shards; band i of a k-point's global batch
+        is drawn from its own stream, so the shards are slices of one batch
+        whatever the world size."""
+        from paper_2406_05577_gb300.shard import band_shard
         parts = []
         for k, (g, b) in enumerate(zip(spheres, self.bands)):
-            c = fi.complex_gaussian((b, len(g)), self.seed + 100 * k + 7919 * rank)
+            start, count = band_shard(world * b, world, rank)
+            c = fi.complex_gaussian_bands(start, count, len(g), self.seed + 100 * k)
             if self.envelope:
                 c = c * fi.gaussian_envelope(g, self.envelope)[None, :]
             parts.append(c)
@@ -405,7 +413,7 @@ def run_ours(args):
     ngws = [len(g) for g in spheres]
     sticks = [fftb.fftb_sphere_sticks(w.n, g)[0] for g in spheres]
     slabs = [fftb.fftb_sphere_sticks(w.n, g)[1] for g in spheres]
-    parts = w.coefficients(spheres, rank)
+    parts = w.coefficients(spheres, rank, world)
     # batch-fastest: each k-point's block is [ngw][B]
     c = np.concatenate([(p.T if w.layout else p).reshape(-1) for p in parts]).astype(np.complex64)
     x = torch.from_numpy(c).to(dev)
@@ -747,7 +755,10 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": w.desc, "name": w.name, "grid": list(w.n), "radius": w.radius,
                            "ngw": ngws, "bands_per_gpu": w.total_bands, "precision": "fp32",
-                           "parallelism": f"bands x{world}", "chunk_bands": plan.info["chunk_bands"],
+                           "parallelism": f"bands x{world}", "global_bands": world * w.total_bands,
+                           "shard": "contiguous band shards of one global batch (band_shard), no collective "
+                                    "on the data path",
+                           "chunk_bands": plan.info["chunk_bands"],
                            "graph": w.graph, "graph_launches_in_timed_steps": graph_steps, "autotuned": w.tune,
                            "l2": "flushed between timed steps (256 MiB write)"},
                 "rel_l2": err,

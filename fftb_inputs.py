@@ -6,7 +6,8 @@ fed bit-identical inputs from it.
 
 Recipes (plane-wave DFT workloads, Sec. 2.2 of the paper; no dataset exists):
   * coefficients c_b(G): i.i.d. complex Gaussian, real and imaginary parts each
-    N(0, 1), from numpy's PCG64 ``default_rng(seed)``;
+    N(0, 1), from numpy's PCG64 ``default_rng(seed)`` (or one stream per band,
+    ``default_rng([seed, band])``, for batches sharded across ranks);
   * optional envelope exp(-|G|^2 / (2 sigma^2)) (sigma = 8 grid units for the
     64^3 round-trip workload);
   * k-shifts uniform in [-0.5, 0.5)^3 grid units;
@@ -42,6 +43,20 @@ def complex_gaussian(shape, seed: int) -> np.ndarray:
     re = rng.standard_normal(shape)
     im = rng.standard_normal(shape)
     return re + 1j * im
+
+
+def complex_gaussian_bands(first: int, count: int, ngw: int, seed: int) -> np.ndarray:
+    """Bands first .. first + count - 1 of a batch of sphere coefficients,
+    (count, ngw) complex128, where band i is drawn from its own stream
+    default_rng([seed, i]) (ngw real parts, then ngw imaginary parts, each
+    N(0, 1)): a contiguous slice of the batch is the same whichever process
+    draws it, so ranks that each draw their shard hold one global batch."""
+    out = np.empty((count, ngw), dtype=np.complex128)
+    for j in range(count):
+        rng = np.random.default_rng([seed, first + j])
+        out[j].real = rng.standard_normal(ngw)
+        out[j].imag = rng.standard_normal(ngw)
+    return out
 
 
 def gaussian_envelope(gvec: np.ndarray, sigma: float) -> np.ndarray:
