@@ -77,7 +77,11 @@ typedef enum {
 typedef enum {
   FFTB_FP64 = 0,          /* complex128 storage and arithmetic                   */
   FFTB_FP32 = 1,          /* complex64 storage and arithmetic                    */
-  FFTB_MIXED_TC = 2       /* complex64 storage; split-precision tensor-core radix stages */
+  FFTB_MIXED_TC = 2       /* complex64 storage; split-precision tensor-core radix stages:
+                             the y/x stages of grids 16-64 (N0 == N1, band-major) as dense
+                             tcgen05 products, radix-8 passes on mma.sync at the lengths
+                             whose schedule has one (64, 128); a stage of any other length
+                             (no tensor-core pass: 24, 96, 160, ...) runs the FP32 kernels */
 } fftb_precision;
 
 /* Plan description. Either radius (+ kshift) or g_list describes the spheres. */
@@ -132,6 +136,11 @@ typedef struct {
   int64_t graph_launches;     /* executes so far that ran as one CUDA graph launch       */
   double scale_g2r;           /* output normalisation factors (fftb_plan_set_scale)     */
   double scale_r2g;
+  int32_t generic_path;       /* 1: extents outside the compiled list (N0 != N1, or an
+                              extent not in 12..256 of the list): runtime-length z,
+                              y and x kernels with a slab buffer between y and x    */
+  int32_t tensor_core_passes; /* MIXED_TC: stages whose radix-8 passes run on mma.sync
+                              (bit 0 z, bit 1 plane); 0 where no stage has one      */
 } fftb_plan_info_t;
 
 /* Builds the spheres, stick/slab tables and twiddles on the host, uploads

@@ -159,6 +159,12 @@ struct fftb_plan_s {
   void* d_tc5w = nullptr;
   int tc5_ctas = 0;
   int stick_prec = P_F32;
+  // generic-extent path (extents outside the compiled list, N0 != N1): one
+  // runtime-length kernel per axis and a slab buffer S between y and x
+  bool generic = false;
+  GenParams gen[3] = {};  // per axis x, y, z: the schedules and the line groups of its kernel
+  void* d_S = nullptr;
+  size_t S_bytes = 0;
   int32_t inject = 0;              // fftb_plan_inject
   int32_t* h_status = nullptr;     // status word in mapped pinned host memory
   int32_t* d_status = nullptr;     // its device address
@@ -253,6 +259,7 @@ void release(fftb_plan_s* p) {
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->h_status) cudaFreeHost(p->h_status);
   if (p->d_tc5w) cudaFree(p->d_tc5w);
+  if (p->d_S) cudaFree(p->d_S);
   if (p->d_groups) cudaFree(p->d_groups);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   delete p;
@@ -261,6 +268,52 @@ void release(fftb_plan_s* p) {
 }  // namespace
 
 static void debug_report(const fftb_plan_s* p, const char* when);
+
+// n >= 1 with no prime factors but 2, 3 and 5, and at most nmax
+static bool generic_extent_ok(int n, int nmax) {
+  if (n < 1 || n > nmax) return false;
+  for (int f : {2, 3, 5})
+    while (n % f == 0) n /= f;
+  return n == 1;
+}
+
+// Radix schedule of a runtime-length line (generic path): 8 while 8 divides
+// what is left, then 4, 2, 3, 5.
+static GenAxis generic_axis(int n) {
+  GenAxis a{};
+  a.n = n;
+  int m = n;
+  while (m % 8 == 0) { a.r[a.np++] = 8; m /= 8; }
+  while (m % 4 == 0) { a.r[a.np++] = 4; m /= 4; }
+  while (m % 2 == 0) { a.r[a.np++] = 2; m /= 2; }
+  while (m % 3 == 0) { a.r[a.np++] = 3; m /= 3; }
+  while (m % 5 == 0) { a.r[a.np++] = 5; m /= 5; }
+  return a;
+}
+
+// Generic path: the per-axis schedules, the line groups each kernel holds in
+// shared memory (up to 64 lines in about 96 KB), and the slab buffer.
+static fftb_status setup_generic(fftb_plan_s* p) {
+  GenParams g{};
+  for (int a = 0; a < 3; ++a) g.ax[a] = generic_axis(p->n[a]);
+  for (int a = 0; a < 3; ++a) {
+    p->gen[a] = g;
+    const int n = p->n[a];
+    const int pitch = n | 1;  // odd pitch: Stockham strides of lines held side by side spread over the banks
+    const size_t budget = (96u << 10) / p->csize;
+    const int lpc = (int)std::max<size_t>(1, std::min<size_t>(64, (budget > (size_t)n ? budget - n : 0) / (2 * (size_t)pitch)));
+    p->gen[a].lpc = lpc;
+    p->gen[a].pitch = pitch;
+  }
+  p->S_bytes = (size_t)p->chunk * p->n[2] * std::max(p->xmax, 1) * p->n[1] * p->csize;
+  if (cudaMalloc(&p->d_S, p->S_bytes) != cudaSuccess) return fail(FFTB_ERR_ALLOC, "cudaMalloc slab buffer failed");
+  for (int a = 0; a < 3; ++a) {
+    p->gen[a].S = p->d_S;
+    p->gen[a].lim_S = (int64_t)(p->S_bytes / p->csize);
+  }
+  p->tiles = p->sms * 4;  // CTAs of a generic launch (about 96 KB of shared memory each: two per SM)
+  return FFTB_OK;
+}
 
 FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fftb_direction dir,
                                          fftb_precision prec) {
@@ -276,10 +329,16 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   if (d->layout != 0 && d->layout != 1) return fail(FFTB_ERR_INVALID_ARG, "layout must be 0 (band-major) or 1 (batch-fastest)");
   if (d->max_chunk_bands < 0) return fail(FFTB_ERR_INVALID_ARG, "max_chunk_bands must be >= 0");
   if (d->g_list && !d->g_count) return fail(FFTB_ERR_INVALID_ARG, "g_list given without g_count");
-  if (!grid_size_supported(d->n[0]) || !grid_size_supported(d->n[1]) || !grid_size_supported(d->n[2]) ||
-      !plane_size_supported(d->n[0], d->n[1]))
-    return fail(FFTB_ERR_UNSUPPORTED,
-                "grid extents must be one of 12,16,20,24,32,40,48,64,96,128,160,256 with N0 == N1");
+  // compiled kernels for the listed extents with N0 == N1; every other extent
+  // whose prime factors are 2, 3 and 5 takes the generic-extent path
+  const bool fast = grid_size_supported(d->n[0]) && grid_size_supported(d->n[1]) && grid_size_supported(d->n[2]) &&
+                    plane_size_supported(d->n[0], d->n[1]);
+  if (!fast) {
+    for (int i = 0; i < 3; ++i)
+      if (!generic_extent_ok(d->n[i], i == 2 ? 256 : 512))
+        return fail(FFTB_ERR_UNSUPPORTED,
+                    "grid extents must have no prime factors but 2, 3 and 5, with N0, N1 <= 512 and N2 <= 256");
+  }
 
   fftb_plan_s* p = new (std::nothrow) fftb_plan_s();
   if (!p) return fail(FFTB_ERR_ALLOC, "host allocation failed");
@@ -289,6 +348,16 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   p->dir = dir;
   p->prec = prec;
   p->prec_kernel = (prec == FFTB_FP64) ? P_F64 : (prec == FFTB_MIXED_TC) ? P_TC : P_F32;
+  p->generic = !fast;
+  if (p->generic && p->prec_kernel == P_TC) p->prec_kernel = P_F32;  // the generic path has no tensor-core stage
+  // MIXED_TC stages whose length has no tensor-core pass (no radix-8 pass in
+  // its schedule: 24, 96, 160, ...) are FP32 arithmetic: they run on the FP32
+  // kernels, with those kernels' alternative schedules and prefetching
+  p->stick_prec = p->prec_kernel;
+  if (p->prec_kernel == P_TC && !tc_pass_in_schedule(d->n[2])) p->stick_prec = P_F32;
+  if (p->prec_kernel == P_TC && !(d->layout == 0 && tc5_supported(d->n[0], d->n[1])) &&
+      !tc_pass_in_schedule(d->n[0]) && !tc_pass_in_schedule(d->n[1]))
+    p->prec_kernel = P_F32;
   p->csize = (prec == FFTB_FP64) ? 16 : 8;
   p->geo.resize(p->nk);
   p->bands.resize(p->nk);
@@ -325,6 +394,7 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   if (p->total_bands > 65535) { release(p); return fail(FFTB_ERR_UNSUPPORTED, "more than 65535 bands in one plan"); }
 
   const size_t smem_limit = kSmemLimit;
+  if (!p->generic) {
   if (plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, 2) > smem_limit) p->a_bufs = 1;
   if (plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, p->a_bufs) > smem_limit && p->n[0] >= 128) {
     // slab planes in global memory, one buffer per CTA by default (two double
@@ -341,6 +411,7 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   }
   const int ts = stick_tile(p->prec_kernel, p->n[2]);
   p->tiles = p->smax > 0 ? (p->smax + ts - 1) / ts : 1;
+  }  // !generic
   const int32_t smax_pitch = (std::max<int32_t>(p->smax, 1) + 1) & ~1;
   p->tpitch = smax_pitch;
 
@@ -348,9 +419,13 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   // give every launch at least about 2048 (band, z) planes so the persistent
   // plane CTAs have several planes each; or as requested
   const size_t t_band = (size_t)p->n[2] * smax_pitch * p->csize;
+  // (generic path: stick and slab buffers of a chunk within 512 MB)
+  const size_t s_band = (size_t)p->n[2] * std::max(p->xmax, 1) * p->n[1] * p->csize;
   int chunk = d->max_chunk_bands > 0
                   ? d->max_chunk_bands
-                  : (int)std::max<size_t>({(size_t)1, (48u << 20) / t_band, (size_t)((2048 + p->n[2] - 1) / p->n[2])});
+                  : p->generic ? (int)std::max<size_t>(1, (512u << 20) / (t_band + s_band))
+                               : (int)std::max<size_t>({(size_t)1, (48u << 20) / t_band,
+                                                        (size_t)((2048 + p->n[2] - 1) / p->n[2])});
   chunk = std::max(1, std::min(chunk, std::max(1, p->total_bands)));
   p->chunk = chunk;
 
@@ -432,6 +507,11 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
   if (e != cudaSuccess) { release(p); return cuda_fail(e, "device attribute"); }
   p->sms = sms;
+  if (p->generic) {
+    fftb_status gst = setup_generic(p);
+    if (gst != FFTB_OK) { release(p); return gst; }
+  }
+  if (!p->generic) {
   fftb_status cst = configure_planes(p);
   if (cst != FFTB_OK) { release(p); return cst; }
   if (p->a_bufs == 2 && !p->a_glob) {
@@ -446,7 +526,6 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
       if (cst != FFTB_OK) { release(p); return cst; }
     }
   }
-  p->stick_prec = p->prec_kernel;
   // the tcgen05 plane kernels read and write band-major cube planes
   if (p->prec_kernel == P_TC && p->layout == 0 && tc5_supported(p->n[0], p->n[1])) {
     // union over k-points of the occupied x values and the stick y values
@@ -508,12 +587,13 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
     p->alt_stick_ok = p->alt_stick_occ >= 1;
   }
   p->tiles = sms * p->stick_occ;  // z stage: one wave of persistent CTAs (the autotuner may pick one warp per task pair)
+  }  // !generic
   e = cudaHostAlloc(reinterpret_cast<void**>(&p->h_status), sizeof(int32_t), cudaHostAllocMapped);
   if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaHostAlloc status word failed"); }
   *p->h_status = 0;
   e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&p->d_status), p->h_status, 0);
   if (e != cudaSuccess) { release(p); return cuda_fail(e, "status word device address"); }
-  if (p->layout == 1 && p->prec_kernel == P_F32 && p->n[0] == p->n[1] && p->total_bands > 0) {
+  if (!p->generic && p->layout == 1 && p->prec_kernel == P_F32 && p->n[0] == p->n[1] && p->total_bands > 0) {
     // batch-fastest: plane stages over groups of bands of one k-point, where they fit
     const int bgs = plane_bg_group(p->n[0]);
     if (bgs > 1 && plane_bg_smem(p->n[0], p->n[1], p->xmax, bgs) <= kSmemLimit) {
@@ -593,12 +673,15 @@ static int scale_launches(const fftb_plan_s* p) {
   const bool cube = p->scale_g2r != 1.0 && (p->dir == FFTB_G_TO_R || p->dir == FFTB_ROUNDTRIP);
   return (cube ? 1 : 0) + (sphere_scale(p) != 1.0 ? 1 : 0);
 }
-static int kernels_per_chunk(fftb_direction d) {
-  switch (d) {
-    case FFTB_G_TO_R: return 2;
-    case FFTB_R_TO_G: return 2;
-    case FFTB_ROUNDTRIP: return 4;
-    case FFTB_APPLY_LOCAL: return 3;
+// Stage kernels per band chunk (the generic path runs the y and x stages as
+// two kernels, and the fused apply as y, x-apply, y)
+static int kernels_per_chunk(const fftb_plan_s* p) {
+  const int g = p->generic ? 1 : 0;
+  switch (p->dir) {
+    case FFTB_G_TO_R: return 2 + g;
+    case FFTB_R_TO_G: return 2 + g;
+    case FFTB_ROUNDTRIP: return 4 + 2 * g;
+    case FFTB_APPLY_LOCAL: return 3 + 2 * g;
   }
   return 0;
 }
@@ -626,12 +709,12 @@ FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) 
   if (!p || !info) return fail(FFTB_ERR_INVALID_ARG, "NULL argument");
   info->sphere_elems = p->sphere_elems;
   info->cube_elems = p->cube_elems;
-  info->scratch_bytes = (int64_t)(p->T_bytes + p->tables_bytes);
+  info->scratch_bytes = (int64_t)(p->T_bytes + p->tables_bytes + p->S_bytes + p->A_bytes);
   info->total_bands = p->total_bands;
   info->max_sticks = p->smax;
   info->max_slabs = p->xmax;
   info->chunk_bands = p->chunk;
-  info->kernels_per_execute = count_chunks(p, 0, p->total_bands) * kernels_per_chunk(p->dir) +
+  info->kernels_per_execute = count_chunks(p, 0, p->total_bands) * kernels_per_chunk(p) +
                               (p->total_bands > 0 ? scale_launches(p) : 0);
   info->scale_g2r = p->scale_g2r;
   info->scale_r2g = p->scale_r2g;
@@ -649,6 +732,8 @@ FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) 
   info->dependent_launch = p->pdl ? 1 : 0;
   info->plane_band_group = p->bg;
   info->graph_launches = p->graph_launches;
+  info->generic_path = p->generic ? 1 : 0;
+  info->tensor_core_passes = (p->stick_prec == P_TC ? 1 : 0) | (p->prec_kernel == P_TC && !p->tc5 ? 2 : 0);
   return FFTB_OK;
 }
 
@@ -693,6 +778,31 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
   }
   cudaError_t e;
   const int pk = p->prec_kernel;
+  if (p->generic) {
+    // z, y, x stages as separate runtime-length kernels (stage 0 z, 1 y, 2 x, 3 x apply)
+    const bool f64 = pk == P_F64;
+    const int ctas = p->tiles;
+    auto gen = [&](int st, int sign) { return launch_generic(f64, st, sign, L, p->gen[st == 3 ? 0 : 2 - st], ctas); };
+    int n = 0;
+    switch (kind) {
+      case K_STICK_G2R: e = gen(0, +1); n = 1; break;
+      case K_PLANE_G2R: e = gen(1, +1); if (e == cudaSuccess) e = gen(2, +1); n = 2; break;
+      case K_PLANE_R2G: e = gen(2, -1); if (e == cudaSuccess) e = gen(1, -1); n = 2; break;
+      case K_STICK_R2G: e = gen(0, -1); n = 1; break;
+      default:
+        e = gen(1, +1);
+        if (e == cudaSuccess) e = gen(3, +1);
+        if (e == cudaSuccess) e = gen(1, -1);
+        n = 3;
+        break;
+    }
+    if (e == cudaSuccess) p->launches += n;
+    if (p->timing) {
+      cudaEventRecord(eb, L.stream);
+      p->recs.push_back({kind, a, b});
+    }
+    return e;
+  }
   // bulk copies read the cube from 16-byte aligned rows
   const bool cube_in_16 = (reinterpret_cast<uintptr_t>(L.cube_in) % 16) == 0;
   switch (kind) {
@@ -864,7 +974,7 @@ static fftb_status launch_all(fftb_plan_s* p, int bands, const void* in, void* o
   if (!s && !p->cap_stream && cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return fail(FFTB_ERR_CUDA, "capture stream creation failed");
   cudaStream_t cap = s ? s : p->cap_stream;
-  const int64_t per_exec = (int64_t)count_chunks(p, 0, p->total_bands) * kernels_per_chunk(p->dir) + scale_launches(p);
+  const int64_t per_exec = (int64_t)count_chunks(p, 0, p->total_bands) * kernels_per_chunk(p) + scale_launches(p);
   if (!(p->gexec && p->g_in == in && p->g_out == out && p->g_cube == cube && p->g_V == p->d_V)) {
     const int64_t before = p->launches;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
@@ -1044,6 +1154,7 @@ FFTB_EXPORT fftb_status fftb_plan_check(fftb_plan p) {
 
 FFTB_EXPORT fftb_status fftb_plan_set_prefetch(fftb_plan p, int32_t level) {
   if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (p->generic) return fail(FFTB_ERR_UNSUPPORTED, "a plan on the generic-extent path has no kernel variants");
   if (level < 0 || level > 2) return fail(FFTB_ERR_INVALID_ARG, "prefetch level must be 0, 1 or 2");
   for (int i = 0; i < 3; ++i) {
     const bool was = pf_active(p, i);
@@ -1063,6 +1174,7 @@ FFTB_EXPORT fftb_status fftb_plan_set_prefetch(fftb_plan p, int32_t level) {
 
 FFTB_EXPORT fftb_status fftb_plan_set_slab_buffers(fftb_plan p, int32_t nbuf) {
   if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (p->generic) return fail(FFTB_ERR_UNSUPPORTED, "a plan on the generic-extent path has no kernel variants");
   if (nbuf != 1 && nbuf != 2) return fail(FFTB_ERR_INVALID_ARG, "slab buffers must be 1 or 2");
   if (!p->a_glob && plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, nbuf) > kSmemLimit)
     return fail(FFTB_ERR_UNSUPPORTED, "two slab planes do not fit in shared memory for this plan");
@@ -1084,6 +1196,7 @@ FFTB_EXPORT fftb_status fftb_plan_set_slab_buffers(fftb_plan p, int32_t nbuf) {
 
 FFTB_EXPORT fftb_status fftb_plan_set_radix_schedule(fftb_plan p, int32_t plane, int32_t stick) {
   if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (p->generic) return fail(FFTB_ERR_UNSUPPORTED, "a plan on the generic-extent path has no kernel variants");
   if (plane < 0 || plane > 1 || stick < 0 || stick > 1) return fail(FFTB_ERR_INVALID_ARG, "schedule must be 0 or 1");
   if (plane && !p->alt_plane_ok) return fail(FFTB_ERR_UNSUPPORTED, "no alternative radix schedule for this plane stage");
   if (stick && !p->alt_stick_ok) return fail(FFTB_ERR_UNSUPPORTED, "no alternative radix schedule for this z stage");
@@ -1123,6 +1236,7 @@ FFTB_EXPORT fftb_status fftb_plan_set_scale(fftb_plan p, double g2r, double r2g)
 
 FFTB_EXPORT fftb_status fftb_plan_set_band_groups(fftb_plan p, int32_t enable) {
   if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (p->generic) return fail(FFTB_ERR_UNSUPPORTED, "a plan on the generic-extent path has no kernel variants");
   if (enable && !p->bg_size)
     return fail(FFTB_ERR_UNSUPPORTED, "no grouped plane kernels for this plan (batch-fastest FP32, N0 == N1, fitting)");
   const int bg = enable ? p->bg_size : 0;
@@ -1395,7 +1509,7 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   NvtxRange range("fftb_plan_autotune");
   if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
   if (trials < 1) return fail(FFTB_ERR_INVALID_ARG, "trials must be >= 1");
-  if (p->total_bands == 0) return FFTB_OK;
+  if (p->total_bands == 0 || p->generic) return FFTB_OK;  // the generic-extent path has one kernel per stage
   int dev = -1;
   cudaGetDevice(&dev);
   if (dev != p->device) return fail(FFTB_ERR_INVALID_ARG, "current device differs from the plan's device");

@@ -10,6 +10,22 @@
 
 namespace fftb {
 
+// Runtime line schedule of one axis (generic-extent path): length and radices.
+constexpr int GEN_MAXP = 12;
+struct GenAxis {
+  int32_t n, np;
+  int32_t r[GEN_MAXP];
+};
+// Parameters of a generic-extent stage launch: the three axes, the slab
+// buffer S [chunk bands][N2][xmax][N1], and the line group held per CTA.
+struct GenParams {
+  GenAxis ax[3];  // x, y, z
+  void* S;
+  int64_t lim_S;  // S elements (bounds checks of a checked build)
+  int32_t lpc;    // lines per CTA group
+  int32_t pitch;  // shared-memory line pitch (elements)
+};
+
 // Per-k-point geometry as the kernels see it.
 struct KInfo {
   int32_t S;           // occupied (x,y) sticks
@@ -147,6 +163,10 @@ struct Tc5Geo {
   const void* w;
 };
 bool tc5_supported(int n0, int n1);
+// generic-extent path: stage 0 z, 1 y, 2 x, 3 fused x apply; sign +1 G -> r, -1 r -> G
+cudaError_t launch_generic(bool fp64, int stage, int sign, const Launch& L, const GenParams& P, int ctas);
+// the default line schedule of length n has a tensor-core (radix-8) pass
+bool tc_pass_in_schedule(int n);
 size_t tc5_weight_bytes(int mode, int n, const Tc5Geo& P);
 // writes the split-FP16 DFT matrices of `mode` into img (device), from the
 // plan's twiddle table tw (device, float2 e^{+2 pi i m / n}); asynchronous

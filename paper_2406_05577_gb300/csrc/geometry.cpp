@@ -127,7 +127,8 @@ std::string build_geometry(const int32_t n[3], const int32_t* g, int64_t ngw, KG
   out.S = s + 1;
   out.stick_ent.push_back((int32_t)ngw);
   for (int32_t xi = 1; xi <= out.X; ++xi) out.col_start[xi] = std::max(out.col_start[xi], out.col_start[xi - 1]);
-  if (out.S >= (1 << 15)) return "too many sticks (limit 32767)";
+  // the entry records hold the stick index in 24 bits
+  if (out.S >= (1 << 24)) return "too many sticks (limit 16777215)";
   return "";
 }
 

@@ -353,7 +353,8 @@ size_t plane_smem_c(int xmax, int a_bufs, bool ag = false, int pf_mode = 0, int 
          plane_pf_bytes<T, N0, N1>(pf_mode, tp) + (V == 2 ? sizeof(uint64_t) * PlaneCfg<T>::NW : 0) + 16;
 }
 
-// packed per-lane slab indices: byte q of w[q / 4] = xi of position q, 255 = empty
+// packed per-lane slab indices: byte q of w[q / 4] = xi of position q, 255 =
+// empty (unless all N0 x values are occupied: then 255 is slab 255)
 template <int E> struct XiPack {
   uint32_t w[(E + 3) / 4];
   __device__ __forceinline__ int get(int q) const { return (int)((w[q >> 2] >> (8 * (q & 3))) & 0xFFu); }
@@ -570,6 +571,9 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
     const int X = ki.X;
     const int cst = ki.bstride;  // cube point stride: 1 band-major, B_k batch-fastest
     const int XP = a_pitch(X);
+    // every x occupied (a full frequency box): all 256 byte values of the
+    // per-lane slab indices are slabs, none marks an empty x
+    const bool allx = X >= N0;
     if (ki.xmap_base != cur_k) {  // a new k-point (uniform across the CTA)
       cur_k = ki.xmap_base;
       const int16_t* xm = L.g.xmap + ki.xmap_base;
@@ -679,7 +683,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
         for (int q = 0; q < EX; ++q) {
           const int xi = xin.get(q);
-          v[q] = (live && xi != 255 && FFTB_IN(row * XP + xi, abuf, L.status)) ? A[row * XP + xi] : czero<C>();
+          v[q] = (live && (allx || xi != 255) && FFTB_IN(row * XP + xi, abuf, L.status)) ? A[row * XP + xi]
+                                                                                          : czero<C>();
         }
         if (MODE == M_G2R && t + NW >= tx) a_release();
         if constexpr (TC) LX::template run_tc<+1>(v, gx, rowx, scr, tw0, tcx, wx_p);
@@ -725,7 +730,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
             for (int q = 0; q < EX; ++q) {
               const int xi = xout.get(q);
-              if (xi != 255 && FFTB_IN(row * XP + xi, abuf, L.status)) A[row * XP + xi] = v[q];
+              if ((allx || xi != 255) && FFTB_IN(row * XP + xi, abuf, L.status)) A[row * XP + xi] = v[q];
             }
           }
         }
@@ -831,7 +836,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
           for (int q = 0; q < EX; ++q) {
             const int xi = xout.get(q);
-            if (xi != 255 && FFTB_IN(row * XP + xi, abuf, L.status)) A[row * XP + xi] = v[q];
+            if ((allx || xi != 255) && FFTB_IN(row * XP + xi, abuf, L.status)) A[row * XP + xi] = v[q];
           }
         }
       }

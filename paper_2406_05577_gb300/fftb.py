@@ -67,6 +67,8 @@ class fftb_plan_info_t(ctypes.Structure):
         ("graph_launches", ctypes.c_int64),
         ("scale_g2r", ctypes.c_double),
         ("scale_r2g", ctypes.c_double),
+        ("generic_path", ctypes.c_int32),
+        ("tensor_core_passes", ctypes.c_int32),
     ]
 
 

@@ -83,9 +83,12 @@ def test_explicit_list_errors(fftb):
 
 def test_plan_errors_before_device(fftb):
     E = fftb.FFTBError
-    with pytest.raises(E) as e:
-        fftb.fftb_plan_create((64, 64, 50), "roundtrip", "fp32", radius=16.0)
-    assert e.value.status == fftb.FFTB_ERR_UNSUPPORTED
+    # extents outside the compiled list take the generic path when their prime
+    # factors are 2, 3 and 5 (N0, N1 <= 512, N2 <= 256); others are refused
+    for n in ((64, 64, 49), (64, 77, 64), (520, 64, 64), (64, 64, 270)):
+        with pytest.raises(E) as e:
+            fftb.fftb_plan_create(n, "roundtrip", "fp32", radius=16.0)
+        assert e.value.status == fftb.FFTB_ERR_UNSUPPORTED, n
     with pytest.raises(E) as e:
         fftb.fftb_plan_create((24, 24, 24), "roundtrip", "fp32", radius=12.0)  # aliases
     assert e.value.status == fftb.FFTB_ERR_INVALID_ARG

@@ -57,6 +57,8 @@ roundtrip((160, 160, 160), 40.0, "fp32", [2], prefetch=2)
 roundtrip((32, 32, 48), 10.0, "fp32", [2, 3], kshift=[(0.1, 0.2, -0.3), (-0.4, 0.0, 0.25)], layout=1)
 roundtrip((256, 256, 256), 64.0, "fp32", [1])
 roundtrip((128, 128, 128), 32.0, "fp64", [1])
+roundtrip((72, 80, 90), 17.5, "fp32", [3], max_chunk_bands=2)   # generic-extent path
+roundtrip((15, 27, 25), 5.0, "fp64", [2], layout=1)
 
 # apply and an explicit (non-canonical) sphere order
 n, r = (32, 32, 32), 8.0

@@ -57,6 +57,28 @@ def test_full_box_g2r_is_the_full_3d_fft(F, n, prec):
         assert relerr(out.cpu().numpy(), oracle.g2r(g, c.astype(np.complex128), n)) <= tol
 
 
+def test_full_box_256_all_slabs_occupied(F):
+    """The whole 256^3 box (65 536 sticks, every one of the 256 x values an
+    occupied slab, slab planes in device memory): G -> r of one band against
+    the oracle, and the round trip of the box equals N0 N1 N2 times its
+    input."""
+    import torch
+    n = (256, 256, 256)
+    g = F.fftb_box_enumerate(n)
+    plan = F.Plan(n, "roundtrip", "fp32", g_lists=[g], bands=[1])
+    assert plan.info["max_sticks"] == 65536 and plan.info["max_slabs"] == 256
+    c = fi.complex_gaussian((1, len(g)), 403).astype(np.complex64)
+    x = torch.from_numpy(c.reshape(-1)).cuda()
+    out = torch.empty_like(x)
+    cube = torch.empty(plan.info["cube_elems"], dtype=torch.complex64, device="cuda")
+    plan.execute(x, out, cube)
+    torch.cuda.synchronize()
+    plan.check()
+    assert relerr(cube.cpu().numpy(), oracle.g2r(g, c[0].astype(np.complex128), n)) <= 2e-6
+    vol = 256 ** 3
+    assert relerr(out.cpu().numpy(), vol * c.reshape(-1).astype(np.complex128)) <= 2e-6
+
+
 def test_full_box_r2g_and_roundtrip(F):
     import torch
     n = (64, 64, 64)
