@@ -135,7 +135,8 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fft_core.cuh", "line_fft.cuh", "kernels.cuh", "async_copy.cuh", "k_f32_pf.cu"):
+    for f in ("fft_core.cuh", "line_fft.cuh", "kernels.cuh", "async_copy.cuh", "check.cuh", "k_f32_pf.cu",
+              "k_f32_alt.cu"):
         h.update(open(os.path.join(ROOT, "paper_2406_05577_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -557,6 +558,10 @@ def run_ours(args):
             p2.check()
             ms2 = sum(a.elapsed_time(b) for a, b in evs2) / len(evs2)
             res = {"value": w.total_bands / (ms2 / 1e3), "ms_per_step": ms2, "ratio_vs_fp32": ms2 / ms}
+            if prec == "mixed":
+                # which stages ran on the tensor cores (none where no length has a tensor-core pass)
+                res["tensor_core_stages"] = {"tcgen05_plane_stages": p2.info["tensor_core_planes"],
+                                             "mma_sync_passes_mask_z1_plane2": p2.info["tensor_core_passes"]}
             if w.direction == "roundtrip":
                 vol = float(np.prod(w.n))
                 res["rel_l2_roundtrip"] = (torch.linalg.vector_norm(o2 - vol * x2) /
