@@ -286,6 +286,7 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
 #define FFTB_PLANE_NW 8
 #endif
 
+
 template <typename T> struct PlaneCfg { static constexpr int NW = FFTB_PLANE_NW; };
 
 // In the variant with slab planes in global memory (EF), data read or written
@@ -538,7 +539,9 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   // plane, and waits for that phase before its first write of the next
   // plane's, so warps still finishing a plane overlap the others' start of
   // the next (one phase per plane, NW arrivals; at most one phase ahead).
-  const bool a_single = nbuf == 1;
+  // (slab planes in shared memory only: with slab planes in global memory,
+  // 256^3, the block barrier measured as fast or slightly faster)
+  const bool a_single = nbuf == 1 && !AG;
   uint32_t a_phase = 0;     // this CTA's plane count: the phase of the current plane
   bool a_got = false;       // this warp has waited for the previous plane's phase
   bool a_rel = false;       // this warp has arrived for the current plane
@@ -901,6 +904,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
         }
       }
     }
+    if (AG && nbuf == 1) __syncthreads();
     // the end of this plane: warps without a slab-plane read arrive now
     a_release();
     ++a_phase;
