@@ -1071,16 +1071,17 @@ FFTB_EXPORT fftb_status fftb_execute_host(fftb_plan p, const void* in_host, void
   if (st != FFTB_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // Band pieces pipelined over three streams: the copy in of piece i + 1 and
-  // the copy out of piece i - 1 overlap the transform of piece i. Two pieces
-  // measured best on GB300 (more pieces cost more in smaller, less efficient
-  // launches than they hide; kernels reading or writing page-locked host
-  // memory directly over the CPU-GPU link measured slower than the copies).
-  // A batch-fastest piece must be whole k-points (a band range of one
-  // k-point is not contiguous there): split at the k-point start nearest the
-  // middle, or not at all.
-  int bounds[3] = {0, p->total_bands / 2, p->total_bands};
-  int pieces = std::min(2, p->total_bands);
-  if (p->layout == 1 && pieces == 2) {
+  // the copy out of piece i - 1 overlap the transform of piece i, so only the
+  // first piece's copy in and the last piece's copy out are exposed. Band-major
+  // batches split into pieces of about 8192 (band, z) planes, at least two and
+  // at most 16 (a piece's launches stay large enough to fill the GPU: on the
+  // 64^3 x 64 workload this is two pieces, which measured best there; kernels
+  // reading or writing page-locked host memory directly over the CPU-GPU link
+  // measured slower than the copies). A batch-fastest piece must be whole
+  // k-points (a band range of one k-point is not contiguous there): split at
+  // the k-point start nearest the middle, or not at all.
+  std::vector<int> bounds;
+  if (p->layout == 1) {
     int best = 0, b = 0;
     for (int k = 0; k + 1 < p->nk; ++k) {
       b += p->bands[k];
@@ -1088,10 +1089,14 @@ FFTB_EXPORT fftb_status fftb_execute_host(fftb_plan p, const void* in_host, void
           (best == 0 || std::abs(2 * b - p->total_bands) < std::abs(2 * best - p->total_bands)))
         best = b;
     }
-    if (best > 0) bounds[1] = best;
-    else pieces = 1;
+    bounds = best > 0 ? std::vector<int>{0, best, p->total_bands} : std::vector<int>{0, p->total_bands};
+  } else {
+    const int64_t planes = (int64_t)p->total_bands * p->n[2];
+    int np = (int)std::max<int64_t>(2, std::min<int64_t>(16, planes / 8192));
+    np = std::max(1, std::min(np, p->total_bands));
+    for (int i = 0; i <= np; ++i) bounds.push_back((int)((int64_t)p->total_bands * i / np));
   }
-  if (pieces == 1) bounds[1] = p->total_bands;
+  const int pieces = (int)bounds.size() - 1;
   if (!p->hs[0]) {
     for (int i = 0; i < 3; ++i)
       if (cudaStreamCreateWithFlags(&p->hs[i], cudaStreamNonBlocking) != cudaSuccess)

@@ -362,3 +362,28 @@ def test_mixed_tc_apply_vs_oracle(F):
     torch.cuda.synchronize()
     want = oracle.apply_potential(g, c, v.astype(np.float64), n)
     assert relerr(out.cpu().numpy(), want) <= 1e-5
+
+
+def test_host_pipeline_many_pieces(F):
+    """A band-major batch of 25 600 (band, z) planes goes through the
+    host-buffer pipeline in three pieces (about 8192 planes each): bit for bit
+    the device entry point's results."""
+    import torch
+    n, r, bands = (64, 64, 64), 16.0, 400
+    plan = F.Plan(n, "roundtrip", "fp32", radius=r, bands=[bands])
+    g = plan.sphere(0)
+    c = fi.complex_gaussian((bands, len(g)), 85).astype(np.complex64).reshape(-1)
+    x = torch.from_numpy(c).cuda()
+    out = torch.empty_like(x)
+    cube = torch.empty(plan.info["cube_elems"], dtype=torch.complex64, device="cuda")
+    plan.execute(x, out, cube)
+    torch.cuda.synchronize()
+    l0 = plan.launches()
+    hin = torch.from_numpy(c).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    cube2 = torch.empty_like(cube)
+    F.fftb_execute_host(plan.handle, hin.data_ptr(), hout.data_ptr(), cube2.data_ptr(), None)
+    assert np.array_equal(hout.numpy(), out.cpu().numpy())
+    assert torch.equal(cube2, cube)
+    # three pieces, each its own launch sequence (at least one chunk each)
+    assert plan.launches() - l0 >= 3 * 4
