@@ -279,9 +279,10 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
 // allows, so one block barrier per plane separates its y and x phases, and a
 // warp that finishes plane p's x phase goes straight on to plane p+1's y
 // phase (with one buffer a second barrier ends each plane). A's pitch is X
-// rounded up to 2 (mod 16): conflict-free for the column writes of the y
-// phase and the row reads of the x phase. x-phase tasks are dealt out after
-// the y-phase tasks, so the warps with fewer y lines get more x rows.
+// rounded up to a residue mod 16 (a_res) chosen for the bank pattern of the
+// y phase's column writes and the x phase's row reads. x-phase tasks are
+// dealt out after the y-phase tasks, so the warps with fewer y lines get more
+// x rows.
 #ifndef FFTB_PLANE_NW
 #define FFTB_PLANE_NW 8
 #endif
@@ -311,7 +312,16 @@ template <typename T, int N0> __host__ __device__ constexpr int plane_minb() {
 #endif
 }
 
-__host__ __device__ constexpr int a_pitch(int x) { return x + ((2 - x % 16) + 16) % 16; }
+__host__ __device__ constexpr int a_pitch(int x, int r = 2) { return x + ((r - x % 16) + 16) % 16; }
+// Residue of the slab-plane pitch. 8-byte elements with G = 4 lanes per y and
+// x line: a warp's column store covers 4 rows x 8 columns and its row load 8
+// rows x 4 columns (16 and 8 banks a row); a pitch of 4 (mod 16) puts
+// successive rows 8 banks apart, so every bank is hit twice, the two
+// wavefronts that 256 bytes need at least (a pitch of 2 (mod 16) hits some
+// banks of a column store four times). Other shapes keep 2 (mod 16).
+template <typename C, int N0, int N1, int V> __host__ __device__ constexpr int a_res() {
+  return sizeof(C) == 8 && Line<N0, V>::G == 4 && Line<N1, V>::G == 4 ? 4 : 2;
+}
 template <int N0, int N1, int V = 0> __host__ __device__ constexpr int plane_scratch() {
   return (32 / Line<N1, V>::G) * Line<N1, V>::PITCH > (32 / Line<N0, V>::G) * Line<N0, V>::PITCH
              ? (32 / Line<N1, V>::G) * Line<N1, V>::PITCH
@@ -349,7 +359,7 @@ template <typename T, int N0, int N1> size_t plane_pf_bytes(int mode, int tp) {
 template <typename T, int N0, int N1, int V = 0>
 size_t plane_smem_c(int xmax, int a_bufs, bool ag = false, int pf_mode = 0, int tp = 0) {
   using C = typename cplx<T>::type;
-  return sizeof(C) * ((ag ? 0 : (size_t)a_bufs * N1 * a_pitch(xmax)) +
+  return sizeof(C) * ((ag ? 0 : (size_t)a_bufs * N1 * a_pitch(xmax, a_res<C, N0, N1, V>())) +
                       (size_t)PlaneCfg<T>::NW * plane_scratch<N0, N1, V>() + N0 + N1) +
          plane_pf_bytes<T, N0, N1>(pf_mode, tp) + (V == 2 ? sizeof(uint64_t) * PlaneCfg<T>::NW : 0) + 16;
 }
@@ -382,7 +392,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gy = lane % LY::G, ly = lane / LY::G;
   const int gx = lane % LX::G, lx = lane / LX::G;
-  const int abuf = N1 * a_pitch(L.g.xmax);
+  constexpr int AR = a_res<C, N0, N1, V>();
+  const int abuf = N1 * a_pitch(L.g.xmax, AR);
   const int nbuf = L.a_bufs;
   // slab planes: shared memory, or (AG) this CTA's block of a global buffer
   C* A0 = AG ? static_cast<C*>(L.a_glob) + (size_t)blockIdx.x * nbuf * abuf : reinterpret_cast<C*>(smem_raw);
@@ -401,6 +412,13 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   // stores by the lanes). Used where the cube is band-major and 16-byte
   // aligned (L.pf).
   constexpr bool XS = V == 2 && !AG && !PF && !TC;
+  // YS (the same schedule, G -> r): where a column's sticks are consecutive
+  // in the stick row (canonical spheres), the stick values of a warp's next y
+  // task, one contiguous run of the row, arrive by one bulk copy in the
+  // warp's exchange rows, completed on the warp's mbarrier. The copy is issued
+  // as soon as the rows are free: after the exchange of the warp's current y
+  // task, or after the exchange of its last x task of the previous plane.
+  constexpr bool YS = XS && MODE == M_G2R;
   static_assert(!XS || (LX::PITCH * sizeof(C)) % 16 == 0, "staged rows start on 16-byte boundaries");
   uint64_t* xbar = reinterpret_cast<uint64_t*>(tw1 + N1);
   // end of the layout (8-byte aligned): the slab-plane barrier of single-buffer kernels
@@ -418,7 +436,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
       mbar_init_fence();
     }
   }
-  if constexpr (XS && MODE == M_R2G) {
+  if constexpr (XS && (MODE == M_R2G || YS)) {
     if (threadIdx.x < NW) {
       mbar_init(xbar + threadIdx.x, 1);
       mbar_init_fence();
@@ -534,6 +552,51 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
     for (int r = 0; r < nr; ++r)
       bulk_g2s(xrows + r * LX::PITCH, src + (size_t)r * N0, (uint32_t)(N0 * sizeof(C)), xbar + warp);
   };
+  // YS (lane 0): the stick values of y task t of plane pp, from the even
+  // stick position at or below its first column's first stick to the end of
+  // its last column, rounded up to 16 bytes (inside the even-pitch row)
+  static_assert(!YS || WY * LY::PITCH >= WY * N1 + 2, "a task's sticks fit the warp's exchange rows");
+  static_assert(!YS || (N1 + WX - 1) / WX >= NW, "every warp has an x task in each plane");
+  auto issue_ycols = [&](int pp, int t) {
+    const int bl2 = pp / n2, z2 = pp - bl2 * n2;
+    const KInfo k2 = L.g.band[L.band0 + bl2].ki;
+    const int4* ci2 = L.g.col_info + k2.col_base;
+    const int c0 = t * WY, cl = c0 + min(WY, k2.X - c0) - 1;
+    const int s_lo = ci2[c0].x & ~1;
+    const int4 cz = ci2[cl];
+    const uint32_t bytes = (uint32_t)(((cz.x + cz.y - s_lo) * (int)sizeof(C) + 15) & ~15);
+    const size_t first = ((size_t)bl2 * n2 + z2) * L.g.smax + s_lo;
+    fence_proxy_async_smem();
+    if (bytes == 0 || !FFTB_IN(first + bytes / sizeof(C) - 1, L.lim_T, L.status)) {
+      mbar_arrive_expect(xbar + warp, 0);  // nothing copied: the phase completes at once
+      return;
+    }
+    mbar_arrive_expect(xbar + warp, bytes);
+    bulk_g2s(xrows, static_cast<const C*>(L.T) + first, bytes, xbar + warp);
+  };
+  // YS (warp-uniform): this warp's first y task of plane pn, if pn's columns
+  // are staged and the warp has a y task there (withheld under test injection)
+  auto ys_issue_first = [&](int pn, bool withhold) {
+    if (!YS || bad || pn >= nplanes) return;
+    const KInfo kn = L.g.band[L.band0 + pn / n2].ki;
+    if (!(kn.flags & KF_CONTIGUOUS_COLUMNS) || warp >= (kn.X + WY - 1) / WY) return;
+    __syncwarp();
+    if (lane == 0 && !withhold) issue_ycols(pn, warp);
+    xpend = true;
+  };
+  // waits for this warp's outstanding row copy (XS, YS); a wait that runs out marks the CTA bad
+  auto xwait = [&]() {
+    if (xpend && !bad) {
+      const bool ok = mbar_wait(xbar + warp, xph, WAIT_LIMIT_NS);
+      if (__any_sync(0xffffffffu, ok)) {
+        xpend = false;
+        xph ^= 1;
+      } else {
+        bad = true;
+      }
+    }
+  };
+  if constexpr (YS) ys_issue_first(blockIdx.x, (L.inject & INJECT_SKIP_FIRST_PREFETCH) && blockIdx.x == 0 && warp == 0);
   // One slab-plane buffer: instead of a block barrier at the end of every
   // plane, each warp arrives on afree after its last read of the plane's slab
   // plane, and waits for that phase before its first write of the next
@@ -573,7 +636,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
     const KInfo ki = bi.ki;
     const int X = ki.X;
     const int cst = ki.bstride;  // cube point stride: 1 band-major, B_k batch-fastest
-    const int XP = a_pitch(X);
+    const int XP = a_pitch(X, AR);
     // every x occupied (a full frequency box): all 256 byte values of the
     // per-lane slab indices are slabs, none marks an empty x
     const bool allx = X >= N0;
@@ -621,7 +684,20 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
         C v[EY];
         const int col = c0 + (ly < nl ? ly : 0);
         const int4 ci = cinfo[col];  // first stick, sticks, signed gy of the first
-        if (ki.flags & KF_CONTIGUOUS_COLUMNS) {
+        if (YS && (ki.flags & KF_CONTIGUOUS_COLUMNS)) {
+          // the task's sticks, staged from the even position sb on
+          xwait();
+          const int sb = __shfl_sync(0xffffffffu, ci.x, 0) & ~1;
+          const int sa = ci.x - sb, len = ci.y, ylo = ci.z;
+#pragma unroll
+          for (int m = 0; m < EY / LY::R0; ++m)
+#pragma unroll
+            for (int j = 0; j < LY::R0; ++j) {
+              const int d = ysigned(LY::first_pos(gy, m, j)) - ylo;
+              v[m * LY::R0 + j] = (unsigned)d < (unsigned)len ? xrows[sa + d] : czero<C>();
+            }
+          __syncwarp();
+        } else if (ki.flags & KF_CONTIGUOUS_COLUMNS) {
           // each column's sticks are consecutive in gy: index them directly
           const int sa = ci.x, len = ci.y, ylo = ci.z;
 #pragma unroll
@@ -654,7 +730,15 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
           __syncwarp();
         }
         if constexpr (TC) LY::template run_tc<+1>(v, gy, rowy, scr, tw1, tcy, wy_p);
-        else LY::template run<+1>(v, gy, rowy, tw1, tcy);
+        else if constexpr (YS) {
+          // once the exchange rows have been read back, fetch the next y task's sticks into them
+          LY::template run2<+1>(v, gy, rowy, tw1, tcy, [] {}, [&] {
+            if ((ki.flags & KF_CONTIGUOUS_COLUMNS) && !bad && t + NW < ty) {
+              if (lane == 0) issue_ycols(p, t + NW);
+              xpend = true;
+            }
+          });
+        } else LY::template run<+1>(v, gy, rowy, tw1, tcy);
         a_acquire();
         if (ly < nl) {
 #pragma unroll
@@ -674,6 +758,13 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
         const int pn = p + gridDim.x;
         if (threadIdx.x == 0 && pn < nplanes) issue_trow(pn);
         outstanding = pn < nplanes;
+      } else if constexpr (YS) {
+        if (__syncthreads_or(bad)) {
+          // leaving after a failed wait: let this warp's copies in flight land, report
+          if (xpend) mbar_wait(xbar + warp, xph, WAIT_LIMIT_NS);
+          if (threadIdx.x == 0) *reinterpret_cast<volatile int32_t*>(L.status) = STATUS_WAIT_TIMEOUT;
+          return;
+        }
       } else {
         __syncthreads();
       }
@@ -691,7 +782,12 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
         }
         if (MODE == M_G2R && t + NW >= tx) a_release();
         if constexpr (TC) LX::template run_tc<+1>(v, gx, rowx, scr, tw0, tcx, wx_p);
-        else LX::template run<+1>(v, gx, rowx, tw0, tcx);
+        else if constexpr (YS) {
+          // after the last exchange of this warp's x phase: the next plane's first y task
+          LX::template run2<+1>(v, gx, rowx, tw0, tcx, [] {}, [&] {
+            if (t + NW >= tx) ys_issue_first(p + gridDim.x, false);
+          });
+        } else LX::template run<+1>(v, gx, rowx, tw0, tcx);
         if constexpr (MODE == M_G2R) {
           if (live && cst == 1) {
             C* out = static_cast<C*>(L.cube_out) + plane + (size_t)row * N0;

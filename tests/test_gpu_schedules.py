@@ -146,3 +146,47 @@ def test_160_two_pass_rows_by_bulk_copies(F):
     torch.cuda.synchronize()
     plan.check()
     assert torch.equal(out, ref)
+
+
+def test_160_two_pass_g2r_staged_sticks(F):
+    """G -> r on the 160 = 40 x 4 plane schedule, whose y tasks take their
+    sticks by bulk copies into the warps' exchange rows where each column's
+    sticks are consecutive in gy: a canonical sphere with a k-point shift and
+    a sphere with one whole stick taken out of a column (copies off for its
+    planes), 2 + 3 bands in chunks of 2 that straddle the k-points, against
+    the oracle; then one copy withheld: the bounded wait runs out, the status
+    is reported, and the next execute is correct."""
+    import torch
+    n, r = (160, 160, 160), 40.0
+    g0 = oracle.sphere_gvectors(n, r, (0.3, -0.2, 0.1))
+    g1 = oracle.sphere_gvectors(n, r)
+    g1 = g1[~((g1[:, 0] == 5) & (g1[:, 1] == 0))]  # a gap in the column x = 5
+    plan = F.Plan(n, "g2r", "fp32", g_lists=[g0, g1], bands=[2, 3], max_chunk_bands=2)
+    plan.set_radix_schedule(1, 0)
+    assert plan.info["radix_schedule_plane"] & 1
+    c = [fi.complex_gaussian((2, len(g0)), 98), fi.complex_gaussian((3, len(g1)), 99)]
+    c = [a.astype(np.complex64) for a in c]
+    x = torch.from_numpy(np.concatenate([a.reshape(-1) for a in c])).cuda()
+    vol = 160 ** 3
+    out = torch.empty(5 * vol, dtype=torch.complex64, device="cuda")
+    plan.execute(x, out)
+    torch.cuda.synchronize()
+    plan.check()
+    got = out.cpu().numpy().reshape(5, 160, 160, 160)
+    want = [oracle.g2r(g0, c[0][b].astype(np.complex128), n) for b in range(2)]
+    want += [oracle.g2r(g1, c[1][b].astype(np.complex128), n) for b in range(3)]
+    for b in range(5):
+        assert relerr(got[b], want[b]) <= 2e-6, b
+    ref = out.clone()
+    plan.inject(F.FFTB_INJECT_SKIP_FIRST_PREFETCH)
+    plan.execute(x, out)
+    torch.cuda.synchronize()
+    with pytest.raises(F.FFTBError) as ei:
+        plan.check()
+    assert ei.value.status == F.FFTB_ERR_DEVICE_TIMEOUT
+    plan.inject(0)
+    out.zero_()
+    plan.execute(x, out)
+    torch.cuda.synchronize()
+    plan.check()
+    assert torch.equal(out, ref)
