@@ -544,30 +544,50 @@ def run_ours(args):
             cube2 = None
             if w.direction == "roundtrip":
                 cube2 = torch.empty(p2.info["cube_elems"], dtype=cdt, device=dev)
-            for _ in range(2):
-                p2.execute(x2, o2, cube2)
-            evs2 = []
-            for _ in range(reps):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                p2.execute(x2, o2, cube2)
-                b.record(stream)
-                evs2.append((a, b))
-            torch.cuda.synchronize(dev)
-            p2.check()
-            ms2 = sum(a.elapsed_time(b) for a, b in evs2) / len(evs2)
+            def run_timed():
+                for _ in range(2):
+                    p2.execute(x2, o2, cube2)
+                evs2 = []
+                for _ in range(reps):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    p2.execute(x2, o2, cube2)
+                    b.record(stream)
+                    evs2.append((a, b))
+                torch.cuda.synchronize(dev)
+                p2.check()
+                return sum(a.elapsed_time(b) for a, b in evs2) / len(evs2)
+
+            def tc_stages():
+                return {"tcgen05_plane_stages": p2.info["tensor_core_planes"],
+                        "mma_sync_passes_mask_z1_plane2": p2.info["tensor_core_passes"]}
+
+            def errors(d):
+                if w.direction == "roundtrip":
+                    vol = float(np.prod(w.n))
+                    d["rel_l2_roundtrip"] = (torch.linalg.vector_norm(o2 - vol * x2) /
+                                             torch.linalg.vector_norm(vol * x2)).item()
+                if ref is not None:
+                    d["rel_l2_vs_fp64_gpu"] = rel_l2(o2, ref)
+
+            ms2 = run_timed()
             res = {"value": w.total_bands / (ms2 / 1e3), "ms_per_step": ms2, "ratio_vs_fp32": ms2 / ms}
+            errors(res)
             if prec == "mixed":
-                # which stages ran on the tensor cores (none where no length has a tensor-core pass)
-                res["tensor_core_stages"] = {"tcgen05_plane_stages": p2.info["tensor_core_planes"],
-                                             "mma_sync_passes_mask_z1_plane2": p2.info["tensor_core_passes"]}
-            if w.direction == "roundtrip":
-                vol = float(np.prod(w.n))
-                res["rel_l2_roundtrip"] = (torch.linalg.vector_norm(o2 - vol * x2) /
-                                           torch.linalg.vector_norm(vol * x2)).item()
-            if ref is not None:
-                res["rel_l2_vs_fp64_gpu"] = rel_l2(o2, ref)
+                # which stages ran on the tensor cores (none where no length has a tensor-core pass,
+                # or where the autotuner measured the FP32 kernels faster)
+                res["tensor_core_stages"] = tc_stages()
+                res["tensor_cores_available"] = bool(p2.info["tensor_cores_available"])
+                if p2.info["tensor_cores_available"]:
+                    # the setting the autotuner did not keep (default schedules), same inputs
+                    in_use = (p2.info["tensor_core_planes"] | p2.info["tensor_core_passes"]) != 0
+                    p2.set_tensor_cores(not in_use)
+                    ms_o = run_timed()
+                    other = {"tensor_cores": not in_use, "value": w.total_bands / (ms_o / 1e3),
+                             "ms_per_step": ms_o, "tensor_core_stages": tc_stages()}
+                    errors(other)
+                    res["other_setting"] = other
             del x2, cube2, p2, vd2
             return res, o2
 

@@ -141,6 +141,8 @@ typedef struct {
                               y and x kernels with a slab buffer between y and x    */
   int32_t tensor_core_passes; /* MIXED_TC: stages whose radix-8 passes run on mma.sync
                               (bit 0 z, bit 1 plane); 0 where no stage has one      */
+  int32_t tensor_cores_available; /* MIXED_TC: 1 if the plan has tensor-core kernels for
+                              some stage (in use or not: fftb_plan_set_tensor_cores)  */
 } fftb_plan_info_t;
 
 /* Builds the spheres, stick/slab tables and twiddles on the host, uploads
@@ -197,11 +199,12 @@ fftb_status fftb_execute(fftb_plan plan, const void* in_dev, void* out_dev,
 /* As fftb_execute, but in_host / out_host are host buffers (pinned for
  * full-speed copies and for overlap). Copies the input to plan-owned device
  * staging, runs the transform, copies the result back and synchronises
- * `stream`. The bands go through in two pieces on three plan-owned
- * streams, so the copy in of one piece, the transform of the previous one
- * and the copy out of the one before that overlap (batch-fastest plans split
- * only at a k-point boundary, and a single k-point goes in one piece); the
- * call is ordered
+ * `stream`. The bands go through in pieces on three plan-owned streams, so
+ * the copy in of one piece, the transform of the previous one and the copy
+ * out of the one before that overlap: band-major plans cut the batch into
+ * about (bands x N2) / 8192 pieces, at least 2 and at most 16 (never more
+ * than the bands); batch-fastest plans split only at k-point boundaries, and
+ * a single k-point goes in one piece. The call is ordered
  * after earlier work on `stream` and returns when all of it is done. The
  * staging buffers and streams are created on the first call and kept with
  * the plan. For ROUNDTRIP cube_dev is a device cube batch (may be NULL:
@@ -305,6 +308,16 @@ fftb_status fftb_plan_set_scale(fftb_plan plan, double g2r, double r2g);
  * no grouped kernels. Results are identical either way. */
 fftb_status fftb_plan_set_band_groups(fftb_plan plan, int32_t enable);
 
+/* MIXED_TC plans: 1 (the default) runs the stages that have tensor-core
+ * kernels on them (tensor_core_planes, tensor_core_passes), 0 runs every
+ * stage on the FP32 kernels, with their radix schedules and prefetching
+ * (FP32 arithmetic also meets the MIXED_TC error bound, rel. L2 <= 1e-5).
+ * fftb_plan_autotune times both and keeps the faster. Resets the radix
+ * schedules to the defaults and the persistent CTAs to one full wave. A no-op
+ * where no stage has tensor-core kernels (tensor_cores_available = 0).
+ * Errors: UNSUPPORTED for FP32 and FP64 plans. */
+fftb_status fftb_plan_set_tensor_cores(fftb_plan plan, int32_t enable);
+
 /* Device status. Every wait of a plane kernel on an asynchronous copy gives
  * up after one second; the CTA then lets its copies in flight land, leaves,
  * and sets the plan's status word (mapped host memory), so the context stays
@@ -319,8 +332,9 @@ fftb_status fftb_plan_check(fftb_plan plan);
 
 /* Test hook for the bounded waits: with FFTB_INJECT_SKIP_FIRST_PREFETCH the
  * first prefetch of CTA 0 (warp 0 in r->G) is not issued in each prefetching
- * plane launch (also in the r->G launches of the 160-point two-pass schedule,
- * whose cube rows arrive by bulk copies), so its wait runs out (about one
+ * plane launch (also in the launches of the 160-point two-pass schedule, whose
+ * cube rows (r->G) and stick values (G->r) arrive by bulk copies in each
+ * warp's exchange rows: warp 0's first copy), so its wait runs out (about one
  * second, twice: the wait, then the exit's wait for copies in flight) and the
  * status word is set. 0 turns injection off. Unknown bits:
  * FFTB_ERR_INVALID_ARG. */

@@ -159,6 +159,11 @@ struct fftb_plan_s {
   void* d_tc5w = nullptr;
   int tc5_ctas = 0;
   int stick_prec = P_F32;
+  // MIXED_TC: the tensor-core kernels the plan was built with (tc5, plane
+  // kernel precision, z-stage precision), and whether they are in use; off,
+  // the plan runs the FP32 kernels (fftb_plan_set_tensor_cores, autotuner)
+  bool tc_avail = false, tc_on = false, tc5_ok = false;
+  int plane_tc = P_F32, stick_tc = P_F32;
   // generic-extent path (extents outside the compiled list, N0 != N1): one
   // runtime-length kernel per axis and a slab buffer S between y and x
   bool generic = false;
@@ -237,6 +242,36 @@ fftb_status configure_planes(fftb_plan_s* p) {
   }
   if (!p->alt_plane_ok) p->sched_plane = 0;
   for (int i = 0; i < 3; ++i) p->plane_ctas[i] = p->sms * occ_in_use(p, i);
+  return FFTB_OK;
+}
+
+// MIXED_TC plans: puts the tensor-core kernels the plan was built with (on)
+// or the FP32 kernels, with their alternative schedules and prefetching
+// (off), on the plan. Default radix schedules, one full wave of plane CTAs.
+fftb_status set_tc(fftb_plan_s* p, bool on) {
+  if (!p->tc_avail || on == p->tc_on) return FFTB_OK;
+  const bool z_wave = p->tiles == stick_wave(p);
+  p->tc_on = on;
+  p->tc5 = on && p->tc5_ok;
+  p->prec_kernel = on ? p->plane_tc : P_F32;
+  p->stick_prec = on ? p->stick_tc : P_F32;
+  p->sched_plane = 0;
+  p->sched_stick = 0;
+  fftb_status st = configure_planes(p);
+  if (st != FFTB_OK) return st;
+  p->stick_occ = std::max(1, stick_occupancy(p->stick_prec, p->n[2]));
+  p->alt_stick_ok = false;
+  if (p->stick_prec == P_F32 && alt_schedule(p->n[2])) {
+    cudaError_t e = prepare_alt(0, p->n[2], 0, 1);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    p->alt_stick_occ = stick_alt_occupancy(p->n[2]);
+    p->alt_stick_ok = p->alt_stick_occ >= 1;
+  }
+  if (z_wave) p->tiles = stick_wave(p);
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);  // recorded with the other kernels
+    p->gexec = nullptr;
+  }
   return FFTB_OK;
 }
 
@@ -587,6 +622,11 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
     p->alt_stick_ok = p->alt_stick_occ >= 1;
   }
   p->tiles = sms * p->stick_occ;  // z stage: one wave of persistent CTAs (the autotuner may pick one warp per task pair)
+  p->tc5_ok = p->tc5;
+  p->plane_tc = p->prec_kernel;
+  p->stick_tc = p->stick_prec;
+  p->tc_avail = p->tc5 || p->prec_kernel == P_TC || p->stick_prec == P_TC;
+  p->tc_on = p->tc_avail;
   }  // !generic
   e = cudaHostAlloc(reinterpret_cast<void**>(&p->h_status), sizeof(int32_t), cudaHostAllocMapped);
   if (e != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaHostAlloc status word failed"); }
@@ -734,6 +774,7 @@ FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) 
   info->graph_launches = p->graph_launches;
   info->generic_path = p->generic ? 1 : 0;
   info->tensor_core_passes = (p->stick_prec == P_TC ? 1 : 0) | (p->prec_kernel == P_TC && !p->tc5 ? 2 : 0);
+  info->tensor_cores_available = p->tc_avail ? 1 : 0;
   return FFTB_OK;
 }
 
@@ -1255,6 +1296,12 @@ FFTB_EXPORT fftb_status fftb_plan_set_band_groups(fftb_plan p, int32_t enable) {
   return FFTB_OK;
 }
 
+FFTB_EXPORT fftb_status fftb_plan_set_tensor_cores(fftb_plan p, int32_t enable) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (p->prec != FFTB_MIXED_TC) return fail(FFTB_ERR_UNSUPPORTED, "tensor-core stages exist in MIXED_TC plans only");
+  return set_tc(p, enable != 0);
+}
+
 FFTB_EXPORT fftb_status fftb_plan_inject(fftb_plan p, int32_t flags) {
   if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
   if (flags & ~FFTB_INJECT_SKIP_FIRST_PREFETCH) return fail(FFTB_ERR_INVALID_ARG, "unknown injection flag");
@@ -1424,6 +1471,7 @@ struct TuneChoice {
   int sched_plane = 0, sched_stick = 0;  // radix schedule variants
   int pdl = 1;                           // programmatic dependent launch
   int bg = 0;                            // band group of the plane stages (batch-fastest)
+  int tc = 0;                            // MIXED_TC: tensor-core kernels in use
 };
 
 TuneChoice current_choice(const fftb_plan_s* p) {
@@ -1436,6 +1484,7 @@ TuneChoice current_choice(const fftb_plan_s* p) {
   c.sched_stick = p->sched_stick;
   c.pdl = p->pdl ? 1 : 0;
   c.bg = p->bg;
+  c.tc = p->tc_on ? 1 : 0;
   for (int i = 0; i < 3; ++i) c.ctas[i] = p->plane_ctas[i];
   return c;
 }
@@ -1451,10 +1500,10 @@ bool tune_cache_lookup(const std::string& key, TuneChoice* out) {
     std::string k;
     TuneChoice c;
     if ((ls >> k >> c.chunk >> c.ctas[0] >> c.ctas[1] >> c.ctas[2] >> c.tiles >> c.level >> c.a_bufs >>
-         c.sched_plane >> c.sched_stick >> c.pdl >> c.bg) &&
+         c.sched_plane >> c.sched_stick >> c.pdl >> c.bg >> c.tc) &&
         k == key && c.chunk >= 1 && c.level >= 0 && c.level <= 2 && (c.a_bufs == 1 || c.a_bufs == 2) &&
         c.sched_plane >= 0 && c.sched_plane <= 7 && (c.sched_stick == 0 || c.sched_stick == 1) &&
-        (c.pdl == 0 || c.pdl == 1) && c.bg >= 0 && c.bg <= 4) {
+        (c.pdl == 0 || c.pdl == 1) && c.bg >= 0 && c.bg <= 4 && (c.tc == 0 || c.tc == 1)) {
       *out = c;
       found = true;  // the last entry wins
     }
@@ -1468,7 +1517,7 @@ void tune_cache_store(const std::string& key, const TuneChoice& c) {
   std::ofstream f(path, std::ios::app);
   f << key << " " << c.chunk << " " << c.ctas[0] << " " << c.ctas[1] << " " << c.ctas[2] << " " << c.tiles << " "
     << c.level << " " << c.a_bufs << " " << c.sched_plane << " " << c.sched_stick << " " << c.pdl << " " << c.bg
-    << "\n";
+    << " " << c.tc << "\n";
 }
 
 fftb_status resize_T(fftb_plan_s* p, int chunk) {
@@ -1485,6 +1534,13 @@ fftb_status resize_T(fftb_plan_s* p, int chunk) {
 // Puts a candidate on the plan (slab buffers first: they change the
 // resident CTAs per SM).
 fftb_status apply_choice(fftb_plan_s* p, const TuneChoice& c) {
+  if (p->tc_avail && (c.tc != 0) != p->tc_on) {
+    fftb_status st = set_tc(p, c.tc != 0);
+    if (st != FFTB_OK) {
+      set_tc(p, !(c.tc != 0));
+      return st;
+    }
+  }
   if (c.a_bufs != p->a_bufs) {
     const int old = p->a_bufs;
     p->a_bufs = c.a_bufs;
@@ -1616,18 +1672,32 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
   // stage 1: kernel variant (slab-plane buffers, prefetch level), each with a
   // full wave of persistent plane CTAs, at the plan's chunk and at the
   // largest chunk (a variant with fewer resident CTAs can need long launches)
+  // (MIXED_TC: first with the tensor-core kernels, then with the FP32 ones)
+  std::vector<int> tcs = {saved.tc};
+  if (p->tc_avail) tcs.push_back(1 - saved.tc);
+  std::vector<int> bgs = {0};
+  if (p->bg_size) bgs.push_back(p->bg_size);
+  std::vector<int> chunks1 = {saved.chunk};
+  if (max_chunk != saved.chunk) chunks1.push_back(max_chunk);
+  for (int tcv : tcs) {
+  if (st != FFTB_OK) break;
+  if (p->tc_avail) {
+    TuneChoice c = saved;
+    c.tc = tcv;
+    c.sched_plane = c.sched_stick = 0;
+    c.tiles = c.tiles ? -1 : 0;
+    c.ctas[0] = c.ctas[1] = c.ctas[2] = -1;
+    st = apply_choice(p, c);
+    if (st != FFTB_OK) break;
+  }
   std::vector<int> nbufs = {saved.a_bufs};
   {
     const int other = 3 - saved.a_bufs;
     if (p->a_glob || plane_smem(p->prec_kernel, p->n[0], p->n[1], p->xmax, other) <= kSmemLimit)
       nbufs.push_back(other);
   }
-  std::vector<int> plane_scheds = {0}, stick_scheds = {0};
+  std::vector<int> stick_scheds = {0};
   if (p->alt_stick_ok) stick_scheds.push_back(1);
-  std::vector<int> bgs = {0};
-  if (p->bg_size) bgs.push_back(p->bg_size);
-  std::vector<int> chunks1 = {saved.chunk};
-  if (max_chunk != saved.chunk) chunks1.push_back(max_chunk);
   for (int ck : chunks1)
   for (int bgv : bgs)
   for (int nb : nbufs) {
@@ -1642,6 +1712,7 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
       for (int sp : sps) {
         for (int lv : {saved.level, 0, 1, 2}) {
           TuneChoice c = saved;
+          c.tc = tcv;
           c.a_bufs = nb;
           c.level = lv;
           c.sched_plane = sp;
@@ -1666,6 +1737,7 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
       if (st != FFTB_OK) break;
     }
   }
+  }  // tcv
   // stage 2: chunk, persistent plane CTAs per SM (0: one CTA per plane) and
   // z-stage CTAs for the chosen variant
   const TuneChoice variant = best_c;

@@ -188,3 +188,74 @@ def test_mixed_bench_workloads_in_their_timed_configuration(F, name, tmp_path, m
         assert relerr(got, oracle.apply_potential(g, c, v, w.n)) <= TOL
     del cube, out, x, plan
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n,r,direction", [((128, 128, 128), 32.0, "apply"), ((64, 64, 64), 16.0, "roundtrip")])
+def test_mixed_tensor_cores_on_and_off(F, n, r, direction, tmp_path, monkeypatch):
+    """MIXED_TC plans that have tensor-core kernels (mma.sync radix-8 passes
+    at 128, tcgen05 plane products at 64): each setting of
+    fftb_plan_set_tensor_cores against the oracle and in the plan's info, then
+    the autotuner's choice between them, recorded in its cache line."""
+    import torch
+    monkeypatch.setenv("FFTB_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    bands = 3
+    plan = F.Plan(n, direction, "mixed", radius=r, bands=[bands])
+    assert plan.info["tensor_cores_available"] == 1
+    used = plan.info["tensor_core_passes"] | plan.info["tensor_core_planes"]
+    assert used != 0
+    g = plan.sphere(0)
+    c = fi.complex_gaussian((bands, len(g)), 61).astype(np.complex64)
+    c64 = c.astype(np.complex128)
+    if direction == "apply":
+        v = fi.gaussian_potential(n, 16, 4.0, seed=62).astype(np.float32)
+        plan.set_potential(torch.from_numpy(v).cuda())
+        want = oracle.apply_potential(g, c64, v.astype(np.float64), n)
+    else:
+        want = np.prod(n) * c64
+        cube0 = oracle.g2r(g, c64[0], n)
+    x = torch.from_numpy(c.reshape(-1)).cuda()
+
+    def run():
+        out = torch.empty_like(x)
+        cube = None
+        if direction == "roundtrip":
+            cube = torch.empty(plan.info["cube_elems"], dtype=torch.complex64, device="cuda")
+        plan.execute(x, out, cube)
+        torch.cuda.synchronize()
+        plan.check()
+        got = out.cpu().numpy().reshape(bands, -1)
+        for b in range(bands):
+            assert relerr(got[b], want[b]) <= TOL, b
+        if cube is not None:
+            R0 = cube[:np.prod(n)].view(n[2], n[1], n[0]).cpu().numpy().astype(np.complex128)
+            assert relerr(R0, cube0) <= TOL
+
+    run()
+    plan.set_tensor_cores(False)
+    assert plan.info["tensor_core_passes"] == 0 and plan.info["tensor_core_planes"] == 0
+    assert plan.info["tensor_cores_available"] == 1
+    run()
+    plan.set_tensor_cores(True)
+    assert plan.info["tensor_core_passes"] | plan.info["tensor_core_planes"] == used
+    run()
+    plan.autotune(2)
+    line = (tmp_path / "tune.txt").read_text().strip().split()
+    assert line[-1] in ("0", "1")
+    assert (line[-1] == "1") == ((plan.info["tensor_core_passes"] | plan.info["tensor_core_planes"]) != 0)
+    run()
+
+
+def test_mixed_tensor_core_switch_where_none_exist(F):
+    """A MIXED_TC plan with no tensor-core stage (160 has no radix-8 pass):
+    the switch is a no-op; FP32 and FP64 plans reject it."""
+    p = F.Plan((160, 160, 160), "g2r", "mixed", radius=40.0, bands=[1])
+    assert p.info["tensor_cores_available"] == 0 and p.info["tensor_core_passes"] == 0
+    p.set_tensor_cores(True)
+    p.set_tensor_cores(False)
+    assert p.info["tensor_core_passes"] == 0 and p.info["tensor_core_planes"] == 0
+    for prec in ("fp32", "fp64"):
+        q = F.Plan((64, 64, 64), "g2r", prec, radius=16.0, bands=[1])
+        assert q.info["tensor_cores_available"] == 0
+        with pytest.raises(F.FFTBError) as e:
+            q.set_tensor_cores(True)
+        assert e.value.status == F.FFTB_ERR_UNSUPPORTED

@@ -98,9 +98,11 @@ def test_schedule_errors_and_autotune(F, tmp_path, monkeypatch):
     torch.cuda.synchronize()
     assert relerr(out.cpu().numpy(), 128 ** 3 * c.reshape(-1).astype(np.complex128)) <= 2e-6
     line = (tmp_path / "tune.txt").read_text().strip().split()
-    assert 0 <= int(line[-4]) <= 3 and line[-3] in ("0", "1") and line[-2] in ("0", "1") and line[-1] == "0"
-    assert int(line[-4]) == plan.info["radix_schedule_plane"] and int(line[-3]) == plan.info["radix_schedule_stick"]
-    assert int(line[-2]) == plan.info["dependent_launch"]
+    # ... plane schedule mask, stick schedule, dependent launch, band group, tensor cores
+    assert 0 <= int(line[-5]) <= 3 and line[-4] in ("0", "1") and line[-3] in ("0", "1") and line[-2] == "0"
+    assert line[-1] == "0"  # an FP32 plan has no tensor-core kernels
+    assert int(line[-5]) == plan.info["radix_schedule_plane"] and int(line[-4]) == plan.info["radix_schedule_stick"]
+    assert int(line[-3]) == plan.info["dependent_launch"]
 
 
 def test_160_two_pass_rows_by_bulk_copies(F):
