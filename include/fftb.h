@@ -143,6 +143,13 @@ typedef struct {
                               (bit 0 z, bit 1 plane); 0 where no stage has one      */
   int32_t tensor_cores_available; /* MIXED_TC: 1 if the plan has tensor-core kernels for
                               some stage (in use or not: fftb_plan_set_tensor_cores)  */
+  int32_t plane_clusters;     /* plane stages on two-CTA clusters, each CTA holding half
+                              of the slab plane in shared memory (bit 0 G->r, bit 1
+                              r->G, bit 2 apply; fftb_plan_set_plane_clusters, or the
+                              autotuner per stage); bit 3: the plan has those kernels
+                              (FP32, 256-point planes)                               */
+  /* slab_planes_global above is 1 while a stage the direction uses keeps its
+     slab planes in global memory. */
 } fftb_plan_info_t;
 
 /* Builds the spheres, stick/slab tables and twiddles on the host, uploads
@@ -307,6 +314,19 @@ fftb_status fftb_plan_set_scale(fftb_plan plan, double g2r, double r2g);
  * fftb_plan_autotune measures both): UNSUPPORTED to enable where the plan has
  * no grouped kernels. Results are identical either way. */
 fftb_status fftb_plan_set_band_groups(fftb_plan plan, int32_t enable);
+
+/* FP32 plans with 256-point planes (N0 == N1 = 256) whose half slab plane,
+ * 128 rows of the occupied x-slabs, fits in shared memory (up to about 150
+ * slabs): 1 runs the y and x stages on clusters of two CTAs, on two SMs,
+ * that share each (band, z) plane, each holding half of its rows and
+ * writing the other half's y outputs into its partner's shared memory
+ * (distributed shared memory, Sec. 3.1's transposes within a cluster); 0 the
+ * single-CTA kernels, whose 256-point slab planes live in global memory.
+ * Sets all three plane stages; fftb_plan_autotune times both kinds per
+ * stage. Results are the same to rounding. Resets the persistent plane CTAs
+ * to one full wave. Errors: UNSUPPORTED to enable where the plan has no
+ * cluster kernels. */
+fftb_status fftb_plan_set_plane_clusters(fftb_plan plan, int32_t enable);
 
 /* MIXED_TC plans: 1 (the default) runs the stages that have tensor-core
  * kernels on them (tensor_core_planes, tensor_core_passes), 0 runs every

@@ -164,6 +164,12 @@ struct fftb_plan_s {
   // the plan runs the FP32 kernels (fftb_plan_set_tensor_cores, autotuner)
   bool tc_avail = false, tc_on = false, tc5_ok = false;
   int plane_tc = P_F32, stick_tc = P_F32;
+  // FP32 256-point plane stages with the slab plane split over two-CTA
+  // clusters (distributed shared memory): available, the stages that use
+  // them (bit i for mode index i: G->r, r->G, apply), clusters resident
+  bool cl_ok = false;
+  int cl = 0;
+  int cl_count[3] = {0, 0, 0};
   // generic-extent path (extents outside the compiled list, N0 != N1): one
   // runtime-length kernel per axis and a slab buffer S between y and x
   bool generic = false;
@@ -186,6 +192,7 @@ namespace {
 // the plane stage of mode index i (G->r, r->G, apply) prefetches
 bool pf_active(const fftb_plan_s* p, int i) {
   if (p->bg && i < 2) return false;  // the grouped kernels do not prefetch
+  if ((p->cl >> i) & 1) return false;  // nor do the cluster kernels
   if (!p->pf_fit[i] || p->pf_level == 0 || ((p->sched_plane >> i) & 1)) return false;
   if (i == 1 && p->layout != 0) return false;  // bulk copies take whole band-major cube rows
   return p->pf_level == 2 || p->pf_occ[i] >= p->plane_occ[i];
@@ -193,8 +200,13 @@ bool pf_active(const fftb_plan_s* p, int i) {
 // resident plane CTAs per SM of the kernel mode index i uses
 int occ_in_use(const fftb_plan_s* p, int i) {
   if (p->bg && i < 2) return p->bg_occ[i];
+  if ((p->cl >> i) & 1) return 1;
   if ((p->sched_plane >> i) & 1) return p->alt_plane_occ[i];
   return pf_active(p, i) ? p->pf_occ[i] : p->plane_occ[i];
+}
+// CTAs of one full wave of the plane kernel mode index i uses
+int plane_wave(const fftb_plan_s* p, int i) {
+  return ((p->cl >> i) & 1) ? 2 * p->cl_count[i] : p->sms * occ_in_use(p, i);
 }
 // persistent z-stage CTAs of one full wave for the schedule in use
 int stick_wave(const fftb_plan_s* p) { return p->sms * (p->sched_stick ? p->alt_stick_occ : p->stick_occ); }
@@ -241,7 +253,21 @@ fftb_status configure_planes(fftb_plan_s* p) {
     p->alt_plane_ok = ok;
   }
   if (!p->alt_plane_ok) p->sched_plane = 0;
-  for (int i = 0; i < 3; ++i) p->plane_ctas[i] = p->sms * occ_in_use(p, i);
+  // FP32 planes split over two-CTA clusters, where the half plane fits
+  p->cl_ok = false;
+  const size_t cls = plane_cluster_smem(p->n[0], p->n[1], p->xmax);
+  if (p->prec_kernel == P_F32 && cls > 0 && cls <= kSmemLimit) {
+    e = prepare_plane_cluster(p->n[0], p->xmax);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    bool ok = true;
+    for (int i = 0; i < 3; ++i) {
+      p->cl_count[i] = plane_cluster_count(modes[i], p->n[0], p->xmax);
+      ok = ok && p->cl_count[i] >= 1;
+    }
+    p->cl_ok = ok;
+  }
+  if (!p->cl_ok) p->cl = 0;
+  for (int i = 0; i < 3; ++i) p->plane_ctas[i] = plane_wave(p, i);
   return FFTB_OK;
 }
 
@@ -666,7 +692,7 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
         p->bg_size = p->bg = bgs;
         p->bg_occ[0] = o0;
         p->bg_occ[1] = o1;
-        for (int i = 0; i < 2; ++i) p->plane_ctas[i] = p->sms * occ_in_use(p, i);
+        for (int i = 0; i < 2; ++i) p->plane_ctas[i] = plane_wave(p, i);
       }
     }
   }
@@ -736,13 +762,13 @@ static void debug_report(const fftb_plan_s* p, const char* when) {
   std::fprintf(stderr,
                "[fftb] %s: grid %dx%dx%d dir %d prec %d layout %d k-points %d bands %d | sticks %d slabs %d | "
                "chunk %d bands, %lld kernels/execute | z CTAs %d, plane CTAs %d | slab buffers %d%s | "
-               "prefetch mask %d | schedule plane %d stick %d | tcgen05 %d | band group %d | PDL %d | "
-               "scratch %lld bytes\n",
+               "prefetch mask %d | schedule plane %d stick %d | tcgen05 %d | mma.sync %d | clusters %d | "
+               "band group %d | PDL %d | scratch %lld bytes\n",
                when, p->n[0], p->n[1], p->n[2], (int)p->dir, (int)p->prec, p->layout, p->nk, p->total_bands,
                i.max_sticks, i.max_slabs, i.chunk_bands, (long long)i.kernels_per_execute, i.stick_ctas,
                i.plane_ctas, i.slab_buffers, i.slab_planes_global ? " (global)" : "", i.prefetch,
-               i.radix_schedule_plane, i.radix_schedule_stick, i.tensor_core_planes, i.plane_band_group,
-               i.dependent_launch, (long long)i.scratch_bytes);
+               i.radix_schedule_plane, i.radix_schedule_stick, i.tensor_core_planes, i.tensor_core_passes,
+               i.plane_clusters & 7, i.plane_band_group, i.dependent_launch, (long long)i.scratch_bytes);
 }
 
 FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) {
@@ -765,7 +791,9 @@ FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) 
   for (int i = 0; i < 3; ++i)
     if (pf_active(p, i)) info->prefetch |= 1 << i;
   info->slab_buffers = p->a_bufs;
-  info->slab_planes_global = p->a_glob ? 1 : 0;
+  const int used = p->dir == FFTB_G_TO_R ? 1 : p->dir == FFTB_R_TO_G ? 2 : p->dir == FFTB_APPLY_LOCAL ? 4 : 3;
+  info->slab_planes_global = p->a_glob && (p->cl & used) != used ? 1 : 0;
+  info->plane_clusters = p->cl | (p->cl_ok ? 8 : 0);
   info->tensor_core_planes = p->tc5 ? 3 : 0;
   info->radix_schedule_plane = p->sched_plane;
   info->radix_schedule_stick = p->sched_stick;
@@ -856,6 +884,7 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
       Lp.pf = pf_active(p, 0);
       if (p->bg) e = launch_plane_bg(M_G2R, Lp);
       else if (p->tc5) e = tc5_launch(M_G2R, Lp, p->tc5g[0], p->tc5_ctas);
+      else if (p->cl & 1) e = launch_plane_cluster(M_G2R, Lp);
       else if (p->sched_plane & 1) e = launch_plane_alt(M_G2R, Lp);
       else e = Lp.pf ? launch_plane_pf(M_G2R, Lp) : launch_plane(pk, M_G2R, Lp);
       break;
@@ -866,6 +895,7 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
       Lp.pf = pf_active(p, 1) && cube_in_16;
       if (p->bg) e = launch_plane_bg(M_R2G, Lp);
       else if (p->tc5 && cube_in_16) e = tc5_launch(M_R2G, Lp, p->tc5g[1], p->tc5_ctas);
+      else if (p->cl & 2) e = launch_plane_cluster(M_R2G, Lp);
       else if (p->sched_plane & 2) {
         Lp.pf = cube_in_16;  // the alternative kernel loads whole cube rows by bulk copies
         e = launch_plane_alt(M_R2G, Lp);
@@ -880,7 +910,8 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
       Launch Lp = L;
       Lp.plane_ctas = p->plane_ctas[2];
       Lp.pf = pf_active(p, 2);
-      if (p->sched_plane & 4) e = launch_plane_alt(M_APPLY, Lp);
+      if (p->cl & 4) e = launch_plane_cluster(M_APPLY, Lp);
+      else if (p->sched_plane & 4) e = launch_plane_alt(M_APPLY, Lp);
       else e = Lp.pf ? launch_plane_pf(M_APPLY, Lp) : launch_plane(pk, M_APPLY, Lp);
       break;
     }
@@ -1250,7 +1281,7 @@ FFTB_EXPORT fftb_status fftb_plan_set_radix_schedule(fftb_plan p, int32_t plane,
   p->sched_plane = plane ? 7 : 0;
   p->sched_stick = stick;
   if (stick_wave_before) p->tiles = stick_wave(p);
-  for (int i = 0; i < 3; ++i) p->plane_ctas[i] = p->sms * occ_in_use(p, i);
+  for (int i = 0; i < 3; ++i) p->plane_ctas[i] = plane_wave(p, i);
   if (p->gexec) {
     cudaGraphExecDestroy(p->gexec);
     p->gexec = nullptr;
@@ -1288,7 +1319,22 @@ FFTB_EXPORT fftb_status fftb_plan_set_band_groups(fftb_plan p, int32_t enable) {
   const int bg = enable ? p->bg_size : 0;
   if (bg == p->bg) return FFTB_OK;
   p->bg = bg;
-  for (int i = 0; i < 2; ++i) p->plane_ctas[i] = p->sms * occ_in_use(p, i);
+  for (int i = 0; i < 2; ++i) p->plane_ctas[i] = plane_wave(p, i);
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  return FFTB_OK;
+}
+
+FFTB_EXPORT fftb_status fftb_plan_set_plane_clusters(fftb_plan p, int32_t enable) {
+  if (!p) return fail(FFTB_ERR_INVALID_ARG, "NULL plan");
+  if (enable && !p->cl_ok)
+    return fail(FFTB_ERR_UNSUPPORTED, "no cluster plane kernels for this plan (FP32, 256-point planes, half plane fitting)");
+  const int cl = enable ? 7 : 0;
+  if (cl == p->cl) return FFTB_OK;
+  p->cl = cl;
+  for (int i = 0; i < 3; ++i) p->plane_ctas[i] = plane_wave(p, i);
   if (p->gexec) {
     cudaGraphExecDestroy(p->gexec);
     p->gexec = nullptr;
@@ -1472,6 +1518,7 @@ struct TuneChoice {
   int pdl = 1;                           // programmatic dependent launch
   int bg = 0;                            // band group of the plane stages (batch-fastest)
   int tc = 0;                            // MIXED_TC: tensor-core kernels in use
+  int cl = 0;                            // plane stages on two-CTA clusters
 };
 
 TuneChoice current_choice(const fftb_plan_s* p) {
@@ -1485,6 +1532,7 @@ TuneChoice current_choice(const fftb_plan_s* p) {
   c.pdl = p->pdl ? 1 : 0;
   c.bg = p->bg;
   c.tc = p->tc_on ? 1 : 0;
+  c.cl = p->cl;
   for (int i = 0; i < 3; ++i) c.ctas[i] = p->plane_ctas[i];
   return c;
 }
@@ -1500,10 +1548,11 @@ bool tune_cache_lookup(const std::string& key, TuneChoice* out) {
     std::string k;
     TuneChoice c;
     if ((ls >> k >> c.chunk >> c.ctas[0] >> c.ctas[1] >> c.ctas[2] >> c.tiles >> c.level >> c.a_bufs >>
-         c.sched_plane >> c.sched_stick >> c.pdl >> c.bg >> c.tc) &&
+         c.sched_plane >> c.sched_stick >> c.pdl >> c.bg >> c.tc >> c.cl) &&
         k == key && c.chunk >= 1 && c.level >= 0 && c.level <= 2 && (c.a_bufs == 1 || c.a_bufs == 2) &&
         c.sched_plane >= 0 && c.sched_plane <= 7 && (c.sched_stick == 0 || c.sched_stick == 1) &&
-        (c.pdl == 0 || c.pdl == 1) && c.bg >= 0 && c.bg <= 4 && (c.tc == 0 || c.tc == 1)) {
+        (c.pdl == 0 || c.pdl == 1) && c.bg >= 0 && c.bg <= 4 && (c.tc == 0 || c.tc == 1) &&
+        c.cl >= 0 && c.cl <= 7) {
       *out = c;
       found = true;  // the last entry wins
     }
@@ -1517,7 +1566,7 @@ void tune_cache_store(const std::string& key, const TuneChoice& c) {
   std::ofstream f(path, std::ios::app);
   f << key << " " << c.chunk << " " << c.ctas[0] << " " << c.ctas[1] << " " << c.ctas[2] << " " << c.tiles << " "
     << c.level << " " << c.a_bufs << " " << c.sched_plane << " " << c.sched_stick << " " << c.pdl << " " << c.bg
-    << " " << c.tc << "\n";
+    << " " << c.tc << " " << c.cl << "\n";
 }
 
 fftb_status resize_T(fftb_plan_s* p, int chunk) {
@@ -1555,12 +1604,13 @@ fftb_status apply_choice(fftb_plan_s* p, const TuneChoice& c) {
   if (st != FFTB_OK) return st;
   p->chunk = c.chunk;
   p->bg = (c.bg && p->bg_size) ? p->bg_size : 0;
+  p->cl = p->cl_ok ? c.cl : 0;
   p->pf_level = c.level;
   p->sched_plane = p->alt_plane_ok ? c.sched_plane : 0;
   p->sched_stick = (c.sched_stick && p->alt_stick_ok) ? 1 : 0;
   p->pdl = c.pdl != 0;
   p->tiles = c.tiles < 0 ? stick_wave(p) : c.tiles;
-  for (int i = 0; i < 3; ++i) p->plane_ctas[i] = c.ctas[i] >= 0 ? c.ctas[i] : p->sms * occ_in_use(p, i);
+  for (int i = 0; i < 3; ++i) p->plane_ctas[i] = c.ctas[i] >= 0 ? c.ctas[i] : plane_wave(p, i);
   return FFTB_OK;
 }
 
@@ -1710,9 +1760,12 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
       for (int m = 0; m <= 7; ++m)
         if ((m & ~used) == 0 && (m == 0 || p->alt_plane_ok)) sps.push_back(m);
       for (int sp : sps) {
-        for (int lv : {saved.level, 0, 1, 2}) {
+        for (int lv : {saved.level, 0, 1, 2})
+        for (int clv = 0; clv <= 7; ++clv) {
+          if ((clv & ~used) || (clv && !p->cl_ok)) continue;  // per stage the direction uses
           TuneChoice c = saved;
           c.tc = tcv;
+          c.cl = clv;
           c.a_bufs = nb;
           c.level = lv;
           c.sched_plane = sp;
@@ -1727,6 +1780,11 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
           int mask = (p->bg ? 64 | (p->sched_plane & 4) : p->sched_plane) << 3;
           for (int i = 0; i < 3; ++i)
             if (pf_active(p, i)) mask |= 1 << i;
+          if (p->cl) {  // the stages on the cluster kernels have no other variants
+            for (int i = 0; i < 3; ++i)
+              if ((p->cl >> i) & 1) mask &= ~((1 << i) | (8 << i));
+            mask |= p->cl << 10;
+          }
           if (std::find(masks.begin(), masks.end(), mask) != masks.end()) continue;
           masks.push_back(mask);
           st = trial(current_choice(p));
@@ -1752,7 +1810,8 @@ FFTB_EXPORT fftb_status fftb_plan_autotune(fftb_plan p, int32_t trials) {
     c.chunk = chunks[k / (2 * mults.size())];
     const int m = mults[(k / 2) % mults.size()];
     c.tiles = (k & 1) ? stick_wave(p) : 0;
-    for (int i = 0; i < 3; ++i) c.ctas[i] = m == 0 ? 0 : p->sms * std::min(m, occ_in_use(p, i));
+    for (int i = 0; i < 3; ++i)
+      c.ctas[i] = m == 0 ? 0 : ((p->cl >> i) & 1) ? plane_wave(p, i) : p->sms * std::min(m, occ_in_use(p, i));
     st = trial(c);
   }
   // stage 3: the best schedule with and without programmatic dependent launch

@@ -150,6 +150,15 @@ size_t plane_bg_smem(int n0, int n1, int xmax, int bg);
 cudaError_t prepare_plane_bg(int n, int xmax);
 int plane_bg_occupancy(int mode, int n, int xmax);
 cudaError_t launch_plane_bg(int mode, const Launch& L);
+// FP32 y/x stages with the slab plane split over a cluster of two CTAs
+// (k_cluster.cu; N0 == N1 = 256): shared memory per CTA of one mode, or the
+// largest over the modes (mode 0; 0: no such kernel), kernel attributes,
+// clusters resident at once, launch (L.plane_ctas CTAs, two per cluster; 0:
+// one cluster per plane).
+size_t plane_cluster_smem(int n0, int n1, int xmax, int mode = 0);
+cudaError_t prepare_plane_cluster(int n, int xmax);
+int plane_cluster_count(int mode, int n, int xmax);
+cudaError_t launch_plane_cluster(int mode, const Launch& L);
 // Multiplies n complex elements (csize bytes each) at data by s on L.stream
 // (k_scale.cu): the optional output normalisation.
 cudaError_t launch_scale(int csize, void* data, int64_t n, double s, const Launch& L, int sms);

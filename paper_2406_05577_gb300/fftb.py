@@ -70,6 +70,7 @@ class fftb_plan_info_t(ctypes.Structure):
         ("generic_path", ctypes.c_int32),
         ("tensor_core_passes", ctypes.c_int32),
         ("tensor_cores_available", ctypes.c_int32),
+        ("plane_clusters", ctypes.c_int32),
     ]
 
 
@@ -102,6 +103,7 @@ EXPORTS = {
     "fftb_plan_set_pdl": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fftb_plan_set_band_groups": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fftb_plan_set_tensor_cores": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "fftb_plan_set_plane_clusters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fftb_plan_set_scale": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]),
     "fftb_plan_inject": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fftb_sphere_enumerate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_double,
@@ -275,6 +277,10 @@ def fftb_plan_set_band_groups(plan, enable):
 
 def fftb_plan_set_tensor_cores(plan, enable):
     _check(lib().fftb_plan_set_tensor_cores(plan, 1 if enable else 0))
+
+
+def fftb_plan_set_plane_clusters(plan, enable):
+    _check(lib().fftb_plan_set_plane_clusters(plan, 1 if enable else 0))
 
 
 def fftb_plan_check(plan):
@@ -468,6 +474,10 @@ class Plan:
 
     def set_tensor_cores(self, enable=True):
         fftb_plan_set_tensor_cores(self.handle, enable)
+        self.info = fftb_plan_get_info(self.handle)
+
+    def set_plane_clusters(self, enable=True):
+        fftb_plan_set_plane_clusters(self.handle, enable)
         self.info = fftb_plan_get_info(self.handle)
 
     def check(self):

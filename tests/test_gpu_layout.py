@@ -235,7 +235,8 @@ def test_batch_fastest_autotune(F, tmp_path, monkeypatch):
     p = F.Plan(n, "roundtrip", "fp32", radius=r, kshift=ks, bands=bands, layout=1)
     p.autotune(2)
     line = (tmp_path / "tune.txt").read_text().strip().split()
-    assert int(line[-2]) == p.info["plane_band_group"] and line[-2] in ("0", "4") and line[-1] == "0"
+    assert len(line) == 14  # key, chunk, 3 plane CTAs, z CTAs, level, buffers, 2 schedules, pdl, group, tc, cl
+    assert int(line[-3]) == p.info["plane_band_group"] and line[-3] in ("0", "4") and line[-2:] == ["0", "0"]
     gs = [p.sphere(k) for k in range(2)]
     ngws = [len(g) for g in gs]
     parts = [fi.complex_gaussian((b, ng), 350 + k).astype(np.complex64) for k, (ng, b) in enumerate(zip(ngws, bands))]

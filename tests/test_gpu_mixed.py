@@ -240,8 +240,8 @@ def test_mixed_tensor_cores_on_and_off(F, n, r, direction, tmp_path, monkeypatch
     run()
     plan.autotune(2)
     line = (tmp_path / "tune.txt").read_text().strip().split()
-    assert line[-1] in ("0", "1")
-    assert (line[-1] == "1") == ((plan.info["tensor_core_passes"] | plan.info["tensor_core_planes"]) != 0)
+    assert len(line) == 14 and line[-2] in ("0", "1") and line[-1] == "0"  # ..., tensor cores, clusters
+    assert (line[-2] == "1") == ((plan.info["tensor_core_passes"] | plan.info["tensor_core_planes"]) != 0)
     run()
 
 

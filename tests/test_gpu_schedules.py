@@ -21,6 +21,16 @@ def F():
     return fftb
 
 
+TUNE_FIELDS = ("chunk", "ctas0", "ctas1", "ctas2", "tiles", "level", "a_bufs", "sched_plane", "sched_stick", "pdl",
+               "bg", "tc", "cl")
+
+
+def tune_fields(line):
+    """The fields of one tune-cache line (key, then the choice)."""
+    assert len(line) == 1 + len(TUNE_FIELDS)
+    return dict(zip(TUNE_FIELDS, (int(v) for v in line[1:])))
+
+
 def relerr(a, b):
     a = np.asarray(a).ravel()
     b = np.asarray(b).ravel()
@@ -98,11 +108,11 @@ def test_schedule_errors_and_autotune(F, tmp_path, monkeypatch):
     torch.cuda.synchronize()
     assert relerr(out.cpu().numpy(), 128 ** 3 * c.reshape(-1).astype(np.complex128)) <= 2e-6
     line = (tmp_path / "tune.txt").read_text().strip().split()
-    # ... plane schedule mask, stick schedule, dependent launch, band group, tensor cores
-    assert 0 <= int(line[-5]) <= 3 and line[-4] in ("0", "1") and line[-3] in ("0", "1") and line[-2] == "0"
-    assert line[-1] == "0"  # an FP32 plan has no tensor-core kernels
-    assert int(line[-5]) == plan.info["radix_schedule_plane"] and int(line[-4]) == plan.info["radix_schedule_stick"]
-    assert int(line[-3]) == plan.info["dependent_launch"]
+    f = tune_fields(line)
+    assert 0 <= f["sched_plane"] <= 3 and f["sched_stick"] in (0, 1) and f["pdl"] in (0, 1) and f["bg"] == 0
+    assert f["tc"] == 0 and f["cl"] == 0  # an FP32 128-point plan has neither tensor-core nor cluster kernels
+    assert f["sched_plane"] == plan.info["radix_schedule_plane"] and f["sched_stick"] == plan.info["radix_schedule_stick"]
+    assert f["pdl"] == plan.info["dependent_launch"]
 
 
 def test_160_two_pass_rows_by_bulk_copies(F):
