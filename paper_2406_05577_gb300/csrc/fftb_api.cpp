@@ -206,7 +206,7 @@ int occ_in_use(const fftb_plan_s* p, int i) {
 }
 // CTAs of one full wave of the plane kernel mode index i uses
 int plane_wave(const fftb_plan_s* p, int i) {
-  return ((p->cl >> i) & 1) ? 2 * p->cl_count[i] : p->sms * occ_in_use(p, i);
+  return ((p->cl >> i) & 1) ? plane_cluster_size() * p->cl_count[i] : p->sms * occ_in_use(p, i);
 }
 // persistent z-stage CTAs of one full wave for the schedule in use
 int stick_wave(const fftb_plan_s* p) { return p->sms * (p->sched_stick ? p->alt_stick_occ : p->stick_occ); }

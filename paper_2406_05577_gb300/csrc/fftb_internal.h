@@ -158,6 +158,7 @@ cudaError_t launch_plane_bg(int mode, const Launch& L);
 size_t plane_cluster_smem(int n0, int n1, int xmax, int mode = 0);
 cudaError_t prepare_plane_cluster(int n, int xmax);
 int plane_cluster_count(int mode, int n, int xmax);
+int plane_cluster_size();
 cudaError_t launch_plane_cluster(int mode, const Launch& L);
 // Multiplies n complex elements (csize bytes each) at data by s on L.stream
 // (k_scale.cu): the optional output normalisation.

@@ -4,8 +4,9 @@
 // A 256 x X slab plane (X up to about 150 occupied x-slabs) does not fit in
 // one CTA's shared memory; the single-CTA kernels then keep it in a per-CTA
 // block of global memory, whose L2 misses add DRAM traffic beyond the cube.
-// Here the two CTAs of a cluster (two SMs) work on the same (band, z) plane
-// and each holds half of its rows: rank r holds y in [r N/2, r N/2 + N/2).
+// Here the CTAs of a cluster (two, on two SMs) work on the same (band, z)
+// plane and each holds part of its rows: rank r holds y in [r H, r H + H),
+// H = N / (CTAs per cluster).
 //   y phase: the y lines (occupied columns) are dealt over the warps of both
 //            CTAs; a line's outputs go to the rank that holds their row, into
 //            the partner's shared memory for the other half (st.shared::cluster).
@@ -31,7 +32,17 @@
 namespace fftb {
 namespace {
 
-constexpr int CL_NW = 16;  // warps per CTA (one CTA per SM)
+// CTAs per cluster and warps per CTA (16 warps: one CTA per SM). Clusters
+// of four CTAs of 8 warps (two CTAs per SM, a quarter plane each) measured
+// slower in every direction; both build with -DFFTB_CL_CS / -DFFTB_CL_NW.
+#ifndef FFTB_CL_CS
+#define FFTB_CL_CS 2
+#endif
+#ifndef FFTB_CL_NW
+#define FFTB_CL_NW 16
+#endif
+constexpr int CL_CS = FFTB_CL_CS, CL_NW = FFTB_CL_NW;
+static_assert(CL_CS == 2 || CL_CS == 4, "clusters of two or four CTAs");
 
 __device__ __forceinline__ uint32_t cl_rank() {
   uint32_t r;
@@ -67,15 +78,15 @@ __device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arri
 __device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
 
 template <int N> __host__ __device__ constexpr int cl_scratch() { return (32 / Line<N>::G) * Line<N>::PITCH; }
-// r -> G: the first column of rank 1 (rank 0 takes the first half of the y
-// tasks, rounded up), for x occupied columns
+// r -> G: the columns of each rank (rank q takes y tasks [q t, q t + t),
+// t = the y tasks of x occupied columns over the ranks, rounded up)
 template <int N> __host__ __device__ constexpr int cl_col_split(int x) {
-  return (((x + 32 / Line<N>::G - 1) / (32 / Line<N>::G) + 1) / 2) * (32 / Line<N>::G);
+  return (((x + 32 / Line<N>::G - 1) / (32 / Line<N>::G) + CL_CS - 1) / CL_CS) * (32 / Line<N>::G);
 }
-// elements of one CTA's half plane: rows [r N/2, r N/2 + N/2) of every
-// column, or (r -> G) every row of its columns
+// elements of one CTA's part of the plane: rows [r N/CS, (r + 1) N/CS) of
+// every column, or (r -> G) every row of its columns
 template <int N> __host__ __device__ constexpr int cl_half(int mode, int xmax) {
-  return mode == M_R2G ? N * a_pitch(cl_col_split<N>(xmax)) : (N / 2) * a_pitch(xmax);
+  return mode == M_R2G ? N * a_pitch(cl_col_split<N>(xmax)) : (N / CL_CS) * a_pitch(xmax);
 }
 // shared memory: half slab plane, warp scratch rows, twiddles
 template <int N> size_t cl_smem_c(int mode, int xmax) {
@@ -83,10 +94,10 @@ template <int N> size_t cl_smem_c(int mode, int xmax) {
 }
 
 template <int N, int MODE>
-__global__ void __launch_bounds__(CL_NW * 32, 1) k_plane_cl(const Launch L) {
+__global__ void __launch_bounds__(CL_NW * 32, 16 / CL_NW) k_plane_cl(const Launch L) {
   using C = float2;
   using LN = Line<N>;
-  constexpr int NW = CL_NW, NT = NW * 32, H = N / 2;
+  constexpr int NW = CL_NW, NT = NW * 32, CS = CL_CS, H = N / CS;
   constexpr int W = 32 / LN::G, E = LN::E, SCR = cl_scratch<N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
 
@@ -99,7 +110,12 @@ __global__ void __launch_bounds__(CL_NW * 32, 1) k_plane_cl(const Launch L) {
   C* scr = A + abuf + warp * SCR;
   C* tw = A + abuf + NW * SCR;
   C* row = scr + li * LN::PITCH;
-  const uint32_t a_peer = cl_map(smem_u32(A), rank ^ 1u);
+  const uint32_t a_own = smem_u32(A);
+  const uint32_t a_pair = cl_map(a_own, rank ^ 1u);  // the partner's (clusters of two)
+  // shared::cluster address of element o of rank own's part
+  auto a_addr = [&](uint32_t own, int o) {
+    return (CS == 2 ? a_pair : cl_map(a_own, own)) + (uint32_t)o * (uint32_t)sizeof(C);
+  };
   {
     const C* t0 = static_cast<const C*>(L.g.tw0);  // N0 == N1: one table serves y and x
     for (int m = threadIdx.x; m < N; m += NT) tw[m] = t0[m];
@@ -114,25 +130,23 @@ __global__ void __launch_bounds__(CL_NW * 32, 1) k_plane_cl(const Launch L) {
   tc.load(g, tw);
   auto ysigned = [](int y) { return y < N - N / 2 ? y : y - N; };
 
-  // element (y, c) of the plane: in this CTA's half, or the partner's
+  // element (y, c) of the plane: in this CTA's rows, or in those of rank y / H
   auto a_put = [&](int y, int c, int XP, C v) {
-    const int local = y - H * (int)rank;
-    if ((unsigned)local < (unsigned)H) {
-      if (FFTB_IN(local * XP + c, abuf, L.status)) A[local * XP + c] = v;
-    } else {
-      const int o = (y - H * (int)(rank ^ 1u)) * XP + c;
-      if (FFTB_IN(o, abuf, L.status)) cl_st(a_peer + (uint32_t)o * (uint32_t)sizeof(C), v);
-    }
+    const uint32_t own = (uint32_t)(y / H);
+    const int o = (y - (int)own * H) * XP + c;
+    if (!FFTB_IN(o, abuf, L.status)) return;
+    if (own == rank) A[o] = v;
+    else cl_st(a_addr(own, o), v);
   };
   auto a_get = [&](int y, int c, int XP) -> C {
-    const int local = y - H * (int)rank;
-    if ((unsigned)local < (unsigned)H) return FFTB_IN(local * XP + c, abuf, L.status) ? A[local * XP + c] : czero<C>();
-    const int o = (y - H * (int)(rank ^ 1u)) * XP + c;
-    return FFTB_IN(o, abuf, L.status) ? cl_ld(a_peer + (uint32_t)o * (uint32_t)sizeof(C)) : czero<C>();
+    const uint32_t own = (uint32_t)(y / H);
+    const int o = (y - (int)own * H) * XP + c;
+    if (!FFTB_IN(o, abuf, L.status)) return czero<C>();
+    return own == rank ? A[o] : cl_ld(a_addr(own, o));
   };
 
   const int nplanes = L.nb * n2;
-  const int cw = (int)rank * NW + warp;  // this warp among the cluster's 2 NW
+  const int cw = (int)rank * NW + warp;  // this warp among the cluster's CS NW
   bool pending = false;                   // arrived for the halves' release, not yet waited
   auto a_acquire = [&]() {                // before this thread's first slab-plane write of a plane
     if (pending) {
@@ -150,7 +164,7 @@ __global__ void __launch_bounds__(CL_NW * 32, 1) k_plane_cl(const Launch L) {
     const KInfo ki = bi.ki;
     const int X = ki.X;
     const int cst = ki.bstride;
-    const int cs = cl_col_split<N>(X);  // r -> G: first column of rank 1
+    const int cs = cl_col_split<N>(X);  // r -> G: columns of each rank
     const int XP = MODE == M_R2G ? a_pitch(cs) : a_pitch(X);
     const bool allx = X >= N;
     if (ki.xmap_base != cur_k) {
@@ -183,7 +197,7 @@ __global__ void __launch_bounds__(CL_NW * 32, 1) k_plane_cl(const Launch L) {
 
     if constexpr (MODE == M_G2R || MODE == M_APPLY) {
 #pragma unroll 1
-      for (int t = cw; t < ty; t += 2 * NW) {
+      for (int t = cw; t < ty; t += CS * NW) {
         const int c0 = t * W, nl = min(W, X - c0);
         C v[E];
         const int col = c0 + (li < nl ? li : 0);
@@ -291,11 +305,13 @@ __global__ void __launch_bounds__(CL_NW * 32, 1) k_plane_cl(const Launch L) {
         for (int q = 0; q < E; ++q) {
           const int xi = xout.get(q);
           if (allx || xi != 255) {
-            const uint32_t own = xi >= cs ? 1u : 0u;  // the rank that holds column xi
+            uint32_t own = 0;  // the rank that holds column xi
+#pragma unroll
+            for (int k = 1; k < CS; ++k) own += xi >= k * cs ? 1u : 0u;
             const int o = y * XP + xi - (int)own * cs;
             if (FFTB_IN(o, abuf, L.status)) {
               if (own == rank) A[o] = v[q];
-              else cl_st(a_peer + (uint32_t)o * (uint32_t)sizeof(C), v[q]);
+              else cl_st(a_addr(own, o), v[q]);
             }
           }
         }
@@ -307,10 +323,10 @@ __global__ void __launch_bounds__(CL_NW * 32, 1) k_plane_cl(const Launch L) {
       cl_arrive();
       cl_wait();
       // r -> G: this rank's y tasks, its own columns; apply: tasks over the cluster
-      const int th = cs / W;  // y tasks of rank 0 (r -> G)
+      const int th = cs / W;  // y tasks of each rank (r -> G)
       const int t_first = MODE == M_R2G ? (int)rank * th + warp : cw;
-      const int t_end = MODE == M_R2G ? (rank ? ty : min(th, ty)) : ty;
-      const int t_step = MODE == M_R2G ? NW : 2 * NW;
+      const int t_end = MODE == M_R2G ? min((int)rank * th + th, ty) : ty;
+      const int t_step = MODE == M_R2G ? NW : CS * NW;
 #pragma unroll 1
       for (int t = t_first; t < t_end; t += t_step) {
         const int c0 = t * W, nl = min(W, X - c0);
@@ -399,18 +415,19 @@ cudaError_t prepare_plane_cluster(int n, int xmax) {
   return cudaSuccess;
 }
 
-// clusters of two CTAs that can be resident at once (0: none)
+// clusters that can be resident at once (0: none), and their CTAs
+int plane_cluster_size() { return CL_CS; }
 int plane_cluster_count(int mode, int n, int xmax) {
   const size_t s = plane_cluster_smem(n, n, xmax, mode);
   const void* fn = mode == M_G2R ? cl_fn<M_G2R>(n) : mode == M_R2G ? cl_fn<M_R2G>(n) : cl_fn<M_APPLY>(n);
   if (s == 0 || !fn) return 0;
   cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(2, 1, 1);
+  cfg.gridDim = dim3(CL_CS, 1, 1);
   cfg.blockDim = dim3(CL_NW * 32, 1, 1);
   cfg.dynamicSmemBytes = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.x = CL_CS;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
@@ -425,15 +442,15 @@ cudaError_t launch_plane_cluster(int mode, const Launch& L) {
   const size_t s = plane_cluster_smem(n, n, L.g.xmax, mode);
   if (s == 0 || L.g.n1 != n) return cudaErrorInvalidValue;
   const int nplanes = L.nb * L.g.n2;
-  const int ncl = L.plane_ctas > 0 ? std::max(1, std::min(L.plane_ctas / 2, nplanes)) : nplanes;
+  const int ncl = L.plane_ctas > 0 ? std::max(1, std::min(L.plane_ctas / CL_CS, nplanes)) : nplanes;
   cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(2 * ncl, 1, 1);
+  cfg.gridDim = dim3(CL_CS * ncl, 1, 1);
   cfg.blockDim = dim3(CL_NW * 32, 1, 1);
   cfg.dynamicSmemBytes = s;
   cfg.stream = L.stream;
   cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.x = CL_CS;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
