@@ -312,7 +312,8 @@ fftb_status fftb_plan_set_scale(fftb_plan plan, double g2r, double r2g);
 /* Batch-fastest FP32 plans with N0 == N1 up to 128 run their G->r and r->G
  * plane stages over groups of bands of one k-point (on by default;
  * fftb_plan_autotune measures both): UNSUPPORTED to enable where the plan has
- * no grouped kernels. Results are identical either way. */
+ * no grouped kernels. Results are identical either way. MIXED_TC plans of
+ * that shape have them too, in use while their tensor cores are off. */
 fftb_status fftb_plan_set_band_groups(fftb_plan plan, int32_t enable);
 
 /* FP32 plans with 256-point planes (N0 == N1 = 256) whose half slab plane,

@@ -283,6 +283,7 @@ fftb_status set_tc(fftb_plan_s* p, bool on) {
   p->stick_prec = on ? p->stick_tc : P_F32;
   p->sched_plane = 0;
   p->sched_stick = 0;
+  p->bg = on ? 0 : p->bg_size;  // the grouped batch-fastest kernels are FP32 kernels
   fftb_status st = configure_planes(p);
   if (st != FFTB_OK) return st;
   p->stick_occ = std::max(1, stick_occupancy(p->stick_prec, p->n[2]));
@@ -659,8 +660,10 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
   *p->h_status = 0;
   e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&p->d_status), p->h_status, 0);
   if (e != cudaSuccess) { release(p); return cuda_fail(e, "status word device address"); }
-  if (!p->generic && p->layout == 1 && p->prec_kernel == P_F32 && p->n[0] == p->n[1] && p->total_bands > 0) {
-    // batch-fastest: plane stages over groups of bands of one k-point, where they fit
+  if (!p->generic && p->layout == 1 && (p->prec_kernel == P_F32 || p->tc_avail) && p->n[0] == p->n[1] &&
+      p->total_bands > 0) {
+    // batch-fastest: plane stages over groups of bands of one k-point, where they fit (FP32
+    // kernels: in MIXED_TC plans while the tensor cores are off)
     const int bgs = plane_bg_group(p->n[0]);
     if (bgs > 1 && plane_bg_smem(p->n[0], p->n[1], p->xmax, bgs) <= kSmemLimit) {
       e = prepare_plane_bg(p->n[0], p->xmax);
@@ -689,7 +692,8 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
           if (cudaMalloc(&p->d_T, need) != cudaSuccess) { release(p); return fail(FFTB_ERR_ALLOC, "cudaMalloc stick scratch failed"); }
           p->T_bytes = need;
         }
-        p->bg_size = p->bg = bgs;
+        p->bg_size = bgs;
+        p->bg = p->tc_on ? 0 : bgs;
         p->bg_occ[0] = o0;
         p->bg_occ[1] = o1;
         for (int i = 0; i < 2; ++i) p->plane_ctas[i] = plane_wave(p, i);
@@ -1316,6 +1320,8 @@ FFTB_EXPORT fftb_status fftb_plan_set_band_groups(fftb_plan p, int32_t enable) {
   if (p->generic) return fail(FFTB_ERR_UNSUPPORTED, "a plan on the generic-extent path has no kernel variants");
   if (enable && !p->bg_size)
     return fail(FFTB_ERR_UNSUPPORTED, "no grouped plane kernels for this plan (batch-fastest FP32, N0 == N1, fitting)");
+  if (enable && p->tc_on)
+    return fail(FFTB_ERR_UNSUPPORTED, "the grouped plane kernels are FP32: turn the tensor cores off first");
   const int bg = enable ? p->bg_size : 0;
   if (bg == p->bg) return FFTB_OK;
   p->bg = bg;
@@ -1603,7 +1609,7 @@ fftb_status apply_choice(fftb_plan_s* p, const TuneChoice& c) {
   fftb_status st = resize_T(p, std::max(c.chunk, p->bg_size));
   if (st != FFTB_OK) return st;
   p->chunk = c.chunk;
-  p->bg = (c.bg && p->bg_size) ? p->bg_size : 0;
+  p->bg = (c.bg && p->bg_size && !p->tc_on) ? p->bg_size : 0;
   p->cl = p->cl_ok ? c.cl : 0;
   p->pf_level = c.level;
   p->sched_plane = p->alt_plane_ok ? c.sched_plane : 0;

@@ -259,3 +259,28 @@ def test_mixed_tensor_core_switch_where_none_exist(F):
         with pytest.raises(F.FFTBError) as e:
             q.set_tensor_cores(True)
         assert e.value.status == F.FFTB_ERR_UNSUPPORTED
+
+
+def test_mixed_batch_fastest_groups_with_tensor_cores_off(F):
+    """A batch-fastest MIXED_TC plan at 64^3: with the tensor cores on the
+    plane stages run one band per plane (the grouped kernels are FP32), with
+    them off the grouped FP32 kernels; both against the oracle."""
+    import torch
+    n, r, bands = (64, 64, 64), 16.0, 6
+    plan = F.Plan(n, "g2r", "mixed", radius=r, bands=[bands], layout=1)
+    assert plan.info["tensor_cores_available"] == 1 and plan.info["plane_band_group"] == 0
+    with pytest.raises(F.FFTBError) as e:
+        plan.set_band_groups(True)
+    assert e.value.status == F.FFTB_ERR_UNSUPPORTED
+    g = plan.sphere(0)
+    c = fi.complex_gaussian((bands, len(g)), 63).astype(np.complex64)
+    want = np.moveaxis(oracle.g2r(g, c.astype(np.complex128), n), 0, -1)  # [N2][N1][N0][B]
+    x = torch.from_numpy(np.ascontiguousarray(c.T).reshape(-1)).cuda()
+    for tc in (True, False):
+        plan.set_tensor_cores(tc)
+        assert plan.info["plane_band_group"] == (0 if tc else 4)
+        out = torch.empty(plan.info["cube_elems"], dtype=torch.complex64, device="cuda")
+        plan.execute(x, out)
+        torch.cuda.synchronize()
+        plan.check()
+        assert relerr(out.cpu().numpy().reshape(want.shape), want) <= TOL, tc
