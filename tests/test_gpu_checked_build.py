@@ -27,7 +27,10 @@ def rel(a, b):
 def roundtrip(n, r, prec, bands, **kw):
     sched = kw.pop("sched", None)
     pf = kw.pop("prefetch", None)
+    clusters = kw.pop("clusters", False)
     plan = fftb.Plan(n, "roundtrip", prec, radius=r, bands=bands, **kw)
+    if clusters:
+        plan.set_plane_clusters(True)
     if sched is not None:
         plan.set_radix_schedule(*sched)
     if pf is not None:
@@ -56,9 +59,27 @@ roundtrip((160, 160, 160), 40.0, "fp32", [2], sched=(1, 1))
 roundtrip((160, 160, 160), 40.0, "fp32", [2], prefetch=2)
 roundtrip((32, 32, 48), 10.0, "fp32", [2, 3], kshift=[(0.1, 0.2, -0.3), (-0.4, 0.0, 0.25)], layout=1)
 roundtrip((256, 256, 256), 64.0, "fp32", [1])
+roundtrip((256, 256, 256), 64.0, "fp32", [2], clusters=True)   # slab planes split over two-CTA clusters
 roundtrip((128, 128, 128), 32.0, "fp64", [1])
 roundtrip((72, 80, 90), 17.5, "fp32", [3], max_chunk_bands=2)   # generic-extent path
 roundtrip((15, 27, 25), 5.0, "fp64", [2], layout=1)
+
+# the apply on two-CTA clusters
+n = (256, 256, 256)
+plan = fftb.Plan(n, "apply", "fp32", radius=64.0, bands=[1])
+plan.set_plane_clusters(True)
+v = fi.gaussian_potential(n, 8, 6.0, seed=6).astype(np.float32)
+plan.set_potential(torch.from_numpy(v).cuda())
+g = plan.sphere(0)
+c = fi.complex_gaussian((1, len(g)), 10).astype(np.complex64)
+x = torch.from_numpy(c.reshape(-1)).cuda()
+out = torch.empty_like(x)
+plan.execute(x, out)
+torch.cuda.synchronize()
+plan.check()
+assert rel(out.cpu().numpy(), oracle.apply_potential(g, c.astype(np.complex128), v.astype(np.float64), n)) <= 2e-6
+del plan, out, x
+torch.cuda.empty_cache()
 
 # apply and an explicit (non-canonical) sphere order
 n, r = (32, 32, 32), 8.0
