@@ -169,6 +169,7 @@ struct fftb_plan_s {
   // them (bit i for mode index i: G->r, r->G, apply), clusters resident
   bool cl_ok = false;
   int cl = 0;
+  bool xq_all = false;  // every k-point has KF_XY_QUARTER
   int cl_count[3] = {0, 0, 0};
   // generic-extent path (extents outside the compiled list, N0 != N1): one
   // runtime-length kernel per axis and a slab buffer S between y and x
@@ -518,6 +519,17 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
     kinfo[k].xmap_base = (int32_t)xmap.size();
     kinfo[k].col_base = (int32_t)(col_info.size() / 4);
     kinfo[k].flags = (G.contiguous_columns ? KF_CONTIGUOUS_COLUMNS : 0) | (G.canonical_sticks ? KF_CANONICAL_STICKS : 0);
+    {
+      bool quarter = true;  // every occupied stick within [-N0/4, N0/4] x [-N1/4, N1/4]
+      for (int32_t x = 0; x < d->n[0]; ++x)
+        if (G.xmap[x] >= 0 && x > d->n[0] / 4 && x < d->n[0] - d->n[0] / 4) quarter = false;
+      for (int32_t xy : G.stick_xy) {
+        const int32_t y = xy & 0xFFFF;
+        if (y > d->n[1] / 4 && y < d->n[1] - d->n[1] / 4) quarter = false;
+      }
+      if (quarter) kinfo[k].flags |= KF_XY_QUARTER;
+      p->xq_all = (k == 0 || p->xq_all) && quarter;
+    }
     sticks_so_far += G.S;
     stick_records(G, d->n, (int32_t)ent_base, stick_info);
     for (int32_t v : G.ent_pos) ent_pos.push_back(v);
@@ -968,6 +980,7 @@ static fftb_status enqueue(fftb_plan_s* p, int bands, const void* in, void* out,
   L.inject = p->inject;
   L.status = p->d_status;
   L.pdl = p->pdl ? 1 : 0;
+  L.xq = p->xq_all ? 1 : 0;
   L.groups = static_cast<const int2*>(p->d_groups);
   L.lim_sph = p->sphere_elems;
   L.lim_cube = p->cube_elems;

@@ -45,6 +45,12 @@ constexpr int32_t KF_CONTIGUOUS_COLUMNS = 1;
 // sphere list (the canonical order of a cutoff sphere); the z stage then
 // indexes the coefficient list directly.
 constexpr int32_t KF_CANONICAL_STICKS = 2;
+// Every occupied stick (x, y) satisfies |x| <= N0/4 and |y| <= N1/4 (signed),
+// as for the cutoff spheres of the paper's shape rule, cube width = twice the
+// sphere diameter: the y and x lines' inputs (G -> r) and needed outputs
+// (r -> G) then avoid the middle half of the line, and the kernels may drop
+// those elements at compile time.
+constexpr int32_t KF_XY_QUARTER = 4;
 
 // Per band: its k-point's geometry and the offsets (complex elements) of
 // its first sphere entry and first cube point, read in one 48-byte load.
@@ -92,6 +98,7 @@ struct Launch {
   int32_t inject;       // INJECT_* bits (tests of the bounded waits)
   int32_t* status;      // device-visible status word (STATUS_* bits), set on a failed wait
   int32_t pdl;          // launch with programmatic dependent launch (overlaps launch and prologue)
+  int32_t xq;           // every k-point of the plan has KF_XY_QUARTER (plane kernel variant choice)
   const int2* groups;   // batch-fastest band groups (first band, bands), plan-global list
   int32_t grp0, ngrp;   // the groups of this launch (they cover [band0, band0 + nb))
   // buffer extents in complex elements from the base pointers above, read by

@@ -2,6 +2,8 @@
 // schedule of the lengths that have one (LPV<N, 1>; the plane stages of 160
 // take the two-pass schedule LPV<160, 2>); the autotuner chooses between them
 // and the default schedule.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace fftb {
@@ -9,16 +11,18 @@ namespace {
 
 #define FFTB_ALT_SIZES(X) X(64) X(96) X(128) X(160)
 
-// schedule variant of the alternative plane kernels
+// schedule variant of the alternative plane kernels (160: the two-pass
+// schedule, and its variant 3 that drops the middle half of each x line for
+// launches whose k-points all have every occupied x within [-N/4, N/4])
 template <int N> constexpr int plane_v() { return N == 160 ? 2 : 1; }
+template <int N> constexpr int plane_vq() { return N == 160 ? 3 : plane_v<N>(); }
 
-template <int N, int MODE> const void* plane_fn() {
-  return (const void*)k_plane<float, N, N, MODE, false, false, false, plane_v<N>()>;
+template <int N, int MODE, int V = plane_v<N>()> const void* plane_fn() {
+  return (const void*)k_plane<float, N, N, MODE, false, false, false, V>;
 }
 template <int N, int MODE> const void* stick_fn() { return (const void*)k_stick<float, N, MODE, false, 1>; }
 
-template <int N> cudaError_t go_plane_v(int mode, const Launch& L) {
-  constexpr int V = plane_v<N>();
+template <int N, int V> cudaError_t go_plane_vv(int mode, const Launch& L) {
   const size_t smem = plane_smem_c<float, N, N, V>(L.g.xmax, L.a_bufs);
   const int nplanes = L.nb * L.g.n2;
   const dim3 grid(L.plane_ctas > 0 ? min(L.plane_ctas, nplanes) : nplanes);
@@ -26,6 +30,10 @@ template <int N> cudaError_t go_plane_v(int mode, const Launch& L) {
   if (mode == M_G2R) return launch_k(k_plane<float, N, N, M_G2R, false, false, false, V>, grid, NT, smem, L, L);
   if (mode == M_R2G) return launch_k(k_plane<float, N, N, M_R2G, false, false, false, V>, grid, NT, smem, L, L);
   return launch_k(k_plane<float, N, N, M_APPLY, false, false, false, V>, grid, NT, smem, L, L);
+}
+template <int N> cudaError_t go_plane_v(int mode, const Launch& L) {
+  if (L.xq && plane_vq<N>() != plane_v<N>()) return go_plane_vv<N, plane_vq<N>()>(mode, L);
+  return go_plane_vv<N, plane_v<N>()>(mode, L);
 }
 template <int N> cudaError_t go_stick_v(int mode, const Launch& L, int ctas) {
   constexpr int WZ = 32 / Line<N, 1>::G;
@@ -41,6 +49,12 @@ template <int N> cudaError_t prep_plane_v(int xmax, int a_bufs) {
   cudaError_t e = raise_smem_limit(plane_fn<N, M_G2R>(), s);
   if (e == cudaSuccess) e = raise_smem_limit(plane_fn<N, M_R2G>(), s);
   if (e == cudaSuccess) e = raise_smem_limit(plane_fn<N, M_APPLY>(), s);
+  if (plane_vq<N>() != plane_v<N>()) {
+    const int sq = (int)plane_smem_c<float, N, N, plane_vq<N>()>(xmax, a_bufs);
+    if (e == cudaSuccess) e = raise_smem_limit(plane_fn<N, M_G2R, plane_vq<N>()>(), sq);
+    if (e == cudaSuccess) e = raise_smem_limit(plane_fn<N, M_R2G, plane_vq<N>()>(), sq);
+    if (e == cudaSuccess) e = raise_smem_limit(plane_fn<N, M_APPLY, plane_vq<N>()>(), sq);
+  }
   return e;
 }
 template <int N> cudaError_t prep_stick_v() {
@@ -53,7 +67,16 @@ template <int N> int occ_plane_v(int mode, int xmax, int a_bufs) {
   const size_t s = plane_smem_c<float, N, N, plane_v<N>()>(xmax, a_bufs);
   const void* fn = mode == M_G2R ? plane_fn<N, M_G2R>() : mode == M_R2G ? plane_fn<N, M_R2G>() : plane_fn<N, M_APPLY>();
   int nb = 0;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, PlaneCfg<float>::NW * 32, s) == cudaSuccess ? nb : 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, PlaneCfg<float>::NW * 32, s) != cudaSuccess) return 0;
+  if (plane_vq<N>() != plane_v<N>()) {  // the variant must be resident the same way
+    const void* fq = mode == M_G2R   ? plane_fn<N, M_G2R, plane_vq<N>()>()
+                     : mode == M_R2G ? plane_fn<N, M_R2G, plane_vq<N>()>()
+                                     : plane_fn<N, M_APPLY, plane_vq<N>()>();
+    int nq = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nq, fq, PlaneCfg<float>::NW * 32, s) != cudaSuccess) return 0;
+    nb = std::min(nb, nq);
+  }
+  return nb;
 }
 template <int N> int occ_stick_v() {
   int nb = 0;

@@ -319,6 +319,13 @@ __host__ __device__ constexpr int a_pitch(int x, int r = 2) { return x + ((r - x
 // successive rows 8 banks apart, so every bank is hit twice, the two
 // wavefronts that 256 bytes need at least (a pitch of 2 (mod 16) hits some
 // banks of a column store four times). Other shapes keep 2 (mod 16).
+// Element q of a lane's first-pass (R = R0) or last-pass (R = RL) order of a
+// length-N line held by G lanes lies, for every lane, strictly inside
+// (N/4, N - N/4): with every occupied x within [-N/4, N/4] it is a zero input
+// (G -> r) or an unneeded output (r -> G) of the x line.
+template <int N, int G, int R> __host__ __device__ constexpr bool x_mid(int q) {
+  return (q / R) * G + (q % R) * (N / R) > N / 4 && (q / R) * G + (q % R) * (N / R) + G - 1 < N - N / 4;
+}
 template <typename C, int N0, int N1, int V> __host__ __device__ constexpr int a_res() {
   return sizeof(C) == 8 && Line<N0, V>::G == 4 && Line<N1, V>::G == 4 ? 4 : 2;
 }
@@ -361,7 +368,7 @@ size_t plane_smem_c(int xmax, int a_bufs, bool ag = false, int pf_mode = 0, int 
   using C = typename cplx<T>::type;
   return sizeof(C) * ((ag ? 0 : (size_t)a_bufs * N1 * a_pitch(xmax, a_res<C, N0, N1, V>())) +
                       (size_t)PlaneCfg<T>::NW * plane_scratch<N0, N1, V>() + N0 + N1) +
-         plane_pf_bytes<T, N0, N1>(pf_mode, tp) + (V == 2 ? sizeof(uint64_t) * PlaneCfg<T>::NW : 0) + 16;
+         plane_pf_bytes<T, N0, N1>(pf_mode, tp) + (V >= 2 ? sizeof(uint64_t) * PlaneCfg<T>::NW : 0) + 16;
 }
 
 // packed per-lane slab indices: byte q of w[q / 4] = xi of position q, 255 =
@@ -411,7 +418,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   // the G -> r rows for bulk stores the same way measured 8 % slower than
   // stores by the lanes). Used where the cube is band-major and 16-byte
   // aligned (L.pf).
-  constexpr bool XS = V == 2 && !AG && !PF && !TC;
+  constexpr bool XS = V >= 2 && !AG && !PF && !TC;
   // YS (the same schedule, G -> r): where a column's sticks are consecutive
   // in the stick row (canonical spheres), the stick values of a warp's next y
   // task, one contiguous run of the row, arrive by one bulk copy in the
@@ -419,6 +426,12 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   // as soon as the rows are free: after the exchange of the warp's current y
   // task, or after the exchange of its last x task of the previous plane.
   constexpr bool YS = XS && MODE == M_G2R;
+  // V = 3 (the two-pass schedule for plans whose k-points all have every
+  // occupied stick within [-N0/4, N0/4] x [-N1/4, N1/4], KF_XY_QUARTER): the y
+  // and x lines drop the middle half of the line at compile time, zero inputs
+  // (G -> r, apply) and unneeded outputs (r -> G, apply), whose arithmetic the
+  // compiler removes
+  constexpr bool XQ = V == 3 && !TC;
   static_assert(!XS || (LX::PITCH * sizeof(C)) % 16 == 0, "staged rows start on 16-byte boundaries");
   uint64_t* xbar = reinterpret_cast<uint64_t*>(tw1 + N1);
   // end of the layout (8-byte aligned): the slab-plane barrier of single-buffer kernels
@@ -693,6 +706,10 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
           for (int m = 0; m < EY / LY::R0; ++m)
 #pragma unroll
             for (int j = 0; j < LY::R0; ++j) {
+              if (XQ && x_mid<N1, LY::G, LY::R0>(m * LY::R0 + j)) {  // no occupied y there
+                v[m * LY::R0 + j] = czero<C>();
+                continue;
+              }
               const int d = ysigned(LY::first_pos(gy, m, j)) - ylo;
               v[m * LY::R0 + j] = (unsigned)d < (unsigned)len ? xrows[sa + d] : czero<C>();
             }
@@ -704,6 +721,10 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
           for (int m = 0; m < EY / LY::R0; ++m)
 #pragma unroll
             for (int j = 0; j < LY::R0; ++j) {
+              if (XQ && x_mid<N1, LY::G, LY::R0>(m * LY::R0 + j)) {  // no occupied y there
+                v[m * LY::R0 + j] = czero<C>();
+                continue;
+              }
               const int d = ysigned(LY::first_pos(gy, m, j)) - ylo;
               if constexpr (PF) v[m * LY::R0 + j] = (unsigned)d < (unsigned)len ? Tr[sa + d] : czero<C>();
               else
@@ -726,7 +747,9 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
           for (int m = 0; m < EY / LY::R0; ++m)
 #pragma unroll
-            for (int j = 0; j < LY::R0; ++j) v[m * LY::R0 + j] = rowy[wpad(LY::first_pos(gy, m, j))];
+            for (int j = 0; j < LY::R0; ++j)
+              v[m * LY::R0 + j] = XQ && x_mid<N1, LY::G, LY::R0>(m * LY::R0 + j) ? czero<C>()  // no stick there
+                                                                                 : rowy[wpad(LY::first_pos(gy, m, j))];
           __syncwarp();
         }
         if constexpr (TC) LY::template run_tc<+1>(v, gy, rowy, scr, tw1, tcy, wy_p);
@@ -776,6 +799,10 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
         C v[EX];
 #pragma unroll
         for (int q = 0; q < EX; ++q) {
+          if (XQ && x_mid<N0, LX::G, LX::R0>(q)) {  // no occupied x there
+            v[q] = czero<C>();
+            continue;
+          }
           const int xi = xin.get(q);
           v[q] = (live && (allx || xi != 255) && FFTB_IN(row * XP + xi, abuf, L.status)) ? A[row * XP + xi]
                                                                                           : czero<C>();
@@ -828,6 +855,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
           if (live) {
 #pragma unroll
             for (int q = 0; q < EX; ++q) {
+              if (XQ && x_mid<N0, LX::G, LX::RL>(q)) continue;  // no occupied x there
               const int xi = xout.get(q);
               if ((allx || xi != 255) && FFTB_IN(row * XP + xi, abuf, L.status)) A[row * XP + xi] = v[q];
             }
@@ -934,6 +962,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
         if (live) {
 #pragma unroll
           for (int q = 0; q < EX; ++q) {
+            if (XQ && x_mid<N0, LX::G, LX::RL>(q)) continue;  // no occupied x there
             const int xi = xout.get(q);
             if ((allx || xi != 255) && FFTB_IN(row * XP + xi, abuf, L.status)) A[row * XP + xi] = v[q];
           }
@@ -980,6 +1009,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
             for (int m = 0; m < EY / LY::RL; ++m)
 #pragma unroll
               for (int j = 0; j < LY::RL; ++j) {
+                if (XQ && x_mid<N1, LY::G, LY::RL>(m * LY::RL + j)) continue;  // no occupied y there
                 const int d = ysigned(LY::last_pos(gy, m, j)) - ylo;
                 if ((unsigned)d < (unsigned)len && FFTB_IN(tz + sa + d, L.lim_T, L.status)) Tz[sa + d] = v[m * LY::RL + j];
               }
@@ -988,7 +1018,10 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
           for (int m = 0; m < EY / LY::RL; ++m)
 #pragma unroll
-            for (int j = 0; j < LY::RL; ++j) rowy[wpad(LY::last_pos(gy, m, j))] = v[m * LY::RL + j];
+            for (int j = 0; j < LY::RL; ++j) {
+              if (XQ && x_mid<N1, LY::G, LY::RL>(m * LY::RL + j)) continue;  // no stick there
+              rowy[wpad(LY::last_pos(gy, m, j))] = v[m * LY::RL + j];
+            }
           __syncwarp();
           const int sbeg = __shfl_sync(0xffffffffu, ci.x, 0);
           const int send = __shfl_sync(0xffffffffu, ci.x + ci.y, (nl - 1) * LY::G);

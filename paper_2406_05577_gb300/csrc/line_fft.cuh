@@ -59,6 +59,9 @@ template <> struct LPV<160, 2> {
   static constexpr int E = 40;
   static constexpr int R[4] = {40, 4, 0, 0};
 };
+// the same schedule for the plane kernels that drop the middle half of each
+// x line (every occupied x within [-N/4, N/4])
+template <> struct LPV<160, 3> : LPV<160, 2> {};
 
 // ----------------------------------------------------------- tensor cores
 // A radix-8 pass as a dense product on the tensor cores (split precision):

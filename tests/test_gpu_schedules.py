@@ -202,3 +202,59 @@ def test_160_two_pass_g2r_staged_sticks(F):
     torch.cuda.synchronize()
     plan.check()
     assert torch.equal(out, ref)
+
+
+@pytest.mark.parametrize("r", [40.0, 41.0])
+def test_160_two_pass_quarter_x_pruning(F, r):
+    """The 160 = 40 x 4 plane kernels drop the middle half of each x line at
+    compile time where every occupied x is within [-40, 40] (|G| <= 40), and
+    run the whole line otherwise (|G| <= 41 reaches x = 41): round trip, the
+    cube of a band and r -> G at sampled G against the oracle, and the fused
+    apply against the oracle, in both cases."""
+    import torch
+    n, bands = (160, 160, 160), 2
+    vol = 160 ** 3
+    plan = F.Plan(n, "roundtrip", "fp32", radius=r, bands=[bands])
+    plan.set_radix_schedule(1, 0)
+    g = plan.sphere(0)
+    assert (np.abs(g[:, 0]).max() <= 40) == (r == 40.0)
+    c = fi.complex_gaussian((bands, len(g)), 121).astype(np.complex64)
+    c64 = c.astype(np.complex128)
+    x = torch.from_numpy(c.reshape(-1)).cuda()
+    out = torch.empty_like(x)
+    cube = torch.empty(plan.info["cube_elems"], dtype=torch.complex64, device="cuda")
+    plan.execute(x, out, cube)
+    torch.cuda.synchronize()
+    plan.check()
+    assert relerr(out.cpu().numpy(), vol * c64.reshape(-1)) <= 2e-6
+    assert relerr(cube[vol:].view(160, 160, 160).cpu().numpy(), oracle.g2r(g, c64[1], n)) <= 2e-6
+    del cube
+    p2 = F.Plan(n, "r2g", "fp32", radius=r, bands=[1])
+    p2.set_radix_schedule(1, 0)
+    R = fi.complex_gaussian((160, 160, 160), 122).astype(np.complex64)
+    o2 = torch.empty(p2.info["sphere_elems"], dtype=torch.complex64, device="cuda")
+    p2.execute(torch.from_numpy(R.reshape(-1)).cuda(), o2)
+    torch.cuda.synchronize()
+    p2.check()
+    sel = np.random.default_rng(123).choice(len(g), 6, replace=False)
+    sel[0] = int(np.argmax(np.abs(g[:, 0])))  # a G on the edge of the occupied x range
+    assert relerr(o2.cpu().numpy()[sel], oracle.r2g_points(g[sel], R.astype(np.complex128), n)) <= 2e-6
+    # a column with a gap: its sticks go through the scratch rows
+    gg = g[~((g[:, 0] == -7) & (g[:, 1] == 3))]
+    p3 = F.Plan(n, "r2g", "fp32", g_lists=[gg], bands=[1])
+    p3.set_radix_schedule(1, 0)
+    o3 = torch.empty(p3.info["sphere_elems"], dtype=torch.complex64, device="cuda")
+    p3.execute(torch.from_numpy(R.reshape(-1)).cuda(), o3)
+    torch.cuda.synchronize()
+    p3.check()
+    s3 = np.random.default_rng(125).choice(len(gg), 6, replace=False)
+    assert relerr(o3.cpu().numpy()[s3], oracle.r2g_points(gg[s3], R.astype(np.complex128), n)) <= 2e-6
+    pa = F.Plan(n, "apply", "fp32", radius=r, bands=[1])
+    pa.set_radix_schedule(1, 0)
+    v = fi.gaussian_potential(n, 16, 5.0, seed=124).astype(np.float32)
+    pa.set_potential(torch.from_numpy(v).cuda())
+    oa = torch.empty(pa.info["sphere_elems"], dtype=torch.complex64, device="cuda")
+    pa.execute(torch.from_numpy(c[0].copy()).cuda(), oa)
+    torch.cuda.synchronize()
+    pa.check()
+    assert relerr(oa.cpu().numpy(), oracle.apply_potential(g, c64[:1], v.astype(np.float64), n)) <= 2e-6
