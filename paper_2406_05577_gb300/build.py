@@ -25,7 +25,7 @@ BUILD_CHECK = os.path.join(HERE, "_build_check")
 LIB_CHECK = os.path.join(HERE, "libfftb_check.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["k_f32.cu", "k_f32_pf.cu", "k_f32_alt.cu", "k_f32_bg.cu", "k_scale.cu", "k_f64.cu", "k_tc.cu", "k_tc5.cu", "noalloc.cu", "k_generic.cu", "k_cluster.cu"]
+CU_SOURCES = ["k_f32.cu", "k_f32_pf.cu", "k_f32_alt.cu", "k_f32_bg.cu", "k_scale.cu", "k_f64.cu", "k_tc.cu", "k_tc5.cu", "noalloc.cu", "k_generic.cu", "k_cluster.cu", "k_f32_zq.cu"]
 CPP_SOURCES = ["geometry.cpp", "fftb_api.cpp"]
 
 

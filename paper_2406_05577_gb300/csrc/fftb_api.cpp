@@ -170,6 +170,7 @@ struct fftb_plan_s {
   bool cl_ok = false;
   int cl = 0;
   bool xq_all = false;  // every k-point has KF_XY_QUARTER
+  bool zq_all = false;  // every k-point has KF_Z_QUARTER
   int cl_count[3] = {0, 0, 0};
   // generic-extent path (extents outside the compiled list, N0 != N1): one
   // runtime-length kernel per axis and a slab buffer S between y and x
@@ -529,6 +530,13 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
       }
       if (quarter) kinfo[k].flags |= KF_XY_QUARTER;
       p->xq_all = (k == 0 || p->xq_all) && quarter;
+      bool zquarter = true;  // every entry within |z| <= N2/4
+      for (int32_t zs : G.ent_zs) {
+        const int32_t z = (int32_t)((uint32_t)zs >> 24);
+        if (z > d->n[2] / 4 && z < d->n[2] - d->n[2] / 4) zquarter = false;
+      }
+      if (zquarter) kinfo[k].flags |= KF_Z_QUARTER;
+      p->zq_all = (k == 0 || p->zq_all) && zquarter;
     }
     sticks_so_far += G.S;
     stick_records(G, d->n, (int32_t)ent_base, stick_info);
@@ -654,6 +662,10 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
     }
   }
   p->stick_occ = std::max(1, stick_occupancy(p->stick_prec, p->n[2]));
+  if (p->prec != FFTB_FP64 && p->zq_all) {  // FP32 z stages (MIXED_TC: once its tensor cores are off)
+    e = prepare_stick_zq(p->n[2]);
+    if (e != cudaSuccess) { release(p); return cuda_fail(e, "kernel attributes"); }
+  }
   if (p->stick_prec == P_F32 && alt_schedule(p->n[2])) {
     e = prepare_alt(0, p->n[2], 0, 1);
     if (e != cudaSuccess) { release(p); return cuda_fail(e, "kernel attributes"); }
@@ -892,7 +904,9 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
   const bool cube_in_16 = (reinterpret_cast<uintptr_t>(L.cube_in) % 16) == 0;
   switch (kind) {
     case K_STICK_G2R:
-      e = p->sched_stick ? launch_stick_alt(M_G2R, L, p->tiles) : launch_stick(p->stick_prec, M_G2R, L, p->tiles);
+      e = p->sched_stick                         ? launch_stick_alt(M_G2R, L, p->tiles)
+          : (p->stick_prec == P_F32 && p->zq_all) ? launch_stick_zq(M_G2R, L, p->tiles)
+                                                  : launch_stick(p->stick_prec, M_G2R, L, p->tiles);
       break;
     case K_PLANE_G2R: {
       Launch Lp = L;
@@ -920,7 +934,9 @@ static cudaError_t stage(fftb_plan_s* p, int kind, const Launch& L) {
       break;
     }
     case K_STICK_R2G:
-      e = p->sched_stick ? launch_stick_alt(M_R2G, L, p->tiles) : launch_stick(p->stick_prec, M_R2G, L, p->tiles);
+      e = p->sched_stick                         ? launch_stick_alt(M_R2G, L, p->tiles)
+          : (p->stick_prec == P_F32 && p->zq_all) ? launch_stick_zq(M_R2G, L, p->tiles)
+                                                  : launch_stick(p->stick_prec, M_R2G, L, p->tiles);
       break;
     default: {
       Launch Lp = L;
@@ -981,6 +997,7 @@ static fftb_status enqueue(fftb_plan_s* p, int bands, const void* in, void* out,
   L.status = p->d_status;
   L.pdl = p->pdl ? 1 : 0;
   L.xq = p->xq_all ? 1 : 0;
+  L.zq = p->zq_all ? 1 : 0;
   L.groups = static_cast<const int2*>(p->d_groups);
   L.lim_sph = p->sphere_elems;
   L.lim_cube = p->cube_elems;

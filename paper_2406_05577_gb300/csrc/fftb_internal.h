@@ -51,6 +51,9 @@ constexpr int32_t KF_CANONICAL_STICKS = 2;
 // (r -> G) then avoid the middle half of the line, and the kernels may drop
 // those elements at compile time.
 constexpr int32_t KF_XY_QUARTER = 4;
+// Every sphere entry satisfies |z| <= N2/4 (signed): the z lines' inputs and
+// needed outputs avoid the middle half of the line in the same way.
+constexpr int32_t KF_Z_QUARTER = 8;
 
 // Per band: its k-point's geometry and the offsets (complex elements) of
 // its first sphere entry and first cube point, read in one 48-byte load.
@@ -99,6 +102,7 @@ struct Launch {
   int32_t* status;      // device-visible status word (STATUS_* bits), set on a failed wait
   int32_t pdl;          // launch with programmatic dependent launch (overlaps launch and prologue)
   int32_t xq;           // every k-point of the plan has KF_XY_QUARTER (plane kernel variant choice)
+  int32_t zq;           // every k-point of the plan has KF_Z_QUARTER (z-stage kernel variant choice)
   const int2* groups;   // batch-fastest band groups (first band, bands), plan-global list
   int32_t grp0, ngrp;   // the groups of this launch (they cover [band0, band0 + nb))
   // buffer extents in complex elements from the base pointers above, read by
@@ -171,6 +175,10 @@ cudaError_t launch_plane_cluster(int mode, const Launch& L);
 // (k_scale.cu): the optional output normalisation.
 cudaError_t launch_scale(int csize, void* data, int64_t n, double s, const Launch& L, int sms);
 cudaError_t launch_stick_alt(int mode, const Launch& L, int ctas);
+// FP32 z-stage kernels that drop the middle half of each z line (k_f32_zq.cu;
+// default schedule; launches whose k-points all have KF_Z_QUARTER)
+cudaError_t prepare_stick_zq(int n2);
+cudaError_t launch_stick_zq(int mode, const Launch& L, int ctas);
 // MIXED_TC plane stage on the 5th-generation tensor cores (k_tc5.cu): the
 // union over k-points of the occupied x values [xlo, xlo + xu) and of the
 // stick y values [ylo, ylo + yu) (signed grid indices), and the device image

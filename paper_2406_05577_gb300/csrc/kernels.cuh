@@ -33,6 +33,14 @@
 
 namespace fftb {
 
+// Element q of a lane's first-pass (R = R0) or last-pass (R = RL) order of a
+// length-N line held by G lanes lies, for every lane, strictly inside
+// (N/4, N - N/4): where every occupied position of that axis is within
+// [-N/4, N/4] it is a zero input (G -> r) or an unneeded output (r -> G).
+template <int N, int G, int R> __host__ __device__ constexpr bool x_mid(int q) {
+  return (q / R) * G + (q % R) * (N / R) > N / 4 && (q / R) * G + (q % R) * (N / R) + G - 1 < N - N / 4;
+}
+
 // ------------------------------------------------------------------ z stage
 // Each occupied (x,y) stick is one length-N2 line held in registers by
 // Line<N2>::G lanes; a warp carries 32 / G consecutive sticks, a CTA 8 warps.
@@ -59,7 +67,11 @@ template <typename T> __host__ __device__ constexpr int stick_minb() {
 #endif
 }
 
-template <typename T, int N2, int MODE, bool TC = false, int V = 0>
+// QZ: every sphere entry of the launch has |z| <= N2/4 (KF_Z_QUARTER): the
+// z lines' inputs (G -> r) and needed outputs (r -> G) avoid the middle half
+// of the line, whose loads, stores and (r -> G) arithmetic are dropped at
+// compile time.
+template <typename T, int N2, int MODE, bool TC = false, int V = 0, bool QZ = false>
 __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(const Launch L) {
   using C = typename cplx<T>::type;
   using LZ = Line<N2, V>;
@@ -138,6 +150,10 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
         for (int m = 0; m < EZ / LZ::R0; ++m)
 #pragma unroll
           for (int j = 0; j < LZ::R0; ++j) {
+            if (QZ && x_mid<N2, LZ::G, LZ::R0>(m * LZ::R0 + j)) {  // no entry there
+              v[m * LZ::R0 + j] = czero<C>();
+              continue;
+            }
             const int d = zsigned(LZ::first_pos(g, m, j)) - k.si.w;
             v[m * LZ::R0 + j] = (unsigned)d < (unsigned)len && FFTB_IN(k.sph + k.si.z + d, L.lim_sph, L.status)
                                     ? in[k.si.z + d]
@@ -148,6 +164,10 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
         for (int m = 0; m < EZ / LZ::R0; ++m)
 #pragma unroll
           for (int j = 0; j < LZ::R0; ++j) {
+            if (QZ && x_mid<N2, LZ::G, LZ::R0>(m * LZ::R0 + j)) {  // no entry there
+              v[m * LZ::R0 + j] = czero<C>();
+              continue;
+            }
             const int d = zsigned(LZ::first_pos(g, m, j)) - k.si.w;
             v[m * LZ::R0 + j] =
                 (unsigned)d < (unsigned)len && FFTB_IN(k.sph + (int64_t)(k.si.z + d) * k.st, L.lim_sph, L.status)
@@ -194,6 +214,7 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
             for (int m = 0; m < EZ / LZ::RL; ++m)
 #pragma unroll
               for (int j = 0; j < LZ::RL; ++j) {
+                if (QZ && x_mid<N2, LZ::G, LZ::RL>(m * LZ::RL + j)) continue;  // no entry there
                 const int d = zsigned(LZ::last_pos(g, m, j)) - k.si.w;
                 if ((unsigned)d < (unsigned)len && FFTB_IN(k.sph + k.si.z + d, L.lim_sph, L.status))
                   out[k.si.z + d] = v[m * LZ::RL + j];
@@ -203,6 +224,7 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
             for (int m = 0; m < EZ / LZ::RL; ++m)
 #pragma unroll
               for (int j = 0; j < LZ::RL; ++j) {
+                if (QZ && x_mid<N2, LZ::G, LZ::RL>(m * LZ::RL + j)) continue;  // no entry there
                 const int d = zsigned(LZ::last_pos(g, m, j)) - k.si.w;
                 if ((unsigned)d < (unsigned)len &&
                     FFTB_IN(k.sph + (int64_t)(k.si.z + d) * k.st, L.lim_sph, L.status))
@@ -216,7 +238,10 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
 #pragma unroll
         for (int m = 0; m < EZ / LZ::RL; ++m)
 #pragma unroll
-          for (int j = 0; j < LZ::RL; ++j) row[wpad(LZ::last_pos(g, m, j))] = v[m * LZ::RL + j];
+          for (int j = 0; j < LZ::RL; ++j) {
+            if (QZ && x_mid<N2, LZ::G, LZ::RL>(m * LZ::RL + j)) continue;  // no entry there
+            row[wpad(LZ::last_pos(g, m, j))] = v[m * LZ::RL + j];
+          }
         __syncwarp();
         for (int e = ea + lane; e < eb; e += 32) {
           const uint32_t zs = (uint32_t)L.g.ent_zs[e];
@@ -319,13 +344,6 @@ __host__ __device__ constexpr int a_pitch(int x, int r = 2) { return x + ((r - x
 // successive rows 8 banks apart, so every bank is hit twice, the two
 // wavefronts that 256 bytes need at least (a pitch of 2 (mod 16) hits some
 // banks of a column store four times). Other shapes keep 2 (mod 16).
-// Element q of a lane's first-pass (R = R0) or last-pass (R = RL) order of a
-// length-N line held by G lanes lies, for every lane, strictly inside
-// (N/4, N - N/4): with every occupied x within [-N/4, N/4] it is a zero input
-// (G -> r) or an unneeded output (r -> G) of the x line.
-template <int N, int G, int R> __host__ __device__ constexpr bool x_mid(int q) {
-  return (q / R) * G + (q % R) * (N / R) > N / 4 && (q / R) * G + (q % R) * (N / R) + G - 1 < N - N / 4;
-}
 template <typename C, int N0, int N1, int V> __host__ __device__ constexpr int a_res() {
   return sizeof(C) == 8 && Line<N0, V>::G == 4 && Line<N1, V>::G == 4 ? 4 : 2;
 }
