@@ -11,9 +11,14 @@ namespace {
 
 template <int N, int MODE> constexpr bool pf_has() { return MODE != M_R2G || rows_prefetchable<float, N, N>(); }
 
-template <int N, int MODE, bool AG> auto pf_kernel() { return k_plane<float, N, N, MODE, false, AG, pf_has<N, MODE>()>; }
+template <int N, int MODE, bool AG, bool QP = false> auto pf_kernel() {
+  return k_plane<float, N, N, MODE, false, AG, pf_has<N, MODE>(), 0, QP>;
+}
 
-template <int N, bool AG> cudaError_t go(int mode, const Launch& L) {
+template <int N, bool AG, bool QP = false> cudaError_t go(int mode, const Launch& L) {
+  if constexpr (!QP && qp_variant<float, false, N>()) {
+    if (L.xq) return go<N, AG, true>(mode, L);  // every sphere within a quarter of the grid
+  }
   const size_t smem = plane_smem_c<float, N, N>(L.g.xmax, L.a_bufs, AG, mode, L.g.smax);
   const int nplanes = L.nb * L.g.n2;
   // AG: persistent CTAs only, never more than the slab-plane blocks allocated
@@ -21,25 +26,30 @@ template <int N, bool AG> cudaError_t go(int mode, const Launch& L) {
   if (ctas < 1) return cudaErrorInvalidValue;
   const dim3 grid(ctas);
   constexpr int NT = PlaneCfg<float>::NW * 32;
-  if (mode == M_G2R) return launch_k(pf_kernel<N, M_G2R, AG>(), grid, NT, smem, L, L);
-  if (mode == M_R2G) return launch_k(pf_kernel<N, M_R2G, AG>(), grid, NT, smem, L, L);
-  return launch_k(pf_kernel<N, M_APPLY, AG>(), grid, NT, smem, L, L);
+  if (mode == M_G2R) return launch_k(pf_kernel<N, M_G2R, AG, QP>(), grid, NT, smem, L, L);
+  if (mode == M_R2G) return launch_k(pf_kernel<N, M_R2G, AG, QP>(), grid, NT, smem, L, L);
+  return launch_k(pf_kernel<N, M_APPLY, AG, QP>(), grid, NT, smem, L, L);
 }
-template <int N, bool AG> cudaError_t prep(int mode, int xmax, int a_bufs, int tp) {
+template <int N, bool AG, bool QP = false> cudaError_t prep(int mode, int xmax, int a_bufs, int tp) {
+  if constexpr (!QP && qp_variant<float, false, N>()) {
+    cudaError_t e = prep<N, AG, true>(mode, xmax, a_bufs, tp);
+    if (e != cudaSuccess) return e;
+  }
   const int s = (int)plane_smem_c<float, N, N>(xmax, a_bufs, AG, mode, tp);
-  if (mode == M_G2R) return raise_smem_limit((const void*)pf_kernel<N, M_G2R, AG>(), s);
-  if (mode == M_R2G) return raise_smem_limit((const void*)pf_kernel<N, M_R2G, AG>(), s);
-  return raise_smem_limit((const void*)pf_kernel<N, M_APPLY, AG>(), s);
+  if (mode == M_G2R) return raise_smem_limit((const void*)pf_kernel<N, M_G2R, AG, QP>(), s);
+  if (mode == M_R2G) return raise_smem_limit((const void*)pf_kernel<N, M_R2G, AG, QP>(), s);
+  return raise_smem_limit((const void*)pf_kernel<N, M_APPLY, AG, QP>(), s);
 }
-template <int N, bool AG> int occ(int mode, int xmax, int a_bufs, int tp) {
+template <int N, bool AG, bool QP = false> int occ(int mode, int xmax, int a_bufs, int tp) {
   constexpr int NT = PlaneCfg<float>::NW * 32;
   const size_t s = plane_smem_c<float, N, N>(xmax, a_bufs, AG, mode, tp);
-  int nb = 0;
+  int nb = 0, nq = 1 << 30;  // the line-pruned variant must be resident the same way
+  if constexpr (!QP && qp_variant<float, false, N>()) nq = occ<N, AG, true>(mode, xmax, a_bufs, tp);
   cudaError_t e;
-  if (mode == M_G2R) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pf_kernel<N, M_G2R, AG>(), NT, s);
-  else if (mode == M_R2G) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pf_kernel<N, M_R2G, AG>(), NT, s);
-  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pf_kernel<N, M_APPLY, AG>(), NT, s);
-  return e == cudaSuccess ? nb : 0;
+  if (mode == M_G2R) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pf_kernel<N, M_G2R, AG, QP>(), NT, s);
+  else if (mode == M_R2G) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pf_kernel<N, M_R2G, AG, QP>(), NT, s);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pf_kernel<N, M_APPLY, AG, QP>(), NT, s);
+  return e == cudaSuccess ? min(nb, nq) : 0;
 }
 
 bool size_listed(int n, bool ag) {

@@ -402,7 +402,8 @@ template <int E> struct XiPack {
 // by the warp itself once it has read the current ones), completed on
 // mbarriers. A wait that runs out sets the plan's status word; the CTA then
 // leaves at the next block barrier, after its copies in flight have landed.
-template <typename T, int N0, int N1, int MODE, bool TC = false, bool AG = false, bool PF = false, int V = 0>
+template <typename T, int N0, int N1, int MODE, bool TC = false, bool AG = false, bool PF = false, int V = 0,
+          bool QP = false>
 __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k_plane(const Launch L) {
   using C = typename cplx<T>::type;
   using LY = Line<N1, V>;
@@ -444,12 +445,12 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   // as soon as the rows are free: after the exchange of the warp's current y
   // task, or after the exchange of its last x task of the previous plane.
   constexpr bool YS = XS && MODE == M_G2R;
-  // V = 3 (the two-pass schedule for plans whose k-points all have every
-  // occupied stick within [-N0/4, N0/4] x [-N1/4, N1/4], KF_XY_QUARTER): the y
-  // and x lines drop the middle half of the line at compile time, zero inputs
-  // (G -> r, apply) and unneeded outputs (r -> G, apply), whose arithmetic the
-  // compiler removes
-  constexpr bool XQ = V == 3 && !TC;
+  // V = 3 (the two-pass schedule) and QP (the other schedules) for plans whose
+  // k-points all have every occupied stick within [-N0/4, N0/4] x
+  // [-N1/4, N1/4] (KF_XY_QUARTER): the y and x lines drop the middle half of
+  // the line at compile time, zero inputs (G -> r, apply) and unneeded outputs
+  // (r -> G, apply), whose arithmetic the compiler removes
+  constexpr bool XQ = (V == 3 || QP) && !TC;
   static_assert(!XS || (LX::PITCH * sizeof(C)) % 16 == 0, "staged rows start on 16-byte boundaries");
   uint64_t* xbar = reinterpret_cast<uint64_t*>(tw1 + N1);
   // end of the layout (8-byte aligned): the slab-plane barrier of single-buffer kernels
@@ -1061,6 +1062,11 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 }
 
 // ---------------------------------------------------------------- dispatch
+// lengths whose default FP32 plane kernels have the line-pruned variant (QP)
+template <typename T, bool TC, int N> constexpr bool qp_variant() {
+  return sizeof(T) == 4 && !TC && (N == 64 || N == 96 || N == 128 || N == 256);
+}
+
 // Launches a stage kernel; with L.pdl the launch allows programmatic
 // dependent launch (every stage kernel starts with pdl_launch_dependents and
 // calls pdl_wait before touching stage data, so neighbours only overlap their
@@ -1134,7 +1140,10 @@ template <typename T, bool TC, int N2> cudaError_t go_stick(int mode, const Laun
   if (mode == M_G2R) return launch_k(k_stick<T, N2, M_G2R, TC>, grid, STICK_NW * 32, smem, L, L);
   return launch_k(k_stick<T, N2, M_R2G, TC>, grid, STICK_NW * 32, smem, L, L);
 }
-template <typename T, bool TC, int N> cudaError_t go_plane(int mode, const Launch& L) {
+template <typename T, bool TC, int N, bool QP = false> cudaError_t go_plane(int mode, const Launch& L) {
+  if constexpr (!QP && qp_variant<T, TC, N>()) {
+    if (L.xq) return go_plane<T, TC, N, true>(mode, L);
+  }
   if constexpr (N >= 128) {
     if (L.a_glob) {  // slab planes too large for shared memory: per-CTA blocks of a global buffer
       const size_t smem = plane_smem_c<T, N, N>(L.g.xmax, L.a_bufs, true);
@@ -1143,9 +1152,9 @@ template <typename T, bool TC, int N> cudaError_t go_plane(int mode, const Launc
       if (ctas < 1) return cudaErrorInvalidValue;
       const dim3 grid(ctas);
       constexpr int NT = PlaneCfg<T>::NW * 32;
-      if (mode == M_G2R) return launch_k(k_plane<T, N, N, M_G2R, TC, true>, grid, NT, smem, L, L);
-      if (mode == M_R2G) return launch_k(k_plane<T, N, N, M_R2G, TC, true>, grid, NT, smem, L, L);
-      return launch_k(k_plane<T, N, N, M_APPLY, TC, true>, grid, NT, smem, L, L);
+      if (mode == M_G2R) return launch_k(k_plane<T, N, N, M_G2R, TC, true, false, 0, QP>, grid, NT, smem, L, L);
+      if (mode == M_R2G) return launch_k(k_plane<T, N, N, M_R2G, TC, true, false, 0, QP>, grid, NT, smem, L, L);
+      return launch_k(k_plane<T, N, N, M_APPLY, TC, true, false, 0, QP>, grid, NT, smem, L, L);
     }
   }
   if (L.a_glob) return cudaErrorInvalidValue;
@@ -1153,9 +1162,9 @@ template <typename T, bool TC, int N> cudaError_t go_plane(int mode, const Launc
   const int nplanes = L.nb * L.g.n2;
   const dim3 grid(L.plane_ctas > 0 ? min(L.plane_ctas, nplanes) : nplanes);
   constexpr int NT = PlaneCfg<T>::NW * 32;
-  if (mode == M_G2R) return launch_k(k_plane<T, N, N, M_G2R, TC>, grid, NT, smem, L, L);
-  if (mode == M_R2G) return launch_k(k_plane<T, N, N, M_R2G, TC>, grid, NT, smem, L, L);
-  return launch_k(k_plane<T, N, N, M_APPLY, TC>, grid, NT, smem, L, L);
+  if (mode == M_G2R) return launch_k(k_plane<T, N, N, M_G2R, TC, false, false, 0, QP>, grid, NT, smem, L, L);
+  if (mode == M_R2G) return launch_k(k_plane<T, N, N, M_R2G, TC, false, false, 0, QP>, grid, NT, smem, L, L);
+  return launch_k(k_plane<T, N, N, M_APPLY, TC, false, false, 0, QP>, grid, NT, smem, L, L);
 }
 template <typename T, bool TC, int N2> cudaError_t prep_stick() {
   const int s = (int)stick_smem_c<T, N2>();
@@ -1164,47 +1173,60 @@ template <typename T, bool TC, int N2> cudaError_t prep_stick() {
     e = raise_smem_limit((const void*)k_stick<T, N2, M_R2G, TC>, s);
   return e;
 }
-template <typename T, bool TC, int N> cudaError_t prep_plane(int xmax, int a_bufs, bool ag) {
+template <typename T, bool TC, int N, bool QP = false> cudaError_t prep_plane(int xmax, int a_bufs, bool ag) {
+  if constexpr (!QP && qp_variant<T, TC, N>()) {
+    cudaError_t e = prep_plane<T, TC, N, true>(xmax, a_bufs, ag);
+    if (e != cudaSuccess) return e;
+  }
   if constexpr (N >= 128) {
     if (ag) {
       const int s = (int)plane_smem_c<T, N, N>(xmax, a_bufs, true);
-      cudaError_t e = raise_smem_limit((const void*)k_plane<T, N, N, M_G2R, TC, true>, s);
+      cudaError_t e = raise_smem_limit((const void*)k_plane<T, N, N, M_G2R, TC, true, false, 0, QP>, s);
       if (e == cudaSuccess)
-        e = raise_smem_limit((const void*)k_plane<T, N, N, M_R2G, TC, true>, s);
+        e = raise_smem_limit((const void*)k_plane<T, N, N, M_R2G, TC, true, false, 0, QP>, s);
       if (e == cudaSuccess)
-        e = raise_smem_limit((const void*)k_plane<T, N, N, M_APPLY, TC, true>, s);
+        e = raise_smem_limit((const void*)k_plane<T, N, N, M_APPLY, TC, true, false, 0, QP>, s);
       return e;
     }
   }
   if (ag) return cudaErrorInvalidValue;
   const int s = (int)plane_smem_c<T, N, N>(xmax, a_bufs);
-  cudaError_t e = raise_smem_limit((const void*)k_plane<T, N, N, M_G2R, TC>, s);
+  cudaError_t e = raise_smem_limit((const void*)k_plane<T, N, N, M_G2R, TC, false, false, 0, QP>, s);
   if (e == cudaSuccess)
-    e = raise_smem_limit((const void*)k_plane<T, N, N, M_R2G, TC>, s);
+    e = raise_smem_limit((const void*)k_plane<T, N, N, M_R2G, TC, false, false, 0, QP>, s);
   if (e == cudaSuccess)
-    e = raise_smem_limit((const void*)k_plane<T, N, N, M_APPLY, TC>, s);
+    e = raise_smem_limit((const void*)k_plane<T, N, N, M_APPLY, TC, false, false, 0, QP>, s);
   return e;
 }
 
-template <typename T, bool TC, int N> int occ_plane(int mode, int xmax, int a_bufs, bool ag) {
+template <typename T, bool TC, int N, bool QP = false> int occ_plane(int mode, int xmax, int a_bufs, bool ag) {
   constexpr int NT = PlaneCfg<T>::NW * 32;
   int nb = 0;
   cudaError_t e;
+  // the line-pruned variant must be resident the same way (the plan sizes one grid for both)
+  int nq = 1 << 30;
+  if constexpr (!QP && qp_variant<T, TC, N>()) nq = occ_plane<T, TC, N, true>(mode, xmax, a_bufs, ag);
   if constexpr (N >= 128) {
     if (ag) {
       const size_t sm = plane_smem_c<T, N, N>(xmax, a_bufs, true);
-      if (mode == M_G2R) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_G2R, TC, true>, NT, sm);
-      else if (mode == M_R2G) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_R2G, TC, true>, NT, sm);
-      else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_APPLY, TC, true>, NT, sm);
-      return e == cudaSuccess ? nb : 0;
+      if (mode == M_G2R)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_G2R, TC, true, false, 0, QP>, NT, sm);
+      else if (mode == M_R2G)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_R2G, TC, true, false, 0, QP>, NT, sm);
+      else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_APPLY, TC, true, false, 0, QP>, NT, sm);
+      return e == cudaSuccess ? min(nb, nq) : 0;
     }
   }
   if (ag) return 0;
   const size_t smem = plane_smem_c<T, N, N>(xmax, a_bufs);
-  if (mode == M_G2R) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_G2R, TC>, NT, smem);
-  else if (mode == M_R2G) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_R2G, TC>, NT, smem);
-  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_APPLY, TC>, NT, smem);
-  return e == cudaSuccess ? nb : 0;
+  if (mode == M_G2R)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_G2R, TC, false, false, 0, QP>, NT, smem);
+  else if (mode == M_R2G)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_R2G, TC, false, false, 0, QP>, NT, smem);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_plane<T, N, N, M_APPLY, TC, false, false, 0, QP>, NT, smem);
+  return e == cudaSuccess ? min(nb, nq) : 0;
 }
 template <typename T, bool TC, int N2> int occ_stick() {
   int nb = 0;
