@@ -12,28 +12,31 @@ namespace {
 #define FFTB_ALT_SIZES(X) X(64) X(96) X(128) X(160)
 
 // schedule variant of the alternative plane kernels (160: the two-pass
-// schedule, and its variant 3 that drops the middle half of each x line for
-// launches whose k-points all have every occupied x within [-N/4, N/4])
+// schedule), and of their line-pruned versions for launches whose k-points
+// all have every occupied stick within a quarter of the grid (160: variant 3;
+// the others: the same schedule with QP)
 template <int N> constexpr int plane_v() { return N == 160 ? 2 : 1; }
 template <int N> constexpr int plane_vq() { return N == 160 ? 3 : plane_v<N>(); }
+template <int N> constexpr bool plane_qp() { return N != 160; }
 
-template <int N, int MODE, int V = plane_v<N>()> const void* plane_fn() {
-  return (const void*)k_plane<float, N, N, MODE, false, false, false, V>;
+template <int N, int MODE, bool Q = false> const void* plane_fn() {
+  if constexpr (Q) return (const void*)k_plane<float, N, N, MODE, false, false, false, plane_vq<N>(), plane_qp<N>()>;
+  else return (const void*)k_plane<float, N, N, MODE, false, false, false, plane_v<N>()>;
 }
 template <int N, int MODE> const void* stick_fn() { return (const void*)k_stick<float, N, MODE, false, 1>; }
 
-template <int N, int V> cudaError_t go_plane_vv(int mode, const Launch& L) {
+template <int N, int V, bool QP> cudaError_t go_plane_vv(int mode, const Launch& L) {
   const size_t smem = plane_smem_c<float, N, N, V>(L.g.xmax, L.a_bufs);
   const int nplanes = L.nb * L.g.n2;
   const dim3 grid(L.plane_ctas > 0 ? min(L.plane_ctas, nplanes) : nplanes);
   constexpr int NT = PlaneCfg<float>::NW * 32;
-  if (mode == M_G2R) return launch_k(k_plane<float, N, N, M_G2R, false, false, false, V>, grid, NT, smem, L, L);
-  if (mode == M_R2G) return launch_k(k_plane<float, N, N, M_R2G, false, false, false, V>, grid, NT, smem, L, L);
-  return launch_k(k_plane<float, N, N, M_APPLY, false, false, false, V>, grid, NT, smem, L, L);
+  if (mode == M_G2R) return launch_k(k_plane<float, N, N, M_G2R, false, false, false, V, QP>, grid, NT, smem, L, L);
+  if (mode == M_R2G) return launch_k(k_plane<float, N, N, M_R2G, false, false, false, V, QP>, grid, NT, smem, L, L);
+  return launch_k(k_plane<float, N, N, M_APPLY, false, false, false, V, QP>, grid, NT, smem, L, L);
 }
 template <int N> cudaError_t go_plane_v(int mode, const Launch& L) {
-  if (L.xq && plane_vq<N>() != plane_v<N>()) return go_plane_vv<N, plane_vq<N>()>(mode, L);
-  return go_plane_vv<N, plane_v<N>()>(mode, L);
+  if (L.xq) return go_plane_vv<N, plane_vq<N>(), plane_qp<N>()>(mode, L);
+  return go_plane_vv<N, plane_v<N>(), false>(mode, L);
 }
 template <int N> cudaError_t go_stick_v(int mode, const Launch& L, int ctas) {
   constexpr int WZ = 32 / Line<N, 1>::G;
@@ -49,12 +52,10 @@ template <int N> cudaError_t prep_plane_v(int xmax, int a_bufs) {
   cudaError_t e = raise_smem_limit(plane_fn<N, M_G2R>(), s);
   if (e == cudaSuccess) e = raise_smem_limit(plane_fn<N, M_R2G>(), s);
   if (e == cudaSuccess) e = raise_smem_limit(plane_fn<N, M_APPLY>(), s);
-  if (plane_vq<N>() != plane_v<N>()) {
-    const int sq = (int)plane_smem_c<float, N, N, plane_vq<N>()>(xmax, a_bufs);
-    if (e == cudaSuccess) e = raise_smem_limit(plane_fn<N, M_G2R, plane_vq<N>()>(), sq);
-    if (e == cudaSuccess) e = raise_smem_limit(plane_fn<N, M_R2G, plane_vq<N>()>(), sq);
-    if (e == cudaSuccess) e = raise_smem_limit(plane_fn<N, M_APPLY, plane_vq<N>()>(), sq);
-  }
+  const int sq = (int)plane_smem_c<float, N, N, plane_vq<N>()>(xmax, a_bufs);
+  if (e == cudaSuccess) e = raise_smem_limit(plane_fn<N, M_G2R, true>(), sq);
+  if (e == cudaSuccess) e = raise_smem_limit(plane_fn<N, M_R2G, true>(), sq);
+  if (e == cudaSuccess) e = raise_smem_limit(plane_fn<N, M_APPLY, true>(), sq);
   return e;
 }
 template <int N> cudaError_t prep_stick_v() {
@@ -68,10 +69,10 @@ template <int N> int occ_plane_v(int mode, int xmax, int a_bufs) {
   const void* fn = mode == M_G2R ? plane_fn<N, M_G2R>() : mode == M_R2G ? plane_fn<N, M_R2G>() : plane_fn<N, M_APPLY>();
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, PlaneCfg<float>::NW * 32, s) != cudaSuccess) return 0;
-  if (plane_vq<N>() != plane_v<N>()) {  // the variant must be resident the same way
-    const void* fq = mode == M_G2R   ? plane_fn<N, M_G2R, plane_vq<N>()>()
-                     : mode == M_R2G ? plane_fn<N, M_R2G, plane_vq<N>()>()
-                                     : plane_fn<N, M_APPLY, plane_vq<N>()>();
+  {  // the line-pruned variant must be resident the same way
+    const void* fq = mode == M_G2R   ? plane_fn<N, M_G2R, true>()
+                     : mode == M_R2G ? plane_fn<N, M_R2G, true>()
+                                     : plane_fn<N, M_APPLY, true>();
     int nq = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nq, fq, PlaneCfg<float>::NW * 32, s) != cudaSuccess) return 0;
     nb = std::min(nb, nq);
