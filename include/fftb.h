@@ -150,6 +150,11 @@ typedef struct {
                               (FP32, 256-point planes)                               */
   /* slab_planes_global above is 1 while a stage the direction uses keeps its
      slab planes in global memory. */
+  int32_t pruned_lines;       /* stages that run the kernel variants dropping the middle
+                              half of every line at compile time (every k-point's
+                              sphere within a quarter of the grid per axis, as with
+                              cube width = twice the sphere diameter): bit 0 the z
+                              stages, bit 1 the plane stages (FP32 kernels)          */
 } fftb_plan_info_t;
 
 /* Builds the spheres, stick/slab tables and twiddles on the host, uploads

@@ -822,6 +822,13 @@ FFTB_EXPORT fftb_status fftb_plan_get_info(fftb_plan p, fftb_plan_info_t* info) 
   const int used = p->dir == FFTB_G_TO_R ? 1 : p->dir == FFTB_R_TO_G ? 2 : p->dir == FFTB_APPLY_LOCAL ? 4 : 3;
   info->slab_planes_global = p->a_glob && (p->cl & used) != used ? 1 : 0;
   info->plane_clusters = p->cl | (p->cl_ok ? 8 : 0);
+  {
+    const int n = p->n[0];
+    const bool z = !p->generic && p->zq_all && p->stick_prec == P_F32 && !p->sched_stick;
+    const bool planes = !p->generic && p->xq_all && p->prec_kernel == P_F32 && !p->tc5 && (p->cl & used) == 0 &&
+                        (n == 64 || n == 96 || n == 128 || n == 256 || (n == 160 && p->sched_plane));
+    info->pruned_lines = (z ? 1 : 0) | (planes ? 2 : 0);
+  }
   info->tensor_core_planes = p->tc5 ? 3 : 0;
   info->radix_schedule_plane = p->sched_plane;
   info->radix_schedule_stick = p->sched_stick;

@@ -51,7 +51,10 @@ template <int N, int BG> size_t bg_smem(int xmax) {
   return sizeof(float2) * ((size_t)BG * bg_abuf(N, xmax) + (size_t)BG_NW * SCR + N);
 }
 
-template <int N, int MODE, int BG>
+// QP: every k-point's sticks lie within a quarter of the grid per axis
+// (KF_XY_QUARTER for all of the plan's k-points): the middle half of every y
+// and x line is dropped at compile time, as in the band-major kernels.
+template <int N, int MODE, int BG, bool QP = false>
 __global__ void __launch_bounds__(BG_NW * 32, (bg_minb<N>())) k_plane_bg(const Launch L) {
   using C = float2;
   using LN = Line<N>;
@@ -137,6 +140,10 @@ __global__ void __launch_bounds__(BG_NW * 32, (bg_minb<N>())) k_plane_bg(const L
           for (int m = 0; m < E / LN::R0; ++m)
 #pragma unroll
             for (int j2 = 0; j2 < LN::R0; ++j2) {
+              if (QP && x_mid<N, LN::G, LN::R0>(m * LN::R0 + j2)) {  // no occupied y there
+                v[m * LN::R0 + j2] = czero<C>();
+                continue;
+              }
               const int d = ysigned(LN::first_pos(g, m, j2)) - ylo;
               v[m * LN::R0 + j2] = (unsigned)d < (unsigned)len ? Tz[sa + d] : czero<C>();
             }
@@ -153,7 +160,9 @@ __global__ void __launch_bounds__(BG_NW * 32, (bg_minb<N>())) k_plane_bg(const L
 #pragma unroll
           for (int m = 0; m < E / LN::R0; ++m)
 #pragma unroll
-            for (int j2 = 0; j2 < LN::R0; ++j2) v[m * LN::R0 + j2] = lrow[wpad(LN::first_pos(g, m, j2))];
+            for (int j2 = 0; j2 < LN::R0; ++j2)
+              v[m * LN::R0 + j2] = QP && x_mid<N, LN::G, LN::R0>(m * LN::R0 + j2) ? czero<C>()  // no stick there
+                                                                                 : lrow[wpad(LN::first_pos(g, m, j2))];
           __syncwarp();
         }
         LN::template run<+1>(v, g, lrow, tw, tc);
@@ -176,6 +185,7 @@ __global__ void __launch_bounds__(BG_NW * 32, (bg_minb<N>())) k_plane_bg(const L
             for (int m = 0; m < E / LN::RL; ++m)
 #pragma unroll
               for (int j2 = 0; j2 < LN::RL; ++j2) {
+                if (QP && x_mid<N, LN::G, LN::RL>(m * LN::RL + j2)) continue;  // no occupied y there
                 const int d = ysigned(LN::last_pos(g, m, j2)) - ylo;
                 if ((unsigned)d < (unsigned)len) Tz[sa + d] = v[m * LN::RL + j2];
               }
@@ -184,7 +194,10 @@ __global__ void __launch_bounds__(BG_NW * 32, (bg_minb<N>())) k_plane_bg(const L
 #pragma unroll
           for (int m = 0; m < E / LN::RL; ++m)
 #pragma unroll
-            for (int j2 = 0; j2 < LN::RL; ++j2) lrow[wpad(LN::last_pos(g, m, j2))] = v[m * LN::RL + j2];
+            for (int j2 = 0; j2 < LN::RL; ++j2) {
+              if (QP && x_mid<N, LN::G, LN::RL>(m * LN::RL + j2)) continue;  // no stick there
+              lrow[wpad(LN::last_pos(g, m, j2))] = v[m * LN::RL + j2];
+            }
           __syncwarp();
           const int sbeg = __shfl_sync(0xffffffffu, ci.x, 0);
           const int send = __shfl_sync(0xffffffffu, ci.x + ci.y, (nl - 1) * LN::G);
@@ -210,6 +223,10 @@ __global__ void __launch_bounds__(BG_NW * 32, (bg_minb<N>())) k_plane_bg(const L
         C v[E];
 #pragma unroll
         for (int q = 0; q < E; ++q) {
+          if (QP && x_mid<N, LN::G, LN::R0>(q)) {  // no occupied x there
+            v[q] = czero<C>();
+            continue;
+          }
           const int xi = xin.get(q);
           v[q] = (live && xi != 255) ? A[xi] : czero<C>();
         }
@@ -241,6 +258,7 @@ __global__ void __launch_bounds__(BG_NW * 32, (bg_minb<N>())) k_plane_bg(const L
           C* A = A0 + xj * abuf + row * XP;
 #pragma unroll
           for (int q = 0; q < E; ++q) {
+            if (QP && x_mid<N, LN::G, LN::RL>(q)) continue;  // no occupied x there
             const int xi = xout.get(q);
             if (xi != 255) A[xi] = v[q];
           }
@@ -254,23 +272,56 @@ __global__ void __launch_bounds__(BG_NW * 32, (bg_minb<N>())) k_plane_bg(const L
   }
 }
 
-template <int N, int BG> const void* bg_fn(int mode) {
-  return mode == M_G2R ? (const void*)k_plane_bg<N, M_G2R, BG> : (const void*)k_plane_bg<N, M_R2G, BG>;
+template <int N> constexpr bool bg_qp() { return N == 64 || N == 96 || N == 128; }
+template <int N, int BG, bool QP = false> const void* bg_fn(int mode) {
+  return mode == M_G2R ? (const void*)k_plane_bg<N, M_G2R, BG, QP> : (const void*)k_plane_bg<N, M_R2G, BG, QP>;
 }
-template <int N, int BG> cudaError_t go_bg(int mode, const Launch& L) {
+template <int N, int BG, bool QP = false> cudaError_t go_bg(int mode, const Launch& L) {
+  if constexpr (!QP && bg_qp<N>()) {
+    if (L.xq) return go_bg<N, BG, true>(mode, L);
+  }
   const size_t smem = bg_smem<N, BG>(L.g.xmax);
   const int units = L.ngrp * L.g.n2;
   const dim3 grid(L.plane_ctas > 0 ? min(L.plane_ctas, units) : units);
   constexpr int NT = BG_NW * 32;
-  if (mode == M_G2R) return launch_k(k_plane_bg<N, M_G2R, BG>, grid, NT, smem, L, L);
-  return launch_k(k_plane_bg<N, M_R2G, BG>, grid, NT, smem, L, L);
+  if (mode == M_G2R) return launch_k(k_plane_bg<N, M_G2R, BG, QP>, grid, NT, smem, L, L);
+  return launch_k(k_plane_bg<N, M_R2G, BG, QP>, grid, NT, smem, L, L);
 }
+
+template <int N> cudaError_t prep_bg(int xmax);
+template <int N> int occ_bg(int mode, int xmax);
 
 // the band group of each length: 4 (a full 32-byte sector of FP32 complex) up
 // to 96 points, 2 above, where four slab planes no longer fit shared memory
 template <int N> __host__ __device__ constexpr int bg_of() { return (N <= 96 && bg_wx<N>() % 4 == 0) ? 4 : 2; }
 
 #define FFTB_BG_SIZES(X) X(12) X(16) X(20) X(24) X(32) X(40) X(48) X(64) X(96) X(128) X(160) X(256)
+
+template <int N> cudaError_t prep_bg(int xmax) {
+  const int s = (int)bg_smem<N, bg_of<N>()>(xmax);
+  cudaError_t e = raise_smem_limit(bg_fn<N, bg_of<N>()>(M_G2R), s);
+  if (e == cudaSuccess) e = raise_smem_limit(bg_fn<N, bg_of<N>()>(M_R2G), s);
+  if constexpr (bg_qp<N>()) {
+    if (e == cudaSuccess) e = raise_smem_limit(bg_fn<N, bg_of<N>(), true>(M_G2R), s);
+    if (e == cudaSuccess) e = raise_smem_limit(bg_fn<N, bg_of<N>(), true>(M_R2G), s);
+  }
+  return e;
+}
+// resident CTAs per SM, the line-pruned variant included (the plan sizes one grid for both)
+template <int N> int occ_bg(int mode, int xmax) {
+  const size_t s = bg_smem<N, bg_of<N>()>(xmax);
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bg_fn<N, bg_of<N>()>(mode), BG_NW * 32, s) != cudaSuccess)
+    return 0;
+  if constexpr (bg_qp<N>()) {
+    int nq = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nq, bg_fn<N, bg_of<N>(), true>(mode), BG_NW * 32, s) !=
+        cudaSuccess)
+      return 0;
+    nb = nb < nq ? nb : nq;
+  }
+  return nb;
+}
 
 }  // namespace
 
@@ -295,12 +346,7 @@ size_t plane_bg_smem(int n0, int n1, int xmax, int bg) {
 
 cudaError_t prepare_plane_bg(int n, int xmax) {
   switch (n) {
-#define C_(N)                                                                                 \
-  case N: {                                                                                   \
-    const int s = (int)bg_smem<N, bg_of<N>()>(xmax);                                          \
-    cudaError_t e = raise_smem_limit(bg_fn<N, bg_of<N>()>(M_G2R), s);                         \
-    return e == cudaSuccess ? raise_smem_limit(bg_fn<N, bg_of<N>()>(M_R2G), s) : e;           \
-  }
+#define C_(N) case N: return prep_bg<N>(xmax);
     FFTB_BG_SIZES(C_)
 #undef C_
   }
@@ -308,15 +354,8 @@ cudaError_t prepare_plane_bg(int n, int xmax) {
 }
 
 int plane_bg_occupancy(int mode, int n, int xmax) {
-  int nb = 0;
   switch (n) {
-#define C_(N)                                                                                          \
-  case N:                                                                                              \
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bg_fn<N, bg_of<N>()>(mode),              \
-                                                         BG_NW * 32,                                   \
-                                                         bg_smem<N, bg_of<N>()>(xmax)) == cudaSuccess \
-               ? nb                                                                                    \
-               : 0;
+#define C_(N) case N: return occ_bg<N>(mode, xmax);
     FFTB_BG_SIZES(C_)
 #undef C_
   }

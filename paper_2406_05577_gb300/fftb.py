@@ -71,6 +71,7 @@ class fftb_plan_info_t(ctypes.Structure):
         ("tensor_core_passes", ctypes.c_int32),
         ("tensor_cores_available", ctypes.c_int32),
         ("plane_clusters", ctypes.c_int32),
+        ("pruned_lines", ctypes.c_int32),
     ]
 
 

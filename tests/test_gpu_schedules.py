@@ -218,6 +218,7 @@ def test_160_two_pass_quarter_x_pruning(F, r):
     plan.set_radix_schedule(1, 0)
     g = plan.sphere(0)
     assert (np.abs(g[:, 0]).max() <= 40) == (r == 40.0)
+    assert plan.info["pruned_lines"] == (3 if r == 40.0 else 0)  # z stages, plane stages
     c = fi.complex_gaussian((bands, len(g)), 121).astype(np.complex64)
     c64 = c.astype(np.complex128)
     x = torch.from_numpy(c.reshape(-1)).cuda()
