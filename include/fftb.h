@@ -215,7 +215,9 @@ fftb_status fftb_execute(fftb_plan plan, const void* in_dev, void* out_dev,
  * the copy in of one piece, the transform of the previous one and the copy
  * out of the one before that overlap: band-major plans cut the batch into
  * about (bands x N2) / 8192 pieces, at least 2 and at most 16 (never more
- * than the bands); batch-fastest plans split only at k-point boundaries, and
+ * than the bands), the first and the last of about 2048 (band, z) planes
+ * where the batch holds at least 32768 (their copy in and copy out are the
+ * ones left exposed); batch-fastest plans split only at k-point boundaries, and
  * a single k-point goes in one piece. The call is ordered
  * after earlier work on `stream` and returns when all of it is done. The
  * staging buffers and streams are created on the first call and kept with

@@ -1187,8 +1187,9 @@ FFTB_EXPORT fftb_status fftb_execute_host(fftb_plan p, const void* in_host, void
   // the copy out of piece i - 1 overlap the transform of piece i, so only the
   // first piece's copy in and the last piece's copy out are exposed. Band-major
   // batches split into pieces of about 8192 (band, z) planes, at least two and
-  // at most 16 (a piece's launches stay large enough to fill the GPU: on the
-  // 64^3 x 64 workload this is two pieces, which measured best there; kernels
+  // at most 16, with a first and a last piece of about 2048 planes where the
+  // batch holds at least 32768 (a piece's launches stay large enough to fill
+  // the GPU: on the 64^3 x 64 workload this is two pieces, which measured best there; kernels
   // reading or writing page-locked host memory directly over the CPU-GPU link
   // measured slower than the copies). A batch-fastest piece must be whole
   // k-points (a band range of one k-point is not contiguous there): split at
@@ -1204,10 +1205,19 @@ FFTB_EXPORT fftb_status fftb_execute_host(fftb_plan p, const void* in_host, void
     }
     bounds = best > 0 ? std::vector<int>{0, best, p->total_bands} : std::vector<int>{0, p->total_bands};
   } else {
-    const int64_t planes = (int64_t)p->total_bands * p->n[2];
-    int np = (int)std::max<int64_t>(2, std::min<int64_t>(16, planes / 8192));
-    np = std::max(1, std::min(np, p->total_bands));
-    for (int i = 0; i <= np; ++i) bounds.push_back((int)((int64_t)p->total_bands * i / np));
+    // the first and the last piece (whose copy in and copy out are the exposed
+    // ones) about 2048 planes where the batch is large enough, the pieces
+    // between them about 8192
+    const int edge = (2048 + p->n[2] - 1) / p->n[2];
+    const int nb = p->total_bands;
+    const bool edges = nb >= 4 * edge && (int64_t)nb * p->n[2] >= 4 * 8192;
+    const int b0 = edges ? edge : 0, b1 = edges ? nb - edge : nb;
+    const int64_t planes = (int64_t)(b1 - b0) * p->n[2];
+    int np = (int)std::max<int64_t>(edges ? 1 : 2, std::min<int64_t>(16, planes / 8192));
+    np = std::max(1, std::min(np, b1 - b0));
+    if (edges) bounds.push_back(0);
+    for (int i = 0; i <= np; ++i) bounds.push_back(b0 + (int)((int64_t)(b1 - b0) * i / np));
+    if (edges) bounds.push_back(nb);
   }
   const int pieces = (int)bounds.size() - 1;
   if (!p->hs[0]) {
