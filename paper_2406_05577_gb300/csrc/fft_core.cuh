@@ -298,6 +298,87 @@ template <int A, int B, int S, typename C> __device__ __forceinline__ void dft_c
   }
 }
 
+// ----------------------------------------------- inputs known to be zero
+// The same transforms when some inputs are zero at compile time (bit i of Z:
+// input i is zero), for lines that carry fewer values than their length: a
+// sum or difference with a known zero is not computed. The results equal the
+// general codelets' (up to the sign of zero results).
+template <bool ZA, bool ZB, typename C> __device__ __forceinline__ C zadd(C a, C b) {
+  if constexpr (ZA && ZB) return czero<C>();
+  else if constexpr (ZA) return b;
+  else if constexpr (ZB) return a;
+  else return a + b;
+}
+template <bool ZA, bool ZB, typename C> __device__ __forceinline__ C zsub(C a, C b) {
+  if constexpr (ZA && ZB) return czero<C>();
+  else if constexpr (ZA) return mk(-b.x, -b.y);
+  else if constexpr (ZB) return a;
+  else return a - b;
+}
+template <int S, unsigned Z, typename C> __device__ __forceinline__ void dft4_z(C& x0, C& x1, C& x2, C& x3) {
+  constexpr bool Z0 = Z & 1, Z1 = (Z >> 1) & 1, Z2 = (Z >> 2) & 1, Z3 = (Z >> 3) & 1;
+  constexpr bool T02 = Z0 && Z2, T13 = Z1 && Z3;
+  const C t0 = zadd<Z0, Z2>(x0, x2), t1 = zsub<Z0, Z2>(x0, x2);
+  const C t2 = zadd<Z1, Z3>(x1, x3), t3 = mulj<S>(zsub<Z1, Z3>(x1, x3));
+  x0 = zadd<T02, T13>(t0, t2);
+  x2 = zsub<T02, T13>(t0, t2);
+  x1 = zadd<T02, T13>(t1, t3);
+  x3 = zsub<T02, T13>(t1, t3);
+}
+// radix 8 as dft8: DFT4 of the even and of the odd inputs, twiddles, radix 2
+template <int S, unsigned Z, typename C> __device__ __forceinline__ void dft8_z(C* v) {
+  using T = decltype(C::x);
+  constexpr unsigned ZE = (Z & 1) | ((Z >> 1) & 2) | ((Z >> 2) & 4) | ((Z >> 3) & 8);           // inputs 0 2 4 6
+  constexpr unsigned ZO = ((Z >> 1) & 1) | ((Z >> 2) & 2) | ((Z >> 3) & 4) | ((Z >> 4) & 8);    // inputs 1 3 5 7
+  constexpr bool EZ = ZE == 15, OZ = ZO == 15;
+  const T h = T(0.70710678118654752440084436);  // 1/sqrt(2)
+  C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4_z<S, ZE>(e0, e1, e2, e3);
+  dft4_z<S, ZO>(o0, o1, o2, o3);
+  if constexpr (!OZ) {
+    o1 = scale(o1 + mulj<S>(o1), h);
+    o2 = mulj<S>(o2);
+    o3 = scale(mulj<S>(o3) - o3, h);
+  }
+  v[0] = zadd<EZ, OZ>(e0, o0); v[4] = zsub<EZ, OZ>(e0, o0);
+  v[1] = zadd<EZ, OZ>(e1, o1); v[5] = zsub<EZ, OZ>(e1, o1);
+  v[2] = zadd<EZ, OZ>(e2, o2); v[6] = zsub<EZ, OZ>(e2, o2);
+  v[3] = zadd<EZ, OZ>(e3, o3); v[7] = zsub<EZ, OZ>(e3, o3);
+}
+// bits of Z at the inputs B n1 + n2 of the DFT-A over n1 (the composite's first stage)
+template <int A, int B> __host__ __device__ constexpr unsigned ct_sub_mask(unsigned long long Z, int n2) {
+  unsigned m = 0;
+  for (int n1 = 0; n1 < A; ++n1) m |= (unsigned)((Z >> (B * n1 + n2)) & 1ull) << n1;
+  return m;
+}
+template <int A, int B, int S, unsigned long long Z, int N2I, typename C>
+__device__ __forceinline__ void ct_stage1_z(C (&y)[B][A], const C* v) {
+  if constexpr (N2I < B) {
+#pragma unroll
+    for (int n1 = 0; n1 < A; ++n1) y[N2I][n1] = v[B * n1 + N2I];
+    constexpr unsigned m = ct_sub_mask<A, B>(Z, N2I);
+    static_assert(A == 8, "zero-aware first stage of radix 8");
+    dft8_z<S, m>(y[N2I]);
+    ct_stage1_z<A, B, S, Z, N2I + 1>(y, v);
+  }
+}
+// composite radix A * B (dft_ct) with the inputs of Z known to be zero
+template <int A, int B, int S, unsigned long long Z, typename C> __device__ __forceinline__ void dft_ct_z(C* v) {
+  C y[B][A];
+  ct_stage1_z<A, B, S, Z, 0>(y, v);
+  ct_twiddle<A, B, S, 0>(y);
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) {
+    C t[B];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) t[n2] = y[n2][k1];
+    dft<B, S>(t);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = t[k2];
+  }
+}
+
 template <int R, int S, typename C> __device__ __forceinline__ void dft(C* v) {
   if constexpr (R == 2) dft2<S>(v[0], v[1]);
   else if constexpr (R == 3) dft3<S>(v[0], v[1], v[2]);
@@ -313,6 +394,14 @@ template <int R, int S, typename C> __device__ __forceinline__ void dft(C* v) {
   else if constexpr (R == 32) dft_ct<8, 4, S>(v);
   else if constexpr (R == 40) dft_ct<8, 5, S>(v);
   else static_assert(R == 2, "unsupported radix");
+}
+// radix R with the inputs of Z zero at compile time (zero-aware for 4, 8 and 40 = 8 x 5)
+template <int R, int S, unsigned long long Z, typename C> __device__ __forceinline__ void dft_z(C* v) {
+  if constexpr (Z == 0) dft<R, S>(v);
+  else if constexpr (R == 4) dft4_z<S, (unsigned)Z>(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 8) dft8_z<S, (unsigned)Z>(v);
+  else if constexpr (R == 40) dft_ct_z<8, 5, S, Z>(v);
+  else dft<R, S>(v);
 }
 
 // ------------------------------------------------------- exchange rows

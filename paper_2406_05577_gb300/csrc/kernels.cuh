@@ -41,6 +41,16 @@ template <int N, int G, int R> __host__ __device__ constexpr bool x_mid(int q) {
   return (q / R) * G + (q % R) * (N / R) > N / 4 && (q / R) * G + (q % R) * (N / R) + G - 1 < N - N / 4;
 }
 
+// the first-pass inputs of a length-N line (E per lane) that are zero when
+// every occupied position is within [-N/4, N/4], as a bit mask for Line::run
+template <int N, int G, int R, int E> __host__ __device__ constexpr unsigned long long mid_mask() {
+  unsigned long long m = 0;
+  if (E > 64) return 0;
+  for (int q = 0; q < E; ++q)
+    if (x_mid<N, G, R>(q)) m |= 1ull << q;
+  return m;
+}
+
 // ------------------------------------------------------------------ z stage
 // Each occupied (x,y) stick is one length-N2 line held in registers by
 // Line<N2>::G lanes; a warp carries 32 / G consecutive sticks, a CTA 8 warps.
@@ -191,7 +201,7 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
   auto finish = [&](const Task& k, C (&v)[EZ]) {
     if constexpr (MODE == M_G2R) {
       if constexpr (TC) LZ::template run_tc<+1>(v, g, row, scr, tw, tc, tcw);
-      else LZ::template run<+1>(v, g, row, tw, tc);
+      else LZ::template run<+1, QZ ? mid_mask<N2, LZ::G, LZ::R0, EZ>() : 0ull>(v, g, row, tw, tc);
       if (l < k.nl) {
         const size_t tb = (size_t)k.bl * N2 * smax + k.s0 + l;
         C* Tb = static_cast<C*>(L.T) + tb;
@@ -328,6 +338,10 @@ template <bool EF, typename C> __device__ __forceinline__ void st_once(C* p, C v
   if constexpr (EF) __stcs(p, v);
   else *p = v;
 }
+// two adjacent FP32 complex values as one 16-byte store (p on a 16-byte boundary)
+__device__ __forceinline__ void st_pair(float2* p, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
 // resident CTAs per SM the register allocation must allow (measured best)
 template <typename T, int N0> __host__ __device__ constexpr int plane_minb() {
 #ifdef FFTB_PLANE_MINB
@@ -407,11 +421,14 @@ template <typename T, int N0, int N1, int MODE, bool TC = false, bool AG = false
 __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k_plane(const Launch L) {
   using C = typename cplx<T>::type;
   using LY = Line<N1, V>;
-  using LX = Line<N0, V>;
+  // G -> r with the two-pass schedule (FP32): the x lines take the paired
+  // variant, whose outputs leave as 16-byte pairs
+  using LX = Line<N0, ((V == 2 || V == 3) && MODE == M_G2R && sizeof(T) == 4 && N0 == 160 && !TC && !AG && !PF) ? 4 : V>;
   constexpr int NW = PlaneCfg<T>::NW, NT = NW * 32;
   constexpr int WY = 32 / LY::G, WX = 32 / LX::G;   // lines per warp
   constexpr int EY = LY::E, EX = LX::E;
   constexpr int SCR = plane_scratch<N0, N1, V>();
+  static_assert(WX * LX::PITCH <= SCR && WY * LY::PITCH <= SCR, "lines' exchange rows fit the warp's scratch");
   extern __shared__ __align__(16) unsigned char smem_raw[];
 
   const int n2 = L.g.n2;
@@ -419,6 +436,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   const int gy = lane % LY::G, ly = lane / LY::G;
   const int gx = lane % LX::G, lx = lane / LX::G;
   constexpr int AR = a_res<C, N0, N1, V>();
+  static_assert(!LX::PAIR || (AR % 2 == 0 && SCR % 2 == 0 && LX::PITCH % 2 == 0),
+                "paired exchange rows start on 16-byte boundaries");
   const int abuf = N1 * a_pitch(L.g.xmax, AR);
   const int nbuf = L.a_bufs;
   // slab planes: shared memory, or (AG) this CTA's block of a global buffer
@@ -451,6 +470,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   // the line at compile time, zero inputs (G -> r, apply) and unneeded outputs
   // (r -> G, apply), whose arithmetic the compiler removes
   constexpr bool XQ = (V == 3 || QP) && !TC;
+  constexpr unsigned long long ZMX = XQ ? mid_mask<N0, LX::G, LX::R0, EX>() : 0ull;  // zero x inputs (G -> r)
+  constexpr unsigned long long ZMY = XQ ? mid_mask<N1, LY::G, LY::R0, EY>() : 0ull;  // zero y inputs (G -> r)
   static_assert(!XS || (LX::PITCH * sizeof(C)) % 16 == 0, "staged rows start on 16-byte boundaries");
   uint64_t* xbar = reinterpret_cast<uint64_t*>(tw1 + N1);
   // end of the layout (8-byte aligned): the slab-plane barrier of single-buffer kernels
@@ -496,6 +517,8 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
     if constexpr (MODE != M_R2G) { wy_p.load(tw1); wx_p.load(tw0); }
     if constexpr (MODE != M_G2R) { wy_m.load(tw1); wx_m.load(tw0); }
   }
+  // the paired x schedule's 16-byte cube stores need a cube on 16-byte boundaries (uniform)
+  const bool pair16 = LX::PAIR && (reinterpret_cast<uintptr_t>(L.cube_out) % 16) == 0;
   // signed y of this lane's first-pass / last-pass y positions (direct stick I/O)
   auto ysigned = [](int y) { return y < N1 - N1 / 2 ? y : y - N1; };
 
@@ -774,13 +797,13 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
         if constexpr (TC) LY::template run_tc<+1>(v, gy, rowy, scr, tw1, tcy, wy_p);
         else if constexpr (YS) {
           // once the exchange rows have been read back, fetch the next y task's sticks into them
-          LY::template run2<+1>(v, gy, rowy, tw1, tcy, [] {}, [&] {
+          LY::template run2<+1, ZMY>(v, gy, rowy, tw1, tcy, [] {}, [&] {
             if ((ki.flags & KF_CONTIGUOUS_COLUMNS) && !bad && t + NW < ty) {
               if (lane == 0) issue_ycols(p, t + NW);
               xpend = true;
             }
           });
-        } else LY::template run<+1>(v, gy, rowy, tw1, tcy);
+        } else LY::template run<+1, ZMY>(v, gy, rowy, tw1, tcy);
         a_acquire();
         if (ly < nl) {
 #pragma unroll
@@ -830,19 +853,33 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
         if constexpr (TC) LX::template run_tc<+1>(v, gx, rowx, scr, tw0, tcx, wx_p);
         else if constexpr (YS) {
           // after the last exchange of this warp's x phase: the next plane's first y task
-          LX::template run2<+1>(v, gx, rowx, tw0, tcx, [] {}, [&] {
+          LX::template run2<+1, ZMX>(v, gx, rowx, tw0, tcx, [] {}, [&] {
             if (t + NW >= tx) ys_issue_first(p + gridDim.x, false);
           });
-        } else LX::template run<+1>(v, gx, rowx, tw0, tcx);
+        } else LX::template run<+1, ZMX>(v, gx, rowx, tw0, tcx);
         if constexpr (MODE == M_G2R) {
           if (live && cst == 1) {
             C* out = static_cast<C*>(L.cube_out) + plane + (size_t)row * N0;
+            bool done = false;
+            if constexpr (LX::PAIR) {
+              if (pair16) {  // the paired schedule's (x, x + 1) as 16-byte stores
 #pragma unroll
-            for (int m = 0; m < EX / LX::RL; ++m)
+                for (int m = 0; m < EX / LX::RL; m += 2)
 #pragma unroll
-              for (int j = 0; j < LX::RL; ++j)
-                if (FFTB_IN(plane + (size_t)row * N0 + LX::last_pos(gx, m, j), L.lim_cube, L.status))
-                  st_once<AG>(out + LX::last_pos(gx, m, j), v[m * LX::RL + j]);
+                  for (int j = 0; j < LX::RL; ++j)
+                    if (FFTB_IN(plane + (size_t)row * N0 + LX::last_pos(gx, m, j) + 1, L.lim_cube, L.status))
+                      st_pair(out + LX::last_pos(gx, m, j), v[m * LX::RL + j], v[(m + 1) * LX::RL + j]);
+                done = true;
+              }
+            }
+            if (!done) {
+#pragma unroll
+              for (int m = 0; m < EX / LX::RL; ++m)
+#pragma unroll
+                for (int j = 0; j < LX::RL; ++j)
+                  if (FFTB_IN(plane + (size_t)row * N0 + LX::last_pos(gx, m, j), L.lim_cube, L.status))
+                    st_once<AG>(out + LX::last_pos(gx, m, j), v[m * LX::RL + j]);
+            }
           } else if (live) {  // batch-fastest cube: points B_k apart
             C* out = static_cast<C*>(L.cube_out) + plane + (size_t)row * N0 * cst;
 #pragma unroll

@@ -13,9 +13,14 @@
 
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "fft_core.cuh"
 
 namespace fftb {
+
+// smallest row pitch >= n that is 8 (mod 16) elements (paired exchange rows)
+__host__ __device__ constexpr int pair_pitch(int n) { return n + ((8 - n % 16) + 16) % 16; }
 
 // E and the radix schedule of each supported length.
 template <int N> struct LP;
@@ -62,6 +67,18 @@ template <> struct LPV<160, 2> {
 // the same schedule for the plane kernels that drop the middle half of each
 // x line (every occupied x within [-N/4, N/4])
 template <> struct LPV<160, 3> : LPV<160, 2> {};
+// V = 4: the 40 x 4 schedule with paired ownership for lines whose outputs
+// leave in 16-byte pairs (FP32): after the exchange each lane holds the
+// radix-4 butterflies of two adjacent positions (k1 = 2 G q + 2 g + b), so
+// every output pair (x, x + 1) is in one lane. The exchange rows put two pad
+// elements after every 40 (pitch 8 (mod 16)), so that the pass-0 stores
+// (pairs of consecutive outputs of a lane) and the pass-1 loads (a lane's two
+// positions) are 16-byte accesses that hit every bank of a quarter warp once.
+template <> struct LPV<160, 4> : LPV<160, 2> {
+  static constexpr bool PAIR = true;
+};
+template <typename P, typename = void> struct lpv_pair { static constexpr bool value = false; };
+template <typename P> struct lpv_pair<P, std::void_t<decltype(P::PAIR)>> { static constexpr bool value = P::PAIR; };
 
 // ----------------------------------------------------------- tensor cores
 // A radix-8 pass as a dense product on the tensor cores (split precision):
@@ -103,14 +120,26 @@ template <int N, int V = 0> struct Line {
   static constexpr int NP = LPN::R[1] == 0 ? 1 : LPN::R[2] == 0 ? 2 : LPN::R[3] == 0 ? 3 : 4;
   static constexpr int R0 = LPN::R[0];
   static constexpr int RL = LPN::R[NP - 1];
-  static constexpr int PITCH = wpitch(N, G);
+  // paired ownership (two passes, one first-pass butterfly a lane, FP32 rows)
+  static constexpr bool PAIR = lpv_pair<LPN>::value;
+  static_assert(!PAIR || (NP == 2 && E == R0 && (E / LPN::R[1]) % 2 == 0 && (N / LPN::R[1]) % (2 * G) == 0),
+                "paired ownership: two passes, one first-pass butterfly, pairs of second-pass butterflies");
+  // exchange-row pad: one element after every 8, or (PAIR) two after every R0
+  __host__ __device__ static constexpr int pad(int e) { return PAIR ? e + 2 * (e / R0) : e + (e >> 3); }
+  static constexpr int PITCH = PAIR ? pair_pitch(N + 2 * (N / R0)) : wpitch(N, G);
   static_assert(32 % G == 0, "lanes per line must divide the warp");
   static_assert(R0 * (NP > 1 ? LPN::R[1] : 1) * (NP > 2 ? LPN::R[2] : 1) * (NP > 3 ? LPN::R[3] : 1) == N,
                 "radix schedule must multiply to N");
 
+  // the index of butterfly m of lane g in the last pass (PAIR: pairs of adjacent indices)
+  __host__ __device__ static constexpr int bfly(int g, int m) {
+    return PAIR ? 2 * G * (m >> 1) + 2 * g + (m & 1) : g + m * G;
+  }
   // position of v[m * R0 + j] before run(), and of v[m * RL + j] after it
   __device__ __forceinline__ static int first_pos(int g, int m, int j) { return g + m * G + j * (N / R0); }
-  __device__ __forceinline__ static int last_pos(int g, int m, int j) { return g + m * G + j * (N / RL); }
+  __device__ __forceinline__ static int last_pos(int g, int m, int j) {
+    return (NP == 1 ? g + m * G : bfly(g, m)) + j * (N / RL);
+  }
 
   template <int p> __host__ __device__ static constexpr int radix() { return LPN::R[p]; }
   template <int p> __host__ __device__ static constexpr int span() {  // product of radices before p
@@ -134,15 +163,16 @@ template <int N, int V = 0> struct Line {
     }
   };
 
-  // twiddle + radix-R butterflies of pass p on the lane's registers
-  template <int p, int S, typename C>
+  // twiddle + radix-R butterflies of pass p on the lane's registers (ZM: the
+  // inputs of pass 0 known to be zero, bit q for v[q])
+  template <int p, int S, unsigned long long ZM = 0, typename C>
   __device__ __forceinline__ static void compute(C (&v)[E], int g, const C* __restrict__ tw,
                                                  const TwCache<C>& tc) {
     constexpr int R = radix<p>(), P = span<p>();
 #pragma unroll
     for (int m = 0; m < E / R; ++m) {
       if constexpr (P > 1) {
-        const int k = (g + m * G) % P;
+        const int k = (p == NP - 1 ? bfly(g, m) : g + m * G) % P;
         constexpr int STEP = N / (P * R);
 #pragma unroll
         for (int j = 1; j < R; ++j) {
@@ -152,7 +182,17 @@ template <int N, int V = 0> struct Line {
           v[m * R + j] = (S > 0) ? cmul(v[m * R + j], w) : cmulc(v[m * R + j], w);
         }
       }
-      dft<R, S>(&v[m * R]);
+      if constexpr (!(p == 0 && ZM != 0)) dft<R, S>(&v[m * R]);
+    }
+    if constexpr (p == 0 && ZM != 0) first_z<S, ZM, 0>(v);
+  }
+  // pass 0 with the inputs of ZM known to be zero: butterfly M takes bits
+  // M R .. M R + R - 1 (no twiddles before the first pass)
+  template <int S, unsigned long long ZM, int M, typename C> __device__ __forceinline__ static void first_z(C (&v)[E]) {
+    constexpr int R = radix<0>();
+    if constexpr (M < E / R) {
+      dft_z<R, S, (ZM >> (M * R)) & (R >= 64 ? ~0ull : (1ull << R) - 1)>(&v[M * R]);
+      first_z<S, ZM, M + 1>(v);
     }
   }
 
@@ -174,6 +214,23 @@ template <int N, int V = 0> struct Line {
       for (int m = 0; m < E / R2; ++m)
 #pragma unroll
         for (int j = 0; j < R2; ++j) v[m * R2 + j] = t[m + j * NB2];
+    } else if constexpr (PAIR) {
+      // lane g's outputs (positions g R + j) in 16-byte pairs, then its two
+      // butterflies' inputs (positions 2 G q + 2 g + {0, 1} + j N / R2) likewise
+      static_assert(sizeof(C) == 8 && p == 0, "paired exchange: FP32, the one exchange");
+#pragma unroll
+      for (int j = 0; j < R; j += 2)
+        *reinterpret_cast<float4*>(row + pad(g * R + j)) = make_float4(v[j].x, v[j].y, v[j + 1].x, v[j + 1].y);
+      __syncwarp();
+#pragma unroll
+      for (int m = 0; m < E / R2; m += 2)
+#pragma unroll
+        for (int j = 0; j < R2; ++j) {
+          const float4 t = *reinterpret_cast<const float4*>(row + pad(bfly(g, m) + j * NB2));
+          v[m * R2 + j] = mk(t.x, t.y);
+          v[(m + 1) * R2 + j] = mk(t.z, t.w);
+        }
+      __syncwarp();
     } else {
 #pragma unroll
       for (int m = 0; m < E / R; ++m) {
@@ -190,10 +247,10 @@ template <int N, int V = 0> struct Line {
     }
   }
 
-  template <int p, int S, typename C>
+  template <int p, int S, unsigned long long ZM = 0, typename C>
   __device__ __forceinline__ static void passes(C (&v)[E], int g, C* __restrict__ row, const C* __restrict__ tw,
                                                 const TwCache<C>& tc) {
-    compute<p, S>(v, g, tw, tc);
+    compute<p, S, ZM>(v, g, tw, tc);
     if constexpr (p + 1 < NP) {
       exchange<p>(v, g, row);
       passes<p + 1, S>(v, g, row, tw, tc);
@@ -357,20 +414,21 @@ template <int N, int V = 0> struct Line {
   // v in first_pos order -> DFT (sign S) in last_pos order. All lanes of the
   // warp must call it (it synchronises the warp when G > 1). tc holds this
   // lane's pass-1 twiddles (TwCache::load with the same g and table).
-  template <int S, typename C>
+  // ZM: inputs known to be zero (bit q: v[q] of the first-pass order)
+  template <int S, unsigned long long ZM = 0, typename C>
   __device__ __forceinline__ static void run(C (&v)[E], int g, C* __restrict__ row, const C* __restrict__ tw,
                                              const TwCache<C>& tc) {
-    passes<0, S>(v, g, row, tw, tc);
+    passes<0, S, ZM>(v, g, row, tw, tc);
   }
 
   // As run() for a two-pass schedule, with two hooks around its one exchange:
   // before() runs (on every lane) before the exchange rows are written,
   // after() once every lane has read them back (the rows are free again).
-  template <int S, typename C, typename B, typename A>
+  template <int S, unsigned long long ZM = 0, typename C, typename B, typename A>
   __device__ __forceinline__ static void run2(C (&v)[E], int g, C* __restrict__ row, const C* __restrict__ tw,
                                               const TwCache<C>& tc, B&& before, A&& after) {
     static_assert(NP == 2 && G > 1, "one exchange between two passes");
-    compute<0, S>(v, g, tw, tc);
+    compute<0, S, ZM>(v, g, tw, tc);
     before();
     exchange<0>(v, g, row);
     after();
