@@ -422,8 +422,11 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
   using C = typename cplx<T>::type;
   using LY = Line<N1, V>;
   // G -> r with the two-pass schedule (FP32): the x lines take the paired
-  // variant, whose outputs leave as 16-byte pairs
-  using LX = Line<N0, ((V == 2 || V == 3) && MODE == M_G2R && sizeof(T) == 4 && N0 == 160 && !TC && !AG && !PF) ? 4 : V>;
+  // variant, whose outputs leave as 16-byte pairs (measured: 14 % faster at
+  // 160^3; the same variant for the y lines, whose outputs go to the slab
+  // plane, measured 1.5 % slower)
+  constexpr bool PAIRED = (V == 2 || V == 3) && MODE == M_G2R && sizeof(T) == 4 && !TC && !AG && !PF;
+  using LX = Line<N0, (PAIRED && N0 == 160) ? 4 : V>;
   constexpr int NW = PlaneCfg<T>::NW, NT = NW * 32;
   constexpr int WY = 32 / LY::G, WX = 32 / LX::G;   // lines per warp
   constexpr int EY = LY::E, EX = LX::E;
@@ -781,9 +784,9 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
           __syncwarp();
           for (int s = sbeg + lane; s < send; s += 32) {
             const int xy = sxy[s];
-            if constexpr (PF) scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)] = Tr[s];
+            if constexpr (PF) scr[((xy >> 16) - c0) * LY::PITCH + LY::pad(xy & 0xFFFF)] = Tr[s];
             else if (FFTB_IN(tz + s, L.lim_T, L.status))
-              scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)] = ld_once<AG>(Tr + s);
+              scr[((xy >> 16) - c0) * LY::PITCH + LY::pad(xy & 0xFFFF)] = ld_once<AG>(Tr + s);
           }
           __syncwarp();
 #pragma unroll
@@ -791,7 +794,7 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
             for (int j = 0; j < LY::R0; ++j)
               v[m * LY::R0 + j] = XQ && x_mid<N1, LY::G, LY::R0>(m * LY::R0 + j) ? czero<C>()  // no stick there
-                                                                                 : rowy[wpad(LY::first_pos(gy, m, j))];
+                                                                                 : rowy[LY::pad(LY::first_pos(gy, m, j))];
           __syncwarp();
         }
         if constexpr (TC) LY::template run_tc<+1>(v, gy, rowy, scr, tw1, tcy, wy_p);
@@ -898,13 +901,13 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
             for (int j = 0; j < LX::RL; ++j) {
               const int x = LX::last_pos(gx, m, j);
               const bool vin = FFTB_IN((size_t)z * (N1 * N0) + (size_t)(live ? row : 0) * N0 + x, L.lim_V, L.status);
-              rowx[wpad(x)] = scale(v[m * LX::RL + j], vin ? __ldg(vr + x) : T(0));
+              rowx[LX::pad(x)] = scale(v[m * LX::RL + j], vin ? __ldg(vr + x) : T(0));
             }
           __syncwarp();
 #pragma unroll
           for (int m = 0; m < EX / LX::R0; ++m)
 #pragma unroll
-            for (int j = 0; j < LX::R0; ++j) v[m * LX::R0 + j] = rowx[wpad(LX::first_pos(gx, m, j))];
+            for (int j = 0; j < LX::R0; ++j) v[m * LX::R0 + j] = rowx[LX::pad(LX::first_pos(gx, m, j))];
           __syncwarp();
           if constexpr (TC) LX::template run_tc<-1>(v, gx, rowx, scr, tw0, tcx, wx_m);
           else LX::template run<-1>(v, gx, rowx, tw0, tcx);
@@ -1076,14 +1079,14 @@ __global__ void __launch_bounds__(PlaneCfg<T>::NW * 32, (plane_minb<T, N0>())) k
 #pragma unroll
             for (int j = 0; j < LY::RL; ++j) {
               if (XQ && x_mid<N1, LY::G, LY::RL>(m * LY::RL + j)) continue;  // no stick there
-              rowy[wpad(LY::last_pos(gy, m, j))] = v[m * LY::RL + j];
+              rowy[LY::pad(LY::last_pos(gy, m, j))] = v[m * LY::RL + j];
             }
           __syncwarp();
           const int sbeg = __shfl_sync(0xffffffffu, ci.x, 0);
           const int send = __shfl_sync(0xffffffffu, ci.x + ci.y, (nl - 1) * LY::G);
           for (int s = sbeg + lane; s < send; s += 32) {
             const int xy = sxy[s];
-            if (FFTB_IN(tz + s, L.lim_T, L.status)) Tz[s] = scr[((xy >> 16) - c0) * LY::PITCH + wpad(xy & 0xFFFF)];
+            if (FFTB_IN(tz + s, L.lim_T, L.status)) Tz[s] = scr[((xy >> 16) - c0) * LY::PITCH + LY::pad(xy & 0xFFFF)];
           }
           __syncwarp();
         }

@@ -259,3 +259,43 @@ def test_160_two_pass_quarter_x_pruning(F, r):
     torch.cuda.synchronize()
     pa.check()
     assert relerr(oa.cpu().numpy(), oracle.apply_potential(g, c64[:1], v.astype(np.float64), n)) <= 2e-6
+
+
+def test_160_two_pass_g2r_paired_store_paths(F):
+    """The G -> r x lines of the 160 = 40 x 4 schedule own adjacent output
+    pairs and store them as 16-byte pairs where the cube starts on a 16-byte
+    boundary: a cube 8 bytes off that boundary takes the 8-byte stores (same
+    values, bit for bit), and the batch-fastest cube (points B_k apart) is
+    stored point by point; both against the oracle."""
+    import torch
+    n, r, bands = (160, 160, 160), 40.0, 2
+    vol = 160 ** 3
+    plan = F.Plan(n, "g2r", "fp32", radius=r, bands=[bands])
+    plan.set_radix_schedule(1, 0)
+    assert plan.info["radix_schedule_plane"] & 1
+    g = plan.sphere(0)
+    c = fi.complex_gaussian((bands, len(g)), 131).astype(np.complex64)
+    x = torch.from_numpy(c.reshape(-1)).cuda()
+    out = torch.empty(bands * vol, dtype=torch.complex64, device="cuda")
+    plan.execute(x, out)
+    buf = torch.zeros(bands * vol + 1, dtype=torch.complex64, device="cuda")
+    off = buf[1:]  # 8 bytes past a 16-byte boundary
+    assert off.data_ptr() % 16 == 8
+    plan.execute(x, off)
+    torch.cuda.synchronize()
+    plan.check()
+    assert torch.equal(off, out)
+    assert buf[0].item() == 0
+    got = out.view(bands, 160, 160, 160)[1].cpu().numpy()
+    assert relerr(got, oracle.g2r(g, c[1].astype(np.complex128), n)) <= 2e-6
+    del out, buf, off
+    pb = F.Plan(n, "g2r", "fp32", radius=r, bands=[3], layout=1)
+    pb.set_radix_schedule(1, 0)
+    cb = fi.complex_gaussian((3, len(g)), 132).astype(np.complex64)
+    ob = torch.empty(pb.info["cube_elems"], dtype=torch.complex64, device="cuda")
+    pb.execute(torch.from_numpy(np.ascontiguousarray(cb.T).reshape(-1)).cuda(), ob)
+    torch.cuda.synchronize()
+    pb.check()
+    band2 = ob.view(160, 160, 160, 3)[..., 2].cpu().numpy()
+    assert relerr(band2, oracle.g2r(g, cb[2].astype(np.complex128), n)) <= 2e-6
+    torch.cuda.empty_cache()
