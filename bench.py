@@ -136,7 +136,7 @@ def peaks():
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("fft_core.cuh", "line_fft.cuh", "kernels.cuh", "async_copy.cuh", "check.cuh", "k_f32_pf.cu",
-              "k_f32_alt.cu"):
+              "k_f32_alt.cu", "k_f32_zq.cu"):
         h.update(open(os.path.join(ROOT, "paper_2406_05577_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
