@@ -78,8 +78,8 @@ struct Geo {
   const void* tw1;           // [N1]
   const void* tw2;           // [N2]
   int32_t n0, n1, n2;
-  int32_t smax;              // T pitch: max sticks over k, rounded up to a multiple of 16
-                             //   (rows start on 128-byte boundaries for FP32)
+  int32_t smax;              // T pitch: max sticks over k, rounded up to even (rows start
+                             //   on 16-byte boundaries for bulk copies)
   int32_t xmax;              // max slabs over k
 };
 
