@@ -212,6 +212,13 @@ int plane_wave(const fftb_plan_s* p, int i) {
 }
 // persistent z-stage CTAs of one full wave for the schedule in use
 int stick_wave(const fftb_plan_s* p) { return p->sms * (p->sched_stick ? p->alt_stick_occ : p->stick_occ); }
+// resident CTAs per SM of the plan's default-schedule z-stage kernels (the
+// pruned FP32 ones where every k-point's entries lie within a quarter in z)
+int default_stick_occ(const fftb_plan_s* p) {
+  const int o = p->stick_prec == P_F32 && p->zq_all ? stick_zq_occupancy(p->n[2])
+                                                      : stick_occupancy(p->stick_prec, p->n[2]);
+  return std::max(1, o);
+}
 
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -288,7 +295,7 @@ fftb_status set_tc(fftb_plan_s* p, bool on) {
   p->bg = on ? 0 : p->bg_size;  // the grouped batch-fastest kernels are FP32 kernels
   fftb_status st = configure_planes(p);
   if (st != FFTB_OK) return st;
-  p->stick_occ = std::max(1, stick_occupancy(p->stick_prec, p->n[2]));
+  p->stick_occ = default_stick_occ(p);
   p->alt_stick_ok = false;
   if (p->stick_prec == P_F32 && alt_schedule(p->n[2])) {
     cudaError_t e = prepare_alt(0, p->n[2], 0, 1);
@@ -661,11 +668,11 @@ FFTB_EXPORT fftb_status fftb_plan_create(fftb_plan* out, const fftb_desc* d, fft
       }
     }
   }
-  p->stick_occ = std::max(1, stick_occupancy(p->stick_prec, p->n[2]));
   if (p->prec != FFTB_FP64 && p->zq_all) {  // FP32 z stages (MIXED_TC: once its tensor cores are off)
     e = prepare_stick_zq(p->n[2]);
     if (e != cudaSuccess) { release(p); return cuda_fail(e, "kernel attributes"); }
   }
+  p->stick_occ = default_stick_occ(p);
   if (p->stick_prec == P_F32 && alt_schedule(p->n[2])) {
     e = prepare_alt(0, p->n[2], 0, 1);
     if (e != cudaSuccess) { release(p); return cuda_fail(e, "kernel attributes"); }

@@ -178,6 +178,7 @@ cudaError_t launch_stick_alt(int mode, const Launch& L, int ctas);
 // FP32 z-stage kernels that drop the middle half of each z line (k_f32_zq.cu;
 // default schedule; launches whose k-points all have KF_Z_QUARTER)
 cudaError_t prepare_stick_zq(int n2);
+int stick_zq_occupancy(int n2);  // resident CTAs per SM (after prepare_stick_zq)
 cudaError_t launch_stick_zq(int mode, const Launch& L, int ctas);
 // MIXED_TC plane stage on the 5th-generation tensor cores (k_tc5.cu): the
 // union over k-points of the occupied x values [xlo, xlo + xu) and of the

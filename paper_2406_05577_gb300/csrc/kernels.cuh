@@ -68,12 +68,13 @@ template <typename T, int N2, int V = 0> constexpr size_t stick_smem_c() {
 }
 
 // resident z-stage CTAs per SM the register allocation must allow (FP32: two,
-// measured best; the 128-point z-stage ran one CTA per SM without the cap)
-template <typename T> __host__ __device__ constexpr int stick_minb() {
+// measured best; the 128-point z-stage ran one CTA per SM without the cap;
+// the two-pass schedule V = 2 holds 40 elements a lane: one)
+template <typename T, int V = 0> __host__ __device__ constexpr int stick_minb() {
 #ifdef FFTB_STICK_MINB
   return FFTB_STICK_MINB;
 #else
-  return sizeof(T) == 8 ? 1 : 2;
+  return (sizeof(T) == 8 || V == 2) ? 1 : 2;
 #endif
 }
 
@@ -82,7 +83,7 @@ template <typename T> __host__ __device__ constexpr int stick_minb() {
 // of the line, whose loads, stores and (r -> G) arithmetic are dropped at
 // compile time.
 template <typename T, int N2, int MODE, bool TC = false, int V = 0, bool QZ = false>
-__global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(const Launch L) {
+__global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T, V>())) k_stick(const Launch L) {
   using C = typename cplx<T>::type;
   using LZ = Line<N2, V>;
   constexpr int WZ = 32 / LZ::G, EZ = LZ::E, NT = STICK_NW * 32;
@@ -282,9 +283,23 @@ __global__ void __launch_bounds__(STICK_NW * 32, (stick_minb<T>())) k_stick(cons
     __syncwarp();
   };
 
+  if (t0 >= t1) return;
+  if constexpr (V == 2) {
+    // the two-pass schedule (40 elements a lane) leaves no registers for a
+    // second task in flight: one task at a time, eight sticks a warp
+#pragma unroll 1
+    for (int t = t0; t < t1; t += nwarps) {
+      const Task k = meta(t);
+      if (!k.live) continue;
+      C v[EZ];
+      if (MODE == M_R2G || k.canon) load(k, v);
+      else scatter_load(k, v);
+      finish(k, v);
+    }
+    return;
+  }
   // two-deep software pipeline: the next task's records and inputs are in
   // flight while the current task is transformed and written
-  if (t0 >= t1) return;
   C va[EZ], vb[EZ];
   Task ka = meta(t0), kb{};
   if (ka.live && (MODE == M_R2G || ka.canon)) load(ka, va);
