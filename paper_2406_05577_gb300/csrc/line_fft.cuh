@@ -3,12 +3,14 @@
 // A length-N line is held by G = N / E lanes, E elements each. The DFT is
 // factored Cooley-Tukey style (Sec. 2.1) into Stockham passes whose radices
 // all divide E, so in every pass each lane owns E / R whole butterflies:
-// butterfly m of lane g is i = g + m G; its inputs sit at i + j N/R. The
+// butterfly m of lane g is i = g + m G (the paired variant's last pass:
+// i = 2 G (m / 2) + 2 g + m mod 2); its inputs sit at i + j N/R. The
 // lane->butterfly map is fixed, so every address below is a per-lane base plus
 // a compile-time offset. Between passes the lanes of a line exchange values
 // through a private shared-memory row of the warp (one pad element after
-// every 8, so stride-R stores fall on distinct banks); a line held by a single
-// lane (G = 1) exchanges by register renaming only.
+// every 8, so stride-R stores fall on distinct banks; the paired variant two
+// after every R0); a line held by a single lane (G = 1) exchanges by register
+// renaming only.
 #pragma once
 
 #include <cuda_fp16.h>

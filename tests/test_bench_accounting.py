@@ -71,3 +71,21 @@ def test_kernel_source_hash_covers_the_profiled_kernels():
     for k, v in d["kernels"].items():
         assert v["dram_bytes_per_band"] == round((v["read_bytes"] + v["write_bytes"]) / v["bands_per_launch"])
     assert len(bench.kernel_source_hash()) == 16
+
+
+def test_kernel_source_hash_ignores_comments_only(tmp_path, monkeypatch):
+    """The traffic record stays valid across comment edits of the kernel
+    sources and goes stale on any code edit."""
+    import os
+    import shutil
+    src = os.path.join(bench.ROOT, "paper_2406_05577_gb300", "csrc")
+    dst = tmp_path / "paper_2406_05577_gb300" / "csrc"
+    shutil.copytree(src, dst)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    f = dst / "line_fft.cuh"
+    text = f.read_text()
+    f.write_text("// a new comment line\n\n" + text.replace("#pragma once", "#pragma once  // trailing note", 1))
+    assert bench.kernel_source_hash() == h0
+    f.write_text(text.replace("#pragma once", "#pragma once\nconstexpr int fftb_unused_probe = 1;", 1))
+    assert bench.kernel_source_hash() != h0
