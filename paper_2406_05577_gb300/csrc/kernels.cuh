@@ -1178,9 +1178,14 @@ template <typename T, bool TC> size_t plane_smem_t(int n0, int n1, int xmax, int
   }
   return 0;
 }
+// schedule of the default z-stage kernels: FP32 160-point lines on the
+// two-pass 40 x 4 schedule (as the pruned ones), the rest their default
+template <typename T, bool TC, int N2> constexpr int stick_v() {
+  return (sizeof(T) == 4 && !TC && N2 == 160) ? 2 : 0;
+}
 template <typename T, bool TC> int stick_tile_t(int n2) {
   switch (n2) {
-#define C_(N) case N: return stick_tile_c2<N>();
+#define C_(N) case N: return stick_tile_c2<N, stick_v<T, TC, N>()>();
     FFTB_SIZES(C_)
 #undef C_
   }
@@ -1188,12 +1193,13 @@ template <typename T, bool TC> int stick_tile_t(int n2) {
 }
 
 template <typename T, bool TC, int N2> cudaError_t go_stick(int mode, const Launch& L, int ctas) {
-  const size_t smem = stick_smem_c<T, N2>();
-  const int gpb = (L.g.smax + (32 / Line<N2>::G) - 1) / (32 / Line<N2>::G);
+  constexpr int V = stick_v<T, TC, N2>();
+  const size_t smem = stick_smem_c<T, N2, V>();
+  const int gpb = (L.g.smax + (32 / Line<N2, V>::G) - 1) / (32 / Line<N2, V>::G);
   const int need = (L.nb * gpb + STICK_NW - 1) / STICK_NW;  // one task per warp
   const dim3 grid(ctas > 0 ? min(ctas, need) : need);
-  if (mode == M_G2R) return launch_k(k_stick<T, N2, M_G2R, TC>, grid, STICK_NW * 32, smem, L, L);
-  return launch_k(k_stick<T, N2, M_R2G, TC>, grid, STICK_NW * 32, smem, L, L);
+  if (mode == M_G2R) return launch_k(k_stick<T, N2, M_G2R, TC, V>, grid, STICK_NW * 32, smem, L, L);
+  return launch_k(k_stick<T, N2, M_R2G, TC, V>, grid, STICK_NW * 32, smem, L, L);
 }
 template <typename T, bool TC, int N, bool QP = false> cudaError_t go_plane(int mode, const Launch& L) {
   if constexpr (!QP && qp_variant<T, TC, N>()) {
@@ -1222,10 +1228,11 @@ template <typename T, bool TC, int N, bool QP = false> cudaError_t go_plane(int 
   return launch_k(k_plane<T, N, N, M_APPLY, TC, false, false, 0, QP>, grid, NT, smem, L, L);
 }
 template <typename T, bool TC, int N2> cudaError_t prep_stick() {
-  const int s = (int)stick_smem_c<T, N2>();
-  cudaError_t e = raise_smem_limit((const void*)k_stick<T, N2, M_G2R, TC>, s);
+  constexpr int V = stick_v<T, TC, N2>();
+  const int s = (int)stick_smem_c<T, N2, V>();
+  cudaError_t e = raise_smem_limit((const void*)k_stick<T, N2, M_G2R, TC, V>, s);
   if (e == cudaSuccess)
-    e = raise_smem_limit((const void*)k_stick<T, N2, M_R2G, TC>, s);
+    e = raise_smem_limit((const void*)k_stick<T, N2, M_R2G, TC, V>, s);
   return e;
 }
 template <typename T, bool TC, int N, bool QP = false> cudaError_t prep_plane(int xmax, int a_bufs, bool ag) {
@@ -1284,9 +1291,10 @@ template <typename T, bool TC, int N, bool QP = false> int occ_plane(int mode, i
   return e == cudaSuccess ? min(nb, nq) : 0;
 }
 template <typename T, bool TC, int N2> int occ_stick() {
+  constexpr int V = stick_v<T, TC, N2>();
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stick<T, N2, M_G2R, TC>, STICK_NW * 32, stick_smem_c<T, N2>()) !=
-      cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stick<T, N2, M_G2R, TC, V>, STICK_NW * 32,
+                                                    stick_smem_c<T, N2, V>()) != cudaSuccess)
     return 0;
   return nb;
 }
