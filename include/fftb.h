@@ -289,10 +289,11 @@ fftb_status fftb_plan_set_prefetch(fftb_plan plan, int32_t level);
 fftb_status fftb_plan_set_slab_buffers(fftb_plan plan, int32_t nbuf);
 
 /* Radix schedule of the FP32 line FFTs: 0 the default, 1 the alternative for
- * the lengths that have one (64 = 16x4, 96 = 12x8, 128 = 8x16, 160 = 10x4x4;
- * the defaults are 8x8, 6x4x4, 16x8, 4x4x2x5), separately for the y/x lines of
- * the plane stages (here all three at once; the autotuner chooses per stage)
- * and the z lines. The alternative plane schedule excludes the bulk-copy
+ * the lengths that have one (64 = 16x4, 96 = 12x8, 128 = 8x16; 160 = 40x4 for
+ * the y/x lines and 10x4x4 for the z lines; the defaults are 8x8, 6x4x4, 16x8,
+ * and 4x4x2x5 for the y/x lines and 40x4 for the z lines of 160), separately
+ * for the y/x lines of the plane stages (here all three at once; the
+ * autotuner chooses per stage) and the z lines. The alternative plane schedule excludes the bulk-copy
  * prefetch. Resets the persistent CTAs to one full wave; fftb_plan_autotune
  * also tries the schedules. Errors: INVALID_ARG for
  * values other than 0/1; UNSUPPORTED where no alternative exists (other
